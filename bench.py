@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Benchmark: coupled Gibbs site-updates/s of fixed-budget coupled score-weighted MCPD on GB300.
+
+Workload: the 1298-clone x 97-pool k = 6 random k-sets design at high noise (fp .10, fn .20, three
+true positives, q = 3/1298), 524288 logical slots per GPU, a budget of 4e10 single-site updates per
+GPU (horizon B = 38146 progress units per slot), window l = n_a = 1298, k = 131.  One step is one
+whole decode: every slot runs its coupled pairs to the horizon with refill (Algorithms 3-4), the
+N*_p buckets are summed and theta_CT and its standard errors are finalized on the device.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` counts single-site updates executed by the sampling kernel
+(two per coupled draw, one for each replication's pre-lag draw) per second of device time with the
+tables resident on the GPU; `e2e` is the same metric through mcpd_decode from host arrays to host
+arrays.  The reference arm times the CPU oracle on the host's cores on a bounded slot sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled Gibbs site-updates/s"
+UNIT = "site-updates/s"
+SLOTS = 524288
+BUDGET = 4e10
+SEED = 20260
+
+
+def workload_config(extra=None):
+    cfg = {"workload": "MCPD high-noise 1298x97 k=6 fp=.10 fn=.20, 3 positives, q=3/1298; "
+                       "524288 coupled-pair slots per GPU, budget 4e10 site-updates per GPU "
+                       "(B=38146), window k=131 l=1298, score-weighted scan, all-negative start",
+           "n_clones": 1298, "n_pools": 97, "pools_per_clone": 6, "slots_per_gpu": SLOTS,
+           "budget_site_updates_per_gpu": BUDGET, "seed": SEED,
+           "l2": "inputs smaller than L2 (tables are staged in shared memory); a 256 MiB buffer "
+                 "is written between timed steps to flush L2"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def algorithmic_ops_per_progress_unit(deg: int) -> float:
+    """Integer operations one coupled draw needs by the method's definition:
+    half a Philox4x32-10 block (78 ops per block), the alias draw (4), per chain and per pool of the
+    drawn site the 'no other positive' test and the (n+, n-) count (2 each), and per chain the
+    64-bit threshold comparison (2)."""
+    return 78 / 2 + 4 + 2 * (2 * deg) + 2 * 2
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.device_index = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{device_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(seconds: float, steps_label: str = ""):
+    """The oracle as it stands on the host's cores on a bounded sample of the workload's slots."""
+    import oracle
+    import synth
+    inst = synth.high_noise_config()
+    k, ell = oracle.window_defaults(inst.n, 1)
+    B = synth.budget_horizon(BUDGET, SLOTS)
+    cores = os.cpu_count() or 1
+    M = oracle.Model(inst)
+    run = oracle.coupled_run(k, ell, B, SEED)
+    t0 = time.perf_counter()
+    r = M.run_slots(run, 0, cores, cores)                      # calibration: one slot per core
+    dt = time.perf_counter() - t0
+    per_round = max(dt, 1e-3)
+    rounds = max(1, int(seconds / per_round))
+    n_slots = cores * rounds
+    t0 = time.perf_counter()
+    r = M.run_slots(oracle.coupled_run(k, ell, B, SEED, slot_offset=cores), 0, n_slots, cores)
+    dt = time.perf_counter() - t0
+    st = r["stats"]
+    site_updates = 2 * st["draws"] - st["reps"]
+    return {"value": site_updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_slots} of the workload's {SLOTS} slots (slot ids {cores}..{cores + n_slots - 1}), "
+                      f"{site_updates} site-updates in {dt:.2f} s with {cores} threads{steps_label}",
+            "seconds": dt, "site_updates": site_updates}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_oracle_sample(2.0)
+    vals, times = [], []
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        s = cpu_oracle_sample(args.ref_seconds)
+        vals.append(s["value"])
+        times.append(s["seconds"])
+    wall = time.perf_counter() - t_all
+    value = sum(vals) / len(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "impl": "reference", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"each step a bounded slot sample of ~{args.ref_seconds:.0f} s"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2608_30239_gb300 import build as lib_build
+    from paper_2608_30239_gb300 import mcpd
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    device = local_rank
+    torch.cuda.set_device(device)
+    lib_build.build()
+
+    inst = synth.high_noise_config()
+    offset = rank * SLOTS
+    ctx = mcpd.Context(device)
+    plan = mcpd.Plan(ctx, inst, slots=SLOTS, budget_site_updates=BUDGET, seed=SEED,
+                     slot_offset=offset)
+    est = torch.empty(plan.n_active, dtype=torch.float64, device=f"cuda:{device}")
+    se = torch.empty_like(est)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{device}")
+    stream = torch.cuda.current_stream(device)
+
+    for _ in range(args.warmup):
+        plan.run_async(est, se)
+        plan.collect()
+
+    clocks = ClockSampler(device)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)                       # L2 flush, outside the timed interval
+        ev[i][0].record(stream)
+        plan.run_async(est, se)
+        ev[i][1].record(stream)
+        stats.append(plan.collect())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1000.0
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device=f"cuda:{device}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    su_step = stats[-1]["site_updates"]
+    pu_step = stats[-1]["progress_units"]
+    value = su_step * args.steps * world / total_s
+    kernel_ms = statistics.mean(s["kernel_ms"] for s in stats)
+
+    # end to end through the public host-array API: plan, upload, run, download, every step
+    e2e_times = []
+    h2d = d2h = 0
+    for i in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = ctx.decode(inst, slots=SLOTS, budget_site_updates=BUDGET, seed=SEED, slot_offset=offset)
+        e2e_times.append(time.perf_counter() - t0)
+        assert out["status"] == 0
+    na = plan.n_active
+    h2d = na * 8 + na * 16 + 81 * 8                  # alias words, clone rows, thresholds
+    d2h = 2 * na * 8 + 16 * 8 + 4                    # estimates, standard errors, counters, flag
+    e2e_val = su_step * world / statistics.mean(e2e_times)
+
+    peaks, peak_kind = _peaks()
+    props = torch.cuda.get_device_properties(device)
+    sm_count = props.multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or 2070.0)
+    peak_ops = 128.0 * sm_count * max_mhz * 1e6       # 4 schedulers x 32 lanes issue per clock
+    ops = algorithmic_ops_per_progress_unit(6) * pu_step
+    achieved = ops / (kernel_ms / 1000.0)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
+                "note": f"issue-slot peak = 128 lane-ops/clk/SM x {sm_count} SMs x {max_mhz:.0f} MHz "
+                        f"({peak_kind} max clock); algorithmic ops = "
+                        f"{algorithmic_ops_per_progress_unit(6):.0f} per coupled draw"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * total_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": workload_config({"parallelism": f"slot shards x{world}",
+                                       "progress_units_per_step": pu_step,
+                                       "site_updates_per_step": su_step,
+                                       "replications_per_step": stats[-1]["reps_retained"],
+                                       "estimators_per_s": stats[-1]["reps_retained"] * args.steps * world / total_s,
+                                       "pairs_kernel_ms": kernel_ms,
+                                       "max_se": float(se.max().item()),
+                                       "wall_s_timed": wall}),
+            "roofline": roofline,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "seconds_per_step": statistics.mean(e2e_times)},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * mcpd.h - C ABI of the GB300 library for coupled score-weighted Markov chain pool decoding.
+ *
+ * Problem (paper, Section "Knill's Method"): a pooling matrix A (m pools x n clones), observed
+ * pool outcomes y, false-positive rate fp, false-negative rate fn and prior q define the posterior
+ * pi(z | y) ∝ prod_i q^{z_i} (1-q)^{1-z_i} prod_j Pr{y_j | xi_j(z)}.  The library estimates
+ * p_i = E_pi[Z_i] for every retained clone with the fixed-budget, completion-time-corrected
+ * aggregate theta_CT of lag-1 coupled score-weighted random-scan Gibbs pairs (Algorithms 3 and 4;
+ * Theorems 1 and 2) and returns a standard error per clone.
+ *
+ * Conventions for every call:
+ *   - Return value 0 (MCPD_OK) on success, a negative MCPD_E* code otherwise; the message of the
+ *     last failure on a context is available from mcpd_last_error().
+ *   - Host inputs are borrowed for the duration of the call only (copied before return).
+ *   - Host outputs are caller-owned arrays of the stated length.  Device outputs are caller-owned
+ *     device allocations on the context's device, written on the context's stream.
+ *   - Sizes are element counts unless a name says bytes.
+ *   - All calls on one context are serialised on that context's stream; a context must not be
+ *     used from two host threads at once.
+ *   - Identical inputs and seed give bit-identical outputs whatever the GPU schedule: every random
+ *     number is keyed by (seed, instance, global slot, replication, time) and every reduction is an
+ *     integer sum.
+ */
+#ifndef MCPD_H
+#define MCPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define MCPD_OK 0
+#define MCPD_EINVAL (-1)       /* an argument is out of range or inconsistent                     */
+#define MCPD_ETOO_LARGE (-2)   /* a size exceeds what the kernels support (see mcpd_params)       */
+#define MCPD_ENOMEM (-3)       /* a host or device allocation failed                              */
+#define MCPD_ECUDA (-4)        /* a CUDA runtime call failed                                      */
+#define MCPD_ESTEP_LIMIT (-5)  /* a pair reached params.step_limit without meeting; the outputs
+                                  are written but must not be used                               */
+#define MCPD_EOVERFLOW (-6)    /* an integer accumulator bound would be exceeded                  */
+
+/* Site-selection schemes (Preliminaries; Section "Score-Weighted Update Gibbs Sampler"). */
+#define MCPD_SCAN_SCORE 0      /* w_i = 0.5 softmax(tau_w s)_i + 0.5/n_a, the paper's weights    */
+#define MCPD_SCAN_UNIFORM 1    /* w_i = 1/n_a (random update)                                    */
+#define MCPD_SCAN_SYSTEMATIC 2 /* I_t = t mod n_a (Knill's systematic scan; uncoupled only)      */
+#define MCPD_SCAN_CUSTOM 3     /* caller weights, each >= 0.25/n_a after normalisation           */
+
+/* Pooling design as a clone -> pool CSR (the nonzeros of A by column).
+ * clone_pools[clone_ptr[i] .. clone_ptr[i+1]) lists the pools holding clone i, strictly
+ * increasing, each in [0, n_pools).  Limits of this build: n_clones <= 65535, n_pools <= 1022,
+ * at most 8 pools per clone, at most 255 clones per pool. */
+typedef struct mcpd_design {
+    int32_t n_clones;          /* n */
+    int32_t n_pools;           /* m */
+    const int32_t *clone_ptr;  /* [n + 1], host */
+    const int32_t *clone_pools;/* [clone_ptr[n]], host */
+} mcpd_design;
+
+/* Run parameters.  Zero-initialise and set what you need; -1 / 0 select the defaults noted. */
+typedef struct mcpd_params {
+    double fp, fn, prior_q;    /* 0 < fp, fn, q < 1 (Assumption 1)                                 */
+    int32_t n_active;          /* 0: keep all clones; else keep the top n_active by the naive
+                                  log score eta_i (ties to the lower index), others fixed to 0    */
+    int32_t scan;              /* MCPD_SCAN_*                                                     */
+    int32_t coupled;           /* 1: Algorithms 3-4 (coupled pairs, unbiased); 0: Algorithms 1-2
+                                  (one chain per replication, burn-in average)                    */
+    int32_t lanes_per_pair;    /* 0: automatic; 1: one thread per pair (the only layout of this
+                                  build)                                                          */
+    const double *scan_weights;   /* MCPD_SCAN_CUSTOM: [n_active] positive weights, host          */
+    const double *init_marginals; /* NULL: Z_0 = 0 (all negative); else [n_active] in [0,1], host:
+                                  Z_0 ~ prod_i Bernoulli(nu_i)                                    */
+    int64_t k, ell;            /* coupled averaging window k:l, 0 <= k <= l; -1: one sweep,
+                                  l = n_a, k = round_half_even(0.1 n_a) + 1                        */
+    int64_t burn, length;      /* uncoupled: average X_b .. X_{b+T-1}; -1: b = round(0.1 n_a),
+                                  T = n_a - b                                                    */
+    int64_t slots;             /* P logical slots (>= 1)                                          */
+    int64_t horizon;           /* B, progress units per slot (one progress unit = one shared draw
+                                  (I_t, U_t)); used when budget_site_updates <= 0                 */
+    double budget_site_updates;/* > 0: B = floor(budget / (2 P)) coupled, floor(budget / P)
+                                  uncoupled                                                       */
+    int64_t step_limit;        /* safety limit on one replication's length; 0: 10^4 n_a           */
+    uint64_t seed;
+    uint32_t instance_id;      /* < 2^24, enters every random-number counter                      */
+    int32_t record_slots;      /* 1: keep per-slot N*_p, retained cost and replication counts     */
+    int64_t slot_offset;       /* global id of slot 0 (partitioning slots across calls or GPUs)   */
+    int64_t trace_stride;      /* > 0: keep the G vector of every slot p with p % stride == 0     */
+} mcpd_params;
+
+/* Counters of one run. */
+typedef struct mcpd_stats {
+    int64_t progress_units;    /* shared draws executed, aborted replications included            */
+    int64_t site_updates;      /* single-site updates executed (2 per coupled draw but the
+                                  pre-lag one, 1 per uncoupled draw)                              */
+    int64_t reps_started, reps_retained, reps_aborted;
+    int64_t zero_completion_slots;  /* slots with N_p(B) = 0 (first replication kept)             */
+    int64_t step_limit_hits;
+    int64_t max_tau, sum_tau;  /* meeting times of completed replications                         */
+    int64_t n_buckets;         /* number of N*_p values the integer sums are kept for             */
+    int64_t n_active;
+    double kernel_ms;          /* device time of the sampling kernel (CUDA events)                */
+} mcpd_stats;
+
+typedef struct mcpd_ctx mcpd_ctx;
+typedef struct mcpd_plan mcpd_plan;
+
+/* Create a context on CUDA device `device` that issues all work on `cuda_stream` (a cudaStream_t,
+ * NULL for the legacy default stream).  The context owns the device scratch memory of its plans. */
+int mcpd_ctx_create(int device, void *cuda_stream, mcpd_ctx **out);
+void mcpd_ctx_destroy(mcpd_ctx *ctx);
+const char *mcpd_last_error(const mcpd_ctx *ctx);
+
+/* Build a plan: validate the inputs, compute the naive scores and pruning (Section "Knill's
+ * Method"), the score weights and their integer alias table (Section "Score-Weighted Update Gibbs
+ * Sampler"), the acceptance thresholds of the full conditional, and upload them with the device
+ * scratch (per-pair accumulators, N*_p buckets).  y: [n_pools] 0/1 bytes, host. */
+int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
+                     const mcpd_params *params, mcpd_plan **out);
+void mcpd_plan_destroy(mcpd_plan *plan);
+
+/* Plan facts: info[0] n_active, [1] n_buckets, [2] horizon B, [3] k (burn b uncoupled),
+ * [4] l (b + T - 1 uncoupled), [5] L (window length), [6] slots P, [7] warps per block,
+ * [8] resident pairs, [9] shared-memory bytes per block, [10] lanes per pair. */
+int mcpd_plan_info(const mcpd_plan *plan, int64_t info[16]);
+/* active[a] = original index of the a-th retained clone (ascending). */
+int mcpd_plan_active(const mcpd_plan *plan, int32_t *active);
+
+/* Run the sampler (Algorithms 3/4, or 1/2 when uncoupled) and finalize on the device.
+ * est_dev, se_dev: device arrays [n_active] (active order) receiving theta_CT and its standard
+ * error.  Asynchronous: returns after enqueueing on the context stream. */
+int mcpd_run_async(mcpd_ctx *ctx, mcpd_plan *plan, double *est_dev, double *se_dev);
+/* Wait for the last run of `plan`, read its counters and its error flag.  Returns
+ * MCPD_ESTEP_LIMIT if any pair hit the safety limit. stats may be NULL. */
+int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *plan, mcpd_stats *stats);
+
+/* Fetch results of the last run to host memory: what = MCPD_FETCH_*; bytes must equal the size
+ * the plan reports for it (mcpd_fetch_bytes). */
+#define MCPD_FETCH_S1 0        /* int64  [n_buckets][n_active]: sum of G_pj over slots with N*_p = n */
+#define MCPD_FETCH_S2_LO 1     /* uint64 [n_buckets][n_active]: low words of sum of G_pj^2          */
+#define MCPD_FETCH_S2_HI 2     /* uint64 [n_buckets][n_active]: high words                         */
+#define MCPD_FETCH_COUNT 3     /* int64  [n_buckets]: slots per N*_p value                          */
+#define MCPD_FETCH_SLOT_NSTAR 4/* int32  [slots] (record_slots = 1)                                 */
+#define MCPD_FETCH_SLOT_S 5    /* int64  [slots] retained progress units (record_slots = 1)         */
+#define MCPD_FETCH_SLOT_REPS 6 /* int32  [slots] replications started (record_slots = 1)            */
+#define MCPD_FETCH_TRACE_G 7   /* int64  [ceil(slots/stride)][n_active] (trace_stride > 0)          */
+size_t mcpd_fetch_bytes(const mcpd_plan *plan, int what);
+int mcpd_fetch(mcpd_ctx *ctx, const mcpd_plan *plan, int what, void *host_dst, size_t bytes);
+
+/* One call from host arrays to host arrays: plan, run, copy back, destroy the plan.
+ * est, se: [n_clones] in the original clone order (pruned clones get 0 and 0);
+ * active: [n_clones] 1 for retained clones, or NULL.  stats may be NULL.  Synchronous. */
+int mcpd_decode(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
+                const mcpd_params *params, double *est, double *se, int32_t *active,
+                mcpd_stats *stats);
+
+/* Host only (no GPU needed): validate the inputs and build the plan's tables without uploading
+ * them, for inspection and tests.  info as mcpd_plan_info (launch-shape entries 7-11 are 0);
+ * active [n_active] original clone ids; w [n_active] scan weights; alias [n_active] words
+ * (prob | alias << 32); T [81] acceptance thresholds indexed 9 n+ + n-.  Any output may be NULL;
+ * the caller sizes them from a first call with all outputs NULL but info. */
+int mcpd_inspect(const mcpd_design *design, const uint8_t *y, const mcpd_params *params,
+                 int64_t info[16], int32_t *active, double *w, uint64_t *alias, uint64_t *T);
+
+/* Philox4x32-10 blocks computed by the device generator the sampler uses: out[4 i .. 4 i + 3] =
+ * Philox(ctr[4 i .. 4 i + 3], key).  ctr, out: device arrays of 4 n words. */
+int mcpd_philox_device(mcpd_ctx *ctx, const uint32_t *ctr_dev, uint32_t key0, uint32_t key1,
+                       uint32_t *out_dev, int64_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCPD_H */

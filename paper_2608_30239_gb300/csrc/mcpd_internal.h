@@ -1,0 +1,94 @@
+// Private declarations shared by the host table builder, the C ABI and the CUDA kernels.
+#pragma once
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mcpd.h"
+
+namespace mcpd {
+
+constexpr int kRow = 8;              // pool entries per clone row (one 16-byte shared load)
+constexpr int kTSide = kRow + 1;     // acceptance table is kTSide x kTSide, indexed 9 n+ + n-
+constexpr int kMaxClones = 65535;
+constexpr int kMaxPools = 1022;      // pool byte offsets must fit 16 bits
+constexpr int kMaxPoolSize = 255;    // per-pool counts are bytes
+constexpr int64_t kMaxBuckets = 1 << 16;
+
+// Counter slots of the device statistics block.
+enum Counter {
+    kWork = 0, kProgress, kSiteUpdates, kRepsStarted, kRepsRetained, kRepsAborted,
+    kZeroCompletion, kStepLimitHits, kMaxTau, kSumTau, kNumCounters = 16
+};
+
+// Everything the sampler needs, built on the host from (design, y, params).
+struct Tables {
+    int32_t n = 0, m = 0, na = 0, deg_max = 0;
+    int32_t scan = MCPD_SCAN_SCORE;
+    bool coupled = true;
+    std::vector<int32_t> active;      // [na] original index of active clone a, ascending
+    std::vector<uint64_t> alias;      // [na] prob (low 32) | alias index (high 32)
+    std::vector<uint16_t> rows;       // [na * kRow] byte offsets of pool counts | y bit
+    std::vector<uint64_t> T;          // [kTSide * kTSide]
+    std::vector<uint64_t> Tnu;        // [na] or empty
+    std::vector<double> w;            // [na] scan weights
+    // shared-memory layout of one pair (32-bit words, interleaved over the 32 lanes of a warp)
+    int32_t W = 0;                    // bit-set words per chain
+    int32_t Mp = 0;                   // count words (two pools per word, the padding pool included)
+    int32_t wpp = 0;                  // words per pair = 2 W + Mp
+    uint16_t dummy_entry = 0;         // row entry of the padding pool
+    uint32_t dummy_word = 0;          // initial value of the word holding the padding pool
+    int32_t dummy_word_index = 0;
+    // run shape
+    int64_t k = 0, ell = 0, L = 0, burn = 0, length = 0, unit = 1;
+    int64_t P = 0, B = 0, nb = 1, step_limit = 0, slot_offset = 0, trace_stride = 0;
+    uint64_t seed = 0;
+    uint32_t instance = 0;
+    bool record_slots = false;
+};
+
+int build_tables(const mcpd_design *design, const uint8_t *y, const mcpd_params *params,
+                 Tables *out, std::string *err);
+
+// Kernel arguments (plain types only: shared by host and device compilation units).
+struct KParams {
+    const uint64_t *alias;
+    const uint16_t *rows;
+    const uint64_t *T;
+    const uint64_t *Tnu;
+    long long *rep_acc;               // [pairs][na]
+    long long *slot_acc;              // [pairs][na]
+    uint32_t *touched_rep;            // [pairs][W]
+    uint32_t *touched_slot;           // [pairs][W]
+    unsigned long long *S1;           // [nb][na]
+    unsigned long long *S2lo;         // [nb][na]
+    unsigned long long *S2hi;         // [nb][na]
+    unsigned long long *bcount;       // [nb]
+    unsigned long long *counters;     // [kNumCounters]
+    int *error;
+    int32_t *slot_nstar;
+    long long *slot_S;
+    int32_t *slot_reps;
+    long long *trace_G;
+    int32_t na, m, W, Mp, wpp, deg, nb, scan;
+    uint32_t dummy_entry, dummy_word;
+    int32_t dummy_word_index, coupled;
+    long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset, trace_stride;
+    unsigned long long seed;
+    uint32_t instance;
+    int32_t warps;
+    uint32_t smem_tables;             // bytes of staged tables at the start of shared memory
+};
+
+// Launchers (mcpd_kernels.cu).
+int launch_pairs(const KParams &kp, int grid, int block, size_t smem, void *stream);
+int launch_finalize(const unsigned long long *S1, const unsigned long long *S2lo,
+                    const unsigned long long *S2hi, int na, int nb, long long P, long long L,
+                    double *est, double *se, void *stream);
+int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, long long n,
+                  void *stream);
+int pairs_max_smem(int device, size_t *bytes);
+int set_pairs_smem(size_t bytes, int coupled);
+
+}  // namespace mcpd

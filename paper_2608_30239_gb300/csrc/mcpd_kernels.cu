@@ -1,0 +1,413 @@
+// CUDA kernels (sm_103a) for coupled score-weighted Markov chain pool decoding.
+//
+// pairs_kernel: persistent; one block per SM (or several when the pair state is small); every
+// thread owns one logical slot at a time and runs its coupled pairs (Algorithm 3) back to back
+// under the fixed horizon B with slot refill (Algorithm 4).  Per pair, shared memory holds the
+// two chains' clone bit sets and the per-pool positive counts of both chains (one byte each), laid
+// out word-interleaved over the warp's 32 lanes so that the per-step loads of different pairs never
+// share a bank.  The clone->pool rows, the alias table of the scan weights and the acceptance
+// thresholds are staged once per block.  The hot loop is integer-only: a Philox4x32-10 block
+// feeds two steps, the site comes from the alias table, the full conditional from a table lookup
+// indexed by (n+, n-), and the update from a 64-bit integer comparison.  The estimator
+// H_{k:l} is accumulated exactly in integers, only when a site flips (see wprefix below), and
+// slot sums go to N*_p buckets with 64/128-bit integer atomics, so the result does not depend on
+// the schedule.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mcpd_internal.h"
+
+namespace mcpd {
+namespace {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32 S-box with the Weyl
+// key schedule.
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Prefix sums of the per-time weights of the estimator.  Swapping the sums in
+// L H_{k:l} = sum_{r=k}^{l} [X_r + sum_{s>=1} (X_{r+s} - Y_{r+s-1})] gives
+//   G_j = sum_{t=0}^{C} w(t) X_t[j] - sum_{t=0}^{C-1} w(t) Y_t[j],  w(t) = clamp(t - k + 1, 0, L),
+// so a chain whose bit j is 1 on the time interval [s, e] contributes +-(W(e) - W(s-1)) with
+// W(u) = sum_{v<=u} w(v).  Uncoupled (Algorithms 1/2) uses w(t) = 1{b <= t <= b + T - 1}.
+template <bool COUPLED>
+__device__ __forceinline__ long long wprefix(long long u, const KParams &p) {
+    if (COUPLED) {
+        if (u < p.k) return 0;
+        if (u <= p.ell) { const long long a = u - p.k + 1; return a * (a + 1) / 2; }
+        return p.L * (p.L + 1) / 2 + (u - p.ell) * p.L;
+    } else {
+        const long long v = u - p.burn + 1;
+        return v < 0 ? 0 : (v > p.length ? p.length : v);
+    }
+}
+
+__device__ __forceinline__ void bucket_add(const KParams &p, int bkt, int j, long long g) {
+    const size_t idx = static_cast<size_t>(bkt) * p.na + j;
+    atomicAdd(&p.S1[idx], static_cast<unsigned long long>(g));
+    const unsigned long long a = static_cast<unsigned long long>(g < 0 ? -g : g);
+    const unsigned long long lo = a * a, hi = __umul64hi(a, a);
+    const unsigned long long old = atomicAdd(&p.S2lo[idx], lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry) atomicAdd(&p.S2hi[idx], hi + carry);
+}
+
+template <bool COUPLED, bool SYSTEMATIC>
+__global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int na = p.na;
+    uint4 *sRows = reinterpret_cast<uint4 *>(smem);
+    unsigned long long *sAlias = reinterpret_cast<unsigned long long *>(smem + static_cast<size_t>(na) * 16);
+    unsigned long long *sT = sAlias + na;
+    for (int i = threadIdx.x; i < na; i += blockDim.x) {
+        sRows[i] = reinterpret_cast<const uint4 *>(p.rows)[i];
+        sAlias[i] = p.alias[i];
+    }
+    for (int i = threadIdx.x; i < kTSide * kTSide; i += blockDim.x) sT[i] = p.T[i];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *st = reinterpret_cast<uint32_t *>(smem + p.smem_tables) +
+                   static_cast<size_t>(warp) * 32 * p.wpp + lane;   // word w of this pair: st[w * 32]
+    unsigned char *cbase = reinterpret_cast<unsigned char *>(st);
+    __syncthreads();
+
+    const long long gpair = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    long long *racc = p.rep_acc + gpair * na;
+    long long *sacc = p.slot_acc + gpair * na;
+    uint32_t *trep = p.touched_rep + gpair * p.W;
+    uint32_t *tslot = p.touched_slot + gpair * p.W;
+    const uint32_t k0 = static_cast<uint32_t>(p.seed), k1 = static_cast<uint32_t>(p.seed >> 32);
+    const uint32_t W = p.W, nwords = p.wpp;
+    const uint32_t B = static_cast<uint32_t>(p.B), unit = static_cast<uint32_t>(p.unit);
+    const uint32_t ell = static_cast<uint32_t>(p.ell), step_limit = static_cast<uint32_t>(p.step_limit);
+    const int deg = p.deg;
+
+    // slot / replication state
+    bool alive = true;
+    uint32_t slot_local = 0, slot_g = 0, r = 0, t = 0, S = 0, N = 0, tau = 0, D = 0;
+    uint32_t abort_t = 0xFFFFFFFFu, sysI = 0, reps_in_slot = 0;
+    unsigned long long c_prog = 0, c_started = 0, c_retained = 0, c_aborted = 0, c_zero = 0,
+                       c_limit = 0, c_sumtau = 0;
+    uint32_t c_maxtau = 0;
+
+    auto start_rep = [&]() {
+        for (uint32_t w = 0; w < nwords; ++w) st[w * 32] = 0u;
+        st[p.dummy_word_index * 32] = p.dummy_word;
+        if (p.Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0
+            for (int a = 0; a < na; a += 2) {
+                const uint4 b = philox10(make_uint4(static_cast<uint32_t>(a) >> 1, r, slot_g,
+                                                    p.instance | (1u << 24)), k0, k1);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = a + h;
+                    if (c >= na) break;
+                    const unsigned long long u = h ? ((static_cast<unsigned long long>(b.z) << 32) | b.w)
+                                                   : ((static_cast<unsigned long long>(b.x) << 32) | b.y);
+                    if (u < p.Tnu[c]) {
+                        const uint32_t q = c >> 5, bit = 1u << (c & 31);
+                        st[(2 * q) * 32] |= bit;
+                        if (COUPLED) st[(2 * q + 1) * 32] |= bit;
+                        const uint4 row = sRows[c];
+                        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
+                                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
+#pragma unroll
+                        for (int l = 0; l < kRow; ++l) {
+                            if (l >= deg || ent[l] == p.dummy_entry) continue;
+                            uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
+                            *cnt = static_cast<uint16_t>(*cnt + (COUPLED ? 0x0101u : 0x0001u));
+                        }
+                    }
+                }
+            }
+        }
+        t = 0; D = 0; tau = 0; sysI = 0;
+        abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
+        ++c_started;
+        ++reps_in_slot;
+    };
+
+    auto start_slot = [&]() {
+        const unsigned long long s = atomicAdd(&p.counters[kWork], 1ull);
+        if (s >= static_cast<unsigned long long>(p.P)) { alive = false; return; }
+        slot_local = static_cast<uint32_t>(s);
+        slot_g = static_cast<uint32_t>(p.slot_offset + static_cast<long long>(s));
+        S = 0; N = 0; r = 0; reps_in_slot = 0;
+        start_rep();
+    };
+
+    auto clear_rep_acc = [&]() {
+        for (uint32_t q = 0; q < W; ++q) {
+            uint32_t tw = trep[q];
+            if (!tw) continue;
+            while (tw) { const int b = __ffs(tw) - 1; tw &= tw - 1; racc[q * 32 + b] = 0; }
+            trep[q] = 0;
+        }
+    };
+
+    auto end_slot = [&](bool valid) {
+        const int bkt = static_cast<int>(N) - 1;
+        long long *tr = nullptr;
+        if (valid && p.trace_stride > 0 && (slot_local % p.trace_stride) == 0)
+            tr = p.trace_G + (static_cast<long long>(slot_local) / p.trace_stride) * na;
+        for (uint32_t q = 0; q < W; ++q) {
+            uint32_t tw = tslot[q];
+            if (!tw) continue;
+            while (tw) {
+                const int b = __ffs(tw) - 1; tw &= tw - 1;
+                const int j = q * 32 + b;
+                const long long g = sacc[j];
+                sacc[j] = 0;
+                if (valid && g != 0) {
+                    bucket_add(p, bkt, j, g);
+                    if (tr) tr[j] = g;
+                }
+            }
+            tslot[q] = 0;
+        }
+        if (valid) atomicAdd(&p.bcount[bkt], 1ull);
+        if (p.slot_nstar) {
+            p.slot_nstar[slot_local] = valid ? static_cast<int32_t>(N) : 0;
+            p.slot_S[slot_local] = S;
+            p.slot_reps[slot_local] = static_cast<int32_t>(reps_in_slot);
+        }
+        start_slot();
+    };
+
+    // Replication completed at C = t: close the open intervals, move the replication's sums into
+    // the slot's sums (every completed replication is retained: a later one that could not finish
+    // within B is aborted before it completes), then refill or end the slot.
+    auto complete = [&]() {
+        const uint32_t C = t;
+        c_prog += C;
+        if (COUPLED) { c_sumtau += tau; c_maxtau = max(c_maxtau, tau); }
+        const long long wX = wprefix<COUPLED>(C, p);
+        const long long wY = COUPLED ? wprefix<COUPLED>(static_cast<long long>(C) - 1, p) : 0;
+        for (uint32_t q = 0; q < W; ++q) {
+            const uint32_t xw = st[(2 * q) * 32];
+            const uint32_t yw = COUPLED ? st[(2 * q + 1) * 32] : 0u;
+            const uint32_t tw = trep[q];
+            uint32_t mask = tw | xw | yw, moved = 0;
+            while (mask) {
+                const int b = __ffs(mask) - 1;
+                const uint32_t bit = 1u << b;
+                mask &= mask - 1;
+                const int j = q * 32 + b;
+                long long v = 0;
+                if (tw & bit) { v = racc[j]; racc[j] = 0; }
+                if (xw & bit) v += wX;
+                if (yw & bit) v -= wY;
+                if (v != 0) { sacc[j] += v; moved |= bit; }
+            }
+            if (tw) trep[q] = 0;
+            if (moved) tslot[q] |= moved;
+        }
+        S += C;
+        N += 1;
+        ++c_retained;
+        if (S > B) ++c_zero;                 // only a slot's first replication can end beyond B
+        if (S < B && B - S >= unit) { ++r; start_rep(); }
+        else end_slot(true);
+    };
+
+    auto abort_rep = [&]() {                  // doomed: S_p(r) would exceed B; discard it
+        c_prog += t;
+        ++c_aborted;
+        clear_rep_acc();
+        end_slot(true);
+    };
+
+    auto limit_hit = [&]() {
+        c_prog += t;
+        ++c_limit;
+        atomicExch(p.error, 1);
+        clear_rep_acc();
+        end_slot(false);
+    };
+
+    // One step at time t with the draw words (ws: site, wu: high half of the uniform).
+    auto step = [&](uint32_t ws, uint32_t wu) -> bool {
+        uint32_t I;
+        if (SYSTEMATIC) {
+            I = sysI;
+        } else {
+            const unsigned long long prod = static_cast<unsigned long long>(ws) * static_cast<uint32_t>(na);
+            const uint32_t col = static_cast<uint32_t>(prod >> 32), coin = static_cast<uint32_t>(prod);
+            const unsigned long long e = sAlias[col];
+            I = coin < static_cast<uint32_t>(e) ? col : static_cast<uint32_t>(e >> 32);
+        }
+        const uint4 row = sRows[I];
+        const uint32_t q = I >> 5, bit = 1u << (I & 31);
+        uint32_t *px = st + (2 * q) * 32;
+        const uint32_t xw = px[0];
+        const uint32_t yw = COUPLED ? px[32] : 0u;
+        const uint32_t xI = (xw & bit) ? 1u : 0u, yI = (yw & bit) ? 1u : 0u;
+        const uint32_t xy = xI | (yI << 8);
+        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
+                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
+        uint32_t ix = 0, iy = 0;
+#pragma unroll
+        for (int l = 0; l < kRow; ++l) {
+            if (l < deg) {
+                const uint32_t e = ent[l];
+                const uint32_t v = *reinterpret_cast<const uint16_t *>(cbase + (e & ~1u));
+                const uint32_t code = (e & 1u) ? 9u : 1u;   // 9 n+ + n- indexes the table
+                const uint32_t d = v ^ xy;
+                if ((d & 0xFFu) == 0) ix += code;          // c_j - x_I = 0: pool j decides
+                if (COUPLED && (d & 0xFF00u) == 0) iy += code;
+            }
+        }
+        const unsigned long long TX = sT[ix];
+        const unsigned long long TY = COUPLED ? sT[iy] : 0ull;
+        const uint32_t thx = static_cast<uint32_t>(TX >> 32), thy = static_cast<uint32_t>(TY >> 32);
+        uint32_t nX = wu < thx ? 1u : 0u, nY = wu < thy ? 1u : 0u;
+        if (wu == thx || (COUPLED && wu == thy)) {   // the low half of U decides (p ~ 2^-32)
+            const uint32_t lo = philox10(make_uint4(t, r, slot_g, p.instance | (2u << 24)), k0, k1).x;
+            if (wu == thx) nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
+            if (COUPLED && wu == thy) nY = lo < static_cast<uint32_t>(TY) ? 1u : 0u;
+        }
+        const bool prelag = COUPLED && t == 0;       // X_1 = Phi(X_0, U_0): X only
+        if (!COUPLED || prelag) nY = yI;
+        const uint32_t fx = nX ^ xI, fy = nY ^ yI;
+        if (fx | fy) {
+            if (fx) px[0] = xw ^ bit;
+            if (fy) px[32] = yw ^ bit;
+            const uint32_t delta = (fx ? (nX ? 0x0001u : 0xFFFFu) : 0u) + (fy ? (nY ? 0x0100u : 0xFF00u) : 0u);
+#pragma unroll
+            for (int l = 0; l < kRow; ++l) {
+                if (l >= deg || ent[l] == p.dummy_entry) continue;
+                uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
+                *cnt = static_cast<uint16_t>(*cnt + delta);
+            }
+            long long ev = 0;
+            if (fx) { const long long w = wprefix<COUPLED>(t, p); ev += nX ? -w : w; }           // X_{t+1}
+            if (fy) { const long long w = wprefix<COUPLED>(static_cast<long long>(t) - 1, p); ev += nY ? w : -w; }  // Y_t
+            if (ev != 0) { racc[I] += ev; trep[q] |= bit; }
+            if (COUPLED) D = D + (nX ^ nY) - (xI ^ yI);
+        }
+        ++t;
+        if (SYSTEMATIC) { ++sysI; if (sysI == static_cast<uint32_t>(na)) sysI = 0; }
+        if (COUPLED) {
+            if (D == 0) {
+                if (tau == 0) tau = t;               // tau_1 = first t >= 1 with X_t = Y_{t-1}
+                if (t >= ell) { complete(); return true; }
+            }
+            if (t >= abort_t) { abort_rep(); return true; }
+        } else if (t >= unit) {
+            complete();
+            return true;
+        }
+        if (t >= step_limit) { limit_hit(); return true; }
+        return false;
+    };
+
+    start_slot();
+    while (alive) {
+        // one Philox block per pair of steps: words (0,1) at even t, (2,3) at odd t
+        const uint4 blk = philox10(make_uint4(t >> 1, r, slot_g, p.instance), k0, k1);
+        if (!step(blk.x, blk.y)) step(blk.z, blk.w);
+    }
+
+    if (c_prog) atomicAdd(&p.counters[kProgress], c_prog);
+    if (c_started) atomicAdd(&p.counters[kRepsStarted], c_started);
+    if (c_retained) atomicAdd(&p.counters[kRepsRetained], c_retained);
+    if (c_aborted) atomicAdd(&p.counters[kRepsAborted], c_aborted);
+    if (c_zero) atomicAdd(&p.counters[kZeroCompletion], c_zero);
+    if (c_limit) atomicAdd(&p.counters[kStepLimitHits], c_limit);
+    if (c_sumtau) atomicAdd(&p.counters[kSumTau], c_sumtau);
+    if (c_maxtau) atomicMax(&p.counters[kMaxTau], static_cast<unsigned long long>(c_maxtau));
+}
+
+// theta_j = (sum_{n ascending} S1[n][j] / n) / (P L);  Q_j = (sum_n S2[n][j] / n^2) / L^2;
+// se_j = sqrt(max(0, (Q_j - (P theta_j) theta_j) / (P (P - 1)))).  Every operation is an
+// explicitly rounded IEEE double operation, in this order.
+__global__ void finalize_kernel(const unsigned long long *S1, const unsigned long long *S2lo,
+                                const unsigned long long *S2hi, int na, int nb, long long P,
+                                long long L, double *est, double *se) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= na) return;
+    const double dP = static_cast<double>(P), dL = static_cast<double>(L);
+    double s1 = 0.0, s2 = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        const size_t idx = static_cast<size_t>(b) * na + j;
+        const double n = static_cast<double>(b + 1);
+        s1 = __dadd_rn(s1, __ddiv_rn(static_cast<double>(static_cast<long long>(S1[idx])), n));
+        const double sq = __dadd_rn(__dmul_rn(static_cast<double>(S2hi[idx]), 18446744073709551616.0),
+                                    static_cast<double>(S2lo[idx]));
+        s2 = __dadd_rn(s2, __ddiv_rn(sq, __dmul_rn(n, n)));
+    }
+    const double th = __ddiv_rn(s1, __dmul_rn(dP, dL));
+    est[j] = th;
+    if (P < 2) { se[j] = __longlong_as_double(0x7FF8000000000000LL); return; }
+    const double Q = __ddiv_rn(s2, __dmul_rn(dL, dL));
+    const double var = __ddiv_rn(__dsub_rn(Q, __dmul_rn(__dmul_rn(dP, th), th)),
+                                 __dmul_rn(dP, __dsub_rn(dP, 1.0)));
+    se[j] = var > 0.0 ? __dsqrt_rn(var) : 0.0;
+}
+
+__global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, long long n) {
+    const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+    const uint4 o = philox10(c, k0, k1);
+    out[4 * i] = o.x; out[4 * i + 1] = o.y; out[4 * i + 2] = o.z; out[4 * i + 3] = o.w;
+}
+
+using PairsFn = void (*)(const KParams);
+
+PairsFn pick(int coupled, int scan) {
+    if (coupled) return pairs_kernel<true, false>;
+    return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true> : pairs_kernel<false, false>;
+}
+
+}  // namespace
+
+int set_pairs_smem(size_t bytes, int coupled) {
+    const PairsFn fns[3] = {pairs_kernel<true, false>, pairs_kernel<false, true>, pairs_kernel<false, false>};
+    (void)coupled;
+    for (PairsFn f : fns)
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) != cudaSuccess)
+            return MCPD_ECUDA;
+    return MCPD_OK;
+}
+
+int pairs_max_smem(int device, size_t *bytes) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
+        return MCPD_ECUDA;
+    *bytes = static_cast<size_t>(v);
+    return MCPD_OK;
+}
+
+int launch_pairs(const KParams &kp, int grid, int block, size_t smem, void *stream) {
+    PairsFn f = pick(kp.coupled, kp.scan);
+    f<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(kp);
+    return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
+}
+
+int launch_finalize(const unsigned long long *S1, const unsigned long long *S2lo,
+                    const unsigned long long *S2hi, int na, int nb, long long P, long long L,
+                    double *est, double *se, void *stream) {
+    finalize_kernel<<<(na + 127) / 128, 128, 0, static_cast<cudaStream_t>(stream)>>>(S1, S2lo, S2hi, na, nb, P, L, est, se);
+    return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
+}
+
+int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, long long n, void *stream) {
+    if (n <= 0) return MCPD_OK;
+    philox_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(ctr, k0, k1, out, n);
+    return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
+}
+
+int pairs_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(coupled, scan), block, smem) == cudaSuccess
+               ? MCPD_OK : MCPD_ECUDA;
+}
+
+}  // namespace mcpd

@@ -1,0 +1,147 @@
+"""The C-ABI library without a GPU: it builds, loads, exports what include/mcpd.h declares, its
+struct layouts match the C compiler's, its host-built tables equal the oracle's, and it rejects
+invalid inputs."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+from paper_2608_30239_gb300 import build as lib_build
+from paper_2608_30239_gb300 import mcpd
+
+
+@pytest.fixture(scope="module")
+def L():
+    lib_build.build()
+    return mcpd.lib()
+
+
+def test_library_exports_every_declared_function(L):
+    names = mcpd.header_functions()
+    assert "mcpd_decode" in names and "mcpd_run_async" in names
+    for name in names:
+        assert hasattr(L, name), name
+    out = subprocess.check_output(["nm", "-D", "--defined-only", lib_build.LIB]).decode()
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(names) <= exported
+
+
+def test_struct_layout_matches_c(tmp_path):
+    """offsetof/sizeof from gcc on include/mcpd.h equal the ctypes mirrors of the binding."""
+    fields = {"mcpd_params": [f for f, _ in mcpd.mcpd_params._fields_],
+              "mcpd_stats": [f for f, _ in mcpd.mcpd_stats._fields_],
+              "mcpd_design": [f for f, _ in mcpd.mcpd_design._fields_]}
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "mcpd.h"', "int main(void){"]
+    for s, fs in fields.items():
+        src.append(f'printf("{s} %zu\\n", sizeof({s}));')
+        for f in fs:
+            src.append(f'printf("{s}.{f} %zu\\n", offsetof({s}, {f}));')
+    src.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", lib_build.INCLUDE, str(c), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for s, fs in fields.items():
+        cls = getattr(mcpd, s)
+        assert int(got[s]) == ctypes.sizeof(cls)
+        for f in fs:
+            assert int(got[f"{s}.{f}"]) == getattr(cls, f).offset, (s, f)
+
+
+CASES = {
+    "tiny": (lambda: synth.tiny_config(1), {}),
+    "library": (lambda: synth.paper_shaped_config(), {}),
+    "high-noise": (lambda: synth.high_noise_config(), {}),
+    "pruned": (lambda: synth.high_noise_config(), {"n_active": 333}),
+    "uniform": (lambda: synth.tiny_config(2), {"scan": mcpd.MCPD_SCAN_UNIFORM}),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_host_tables_equal_oracle_tables(L, oracle_lib, case):
+    """Same written spec, separate code: weights, alias words and thresholds agree bit for bit."""
+    make, kw = CASES[case]
+    inst = make()
+    lib_t = mcpd.mcpd_inspect(inst, slots=16, horizon=100, **kw)
+    M = oracle_lib.Model(inst, n_active=kw.get("n_active", 0), scan=kw.get("scan", 0))
+    ref = M.tables()
+    assert np.array_equal(lib_t["active"], ref["active"])
+    assert np.array_equal(lib_t["w"].view(np.uint64), ref["w"].view(np.uint64))
+    assert np.array_equal(lib_t["alias"] & np.uint64(0xFFFFFFFF), ref["prob"].astype(np.uint64))
+    assert np.array_equal(lib_t["alias"] >> np.uint64(32), ref["alias"].astype(np.uint64))
+    side = M.deg_max + 1
+    assert np.array_equal(lib_t["T"][:side, :side], ref["T"])
+
+
+def test_custom_weights_tables(L, oracle_lib):
+    inst = synth.tiny_config(5)
+    w = np.linspace(1.0, 2.0, inst.n)
+    lib_t = mcpd.mcpd_inspect(inst, slots=4, scan=mcpd.MCPD_SCAN_CUSTOM, scan_weights=w)
+    ref = oracle_lib.Model(inst, scan=oracle_lib.SCAN_CUSTOM, custom_w=w).tables()
+    assert np.array_equal(lib_t["alias"] & np.uint64(0xFFFFFFFF), ref["prob"].astype(np.uint64))
+    assert np.array_equal(lib_t["alias"] >> np.uint64(32), ref["alias"].astype(np.uint64))
+
+
+def test_window_and_horizon_defaults(L, oracle_lib):
+    inst = synth.high_noise_config()
+    t = mcpd.mcpd_inspect(inst, slots=524288, budget_site_updates=4e10)
+    info = t["info"]
+    k, ell = oracle_lib.window_defaults(1298, 1)
+    assert (int(info[3]), int(info[4]), int(info[5])) == (k, ell, ell - k + 1) == (131, 1298, 1168)
+    assert int(info[2]) == synth.budget_horizon(4e10, 524288) == 38146
+    assert int(info[1]) == 38146 // 1298
+    u = mcpd.mcpd_inspect(inst, slots=1000, coupled=False, scan=mcpd.MCPD_SCAN_SYSTEMATIC,
+                          budget_site_updates=1e8)
+    assert int(u["info"][3]) == 130 and int(u["info"][5]) == 1298 - 130
+    assert int(u["info"][2]) == 100000
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(fp=0.0), mcpd.MCPD_EINVAL),
+    (dict(fn=1.0), mcpd.MCPD_EINVAL),
+    (dict(prior_q=1.5), mcpd.MCPD_EINVAL),
+    (dict(k=5, ell=4), mcpd.MCPD_EINVAL),
+    (dict(scan=mcpd.MCPD_SCAN_SYSTEMATIC), mcpd.MCPD_EINVAL),
+    (dict(scan=7), mcpd.MCPD_EINVAL),
+    (dict(slots=0), mcpd.MCPD_EINVAL),
+    (dict(instance_id=1 << 24), mcpd.MCPD_EINVAL),
+    (dict(coupled=False, burn=0, length=1), mcpd.MCPD_EINVAL),
+    (dict(horizon=10 ** 6, ell=1, k=0), mcpd.MCPD_ETOO_LARGE),
+])
+def test_invalid_parameters_rejected(L, kw, code):
+    inst = synth.tiny_config(1)
+    base = dict(slots=8, horizon=100)
+    base.update(kw)
+    with pytest.raises(mcpd.McpdError) as ei:
+        mcpd.mcpd_inspect(inst, **base)
+    assert ei.value.code == code
+
+
+def test_invalid_designs_rejected(L):
+    inst = synth.tiny_config(1)
+    bad = synth.Instance(**{**inst.__dict__})
+    bad.clone_pools = inst.clone_pools.copy()
+    bad.clone_pools[0], bad.clone_pools[1] = bad.clone_pools[1], bad.clone_pools[0]   # unsorted row
+    with pytest.raises(mcpd.McpdError) as ei:
+        mcpd.mcpd_inspect(bad, slots=4)
+    assert ei.value.code == mcpd.MCPD_EINVAL
+    wide = synth.make_instance(40, 12, 9, 2, 0.1, 0.1, 0.05, 3, 4)                        # 9 pools
+    with pytest.raises(mcpd.McpdError) as ei:
+        mcpd.mcpd_inspect(wide, slots=4)
+    assert ei.value.code == mcpd.MCPD_ETOO_LARGE
+    y2 = synth.Instance(**{**inst.__dict__})
+    y2.y = inst.y.copy()
+    y2.y[0] = 2
+    with pytest.raises(mcpd.McpdError):
+        mcpd.mcpd_inspect(y2, slots=4)
+
+
+def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(mcpd, "_lib", None)
+    monkeypatch.setattr(lib_build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(ImportError):
+        mcpd.lib()

@@ -1,0 +1,240 @@
+"""GPU path vs the CPU oracle, through the C ABI (needs a GB300).
+
+Integer outputs (N*_p buckets of sum G and sum G^2, per-slot N*_p, retained cost, replication
+counts, traced G vectors) must be bit-exact; the finalized doubles too, since both sides evaluate
+the same correctly rounded expression on the same integers (the bound north of that is 1e-12
+relative, asserted as equality here)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2608_30239_gb300 import build, mcpd
+    build.build()
+    c = mcpd.Context(0)
+    yield c
+    c.close()
+
+
+def _gpu_run(ctx, inst, **kw):
+    import torch
+    from paper_2608_30239_gb300 import mcpd
+    plan = mcpd.Plan(ctx, inst, **kw)
+    est = torch.empty(plan.n_active, dtype=torch.float64, device="cuda:0")
+    se = torch.empty_like(est)
+    plan.run_async(est, se)
+    stats = plan.collect(allow_step_limit=True)
+    out = dict(plan=plan, est=est.cpu().numpy(), se=se.cpu().numpy(), stats=stats)
+    out.update(plan.buckets())
+    if kw.get("record_slots"):
+        out["slot_nstar"] = plan.fetch(mcpd.MCPD_FETCH_SLOT_NSTAR)
+        out["slot_S"] = plan.fetch(mcpd.MCPD_FETCH_SLOT_S)
+        out["slot_reps"] = plan.fetch(mcpd.MCPD_FETCH_SLOT_REPS)
+    if kw.get("trace_stride"):
+        out["trace_G"] = plan.fetch(mcpd.MCPD_FETCH_TRACE_G)
+    return out
+
+
+def _oracle_run(inst, P, k, ell, B, seed, coupled=True, burn=0, length=1, n_active=0,
+                scan=oracle.SCAN_SCORE, custom_w=None, init=None, slot_offset=0, slot_G=False):
+    M = oracle.Model(inst, n_active=n_active, scan=scan, custom_w=custom_w, init_marginals=init)
+    run = (oracle.coupled_run(k, ell, B, seed, slot_offset=slot_offset) if coupled
+           else oracle.uncoupled_run(burn, length, B, seed, slot_offset=slot_offset))
+    res = M.run_slots(run, 0, P, THREADS, per_slot=True, slot_G=slot_G)
+    L = (ell - k + 1) if coupled else length
+    res["est"], res["se"] = M.finalize(res, P, L)
+    return res
+
+
+def _assert_same(g, o, per_slot=True):
+    for key in ("S1", "S2_lo", "S2_hi", "count"):
+        assert np.array_equal(g[key], o[key]), key
+    if per_slot:
+        assert np.array_equal(g["slot_nstar"], o["slot_nstar"])
+        assert np.array_equal(g["slot_S"], o["slot_S"])
+    assert np.array_equal(g["est"], o["est"])
+    assert np.array_equal(g["se"], o["se"], equal_nan=True)
+
+
+def test_device_philox_matches_oracle(ctx):
+    import torch
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    d_ctr = torch.from_numpy(ctr.view(np.int32).copy()).cuda()
+    d_out = torch.empty_like(d_ctr)
+    key = (0xA4093822, 0x299F31D0)
+    ctx.philox(d_ctr, key[0], key[1], d_out, len(ctr))
+    got = d_out.cpu().numpy().view(np.uint32)
+    for i in range(0, len(ctr), 97):
+        assert np.array_equal(got[i], oracle.philox(ctr[i], key))
+
+
+@pytest.mark.parametrize("k,ell", [(3, 20), (0, 0), (0, 1), (20, 20)])
+def test_tiny_one_replication_per_slot(ctx, k, ell):
+    """20 clones x 8 pools, 4096 pairs run to meeting (B = 0: every slot keeps its first pair)."""
+    inst = synth.tiny_config(1)
+    P = 4096
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=0, seed=77, record_slots=True)
+    o = _oracle_run(inst, P, k, ell, 0, 77)
+    _assert_same(g, o)
+    assert g["stats"]["reps_started"] == P and g["stats"]["zero_completion_slots"] == P
+
+
+@pytest.mark.parametrize("B", [0, 25, 60, 400])
+def test_tiny_refill(ctx, B):
+    inst = synth.tiny_config(2)
+    P = 3001
+    g = _gpu_run(ctx, inst, slots=P, k=3, ell=20, horizon=B, seed=5, record_slots=True,
+                 trace_stride=1)
+    o = _oracle_run(inst, P, 3, 20, B, 5, slot_G=True)
+    _assert_same(g, o)
+    assert np.array_equal(g["trace_G"], o["slot_G"])
+
+
+def test_medium_design_refill_ragged(ctx):
+    """400 clones x 31 pools (k = 5): several blocks, a ragged last wave, per-slot G vectors."""
+    inst = synth.make_instance(400, 31, 5, 3, 0.05, 0.1, 3 / 400, 41, 42)
+    P = 7777
+    k, ell = oracle.window_defaults(400, 1)
+    B = 5 * ell + 17
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=2024, record_slots=True,
+                 trace_stride=7)
+    o = _oracle_run(inst, P, k, ell, B, 2024, slot_G=True)
+    _assert_same(g, o)
+    assert np.array_equal(g["trace_G"], o["slot_G"][::7])
+
+
+def test_bernoulli_initial_state(ctx):
+    inst = synth.tiny_config(3)
+    rng = np.random.default_rng(3)
+    nu = rng.random(inst.n)
+    nu[0], nu[1], nu[2] = 0.0, 1.0, 0.5
+    P = 2000
+    g = _gpu_run(ctx, inst, slots=P, k=2, ell=15, horizon=70, seed=9, init_marginals=nu,
+                 record_slots=True)
+    o = _oracle_run(inst, P, 2, 15, 70, 9, init=nu)
+    _assert_same(g, o)
+
+
+@pytest.mark.parametrize("scan", ["score", "uniform", "systematic"])
+def test_uncoupled_comparators(ctx, scan):
+    from paper_2608_30239_gb300 import mcpd
+    inst = synth.make_instance(120, 12, 4, 2, 0.05, 0.1, 2 / 120, 7, 8)
+    code = {"score": 0, "uniform": 1, "systematic": 2}[scan]
+    P = 1500
+    g = _gpu_run(ctx, inst, slots=P, coupled=False, scan=code, burn=12, length=108, horizon=600,
+                 seed=31, record_slots=True)
+    o = _oracle_run(inst, P, 0, 0, 600, 31, coupled=False, burn=12, length=108, scan=code)
+    _assert_same(g, o)
+    assert g["stats"]["site_updates"] == P * (600 // 119) * 119
+    _ = mcpd
+
+
+def test_custom_weights_and_pruning(ctx):
+    inst = synth.high_noise_config()
+    P = 600
+    na = 333
+    w = np.linspace(1.0, 3.0, na)
+    k, ell = oracle.window_defaults(na, 1)
+    g = _gpu_run(ctx, inst, slots=P, n_active=na, scan=3, scan_weights=w, k=k, ell=ell,
+                 horizon=3 * ell, seed=4, record_slots=True)
+    o = _oracle_run(inst, P, k, ell, 3 * ell, 4, n_active=na, scan=oracle.SCAN_CUSTOM, custom_w=w)
+    _assert_same(g, o)
+
+
+def test_decode_host_api_matches_plan(ctx):
+    """mcpd_decode (host arrays, original clone order, pruned clones 0) equals the plan path."""
+    inst = synth.high_noise_config()
+    kw = dict(slots=512, n_active=333, horizon=2000, seed=11)
+    d = ctx.decode(inst, **kw)
+    g = _gpu_run(ctx, inst, **kw)
+    act = g["plan"].active
+    assert np.array_equal(np.flatnonzero(d["active"]), act)
+    assert np.array_equal(d["est"][act], g["est"])
+    assert np.array_equal(d["se"][act], g["se"])
+    pruned = np.setdiff1d(np.arange(inst.n), act)
+    assert np.all(d["est"][pruned] == 0) and np.all(d["se"][pruned] == 0)
+
+
+def test_step_limit_reports_error_and_context_survives(ctx):
+    from paper_2608_30239_gb300 import mcpd
+    inst = synth.tiny_config(1)
+    g = _gpu_run(ctx, inst, slots=256, k=3, ell=20, horizon=0, seed=77, step_limit=25)
+    assert g["stats"]["status"] == mcpd.MCPD_ESTEP_LIMIT
+    assert g["stats"]["step_limit_hits"] > 0
+    again = _gpu_run(ctx, inst, slots=256, k=3, ell=20, horizon=0, seed=77)
+    assert again["stats"]["status"] == mcpd.MCPD_OK
+
+
+# -------------------------------------------------------------------------------------------
+# Full size: the 1298 x 97 high-noise configuration with 524288 slots and a 4e10 site-update
+# budget, in the launch configuration the bench times.  Sampled slots are recomputed one by one.
+P_FULL = 524288
+BUDGET = 4e10
+
+
+@pytest.fixture(scope="module")
+def full_run(ctx):
+    inst = synth.high_noise_config()
+    stride = P_FULL // 12 + 1
+    g = _gpu_run(ctx, inst, slots=P_FULL, budget_site_updates=BUDGET, seed=20260,
+                 record_slots=True, trace_stride=stride)
+    return inst, stride, g
+
+
+def test_full_size_sampled_slots_bit_exact(full_run):
+    inst, stride, g = full_run
+    M = oracle.Model(inst)
+    k, ell = oracle.window_defaults(inst.n, 1)
+    B = synth.budget_horizon(BUDGET, P_FULL)
+    for idx, p in enumerate(range(0, P_FULL, stride)):
+        run = oracle.coupled_run(k, ell, B, 20260, slot_offset=p)
+        r = M.run_slots(run, 0, 1, 1, per_slot=True, slot_G=True)
+        assert g["slot_nstar"][p] == r["slot_nstar"][0]
+        assert g["slot_S"][p] == r["slot_S"][0]
+        assert np.array_equal(g["trace_G"][idx], r["slot_G"][0]), p
+
+
+def test_full_size_properties(full_run):
+    inst, stride, g = full_run
+    st = g["stats"]
+    assert st["status"] == 0
+    assert int(g["count"].sum()) == P_FULL
+    assert np.array_equal(np.bincount(g["slot_nstar"], minlength=len(g["count"]) + 1)[1:], g["count"])
+    assert st["site_updates"] <= 2 * st["progress_units"]
+    assert np.all(np.isfinite(g["est"])) and np.all(g["se"] > 0)
+    # the bucketed integer sums reproduce the per-slot bookkeeping
+    B = synth.budget_horizon(BUDGET, P_FULL)
+    assert np.all(g["slot_S"][g["slot_nstar"] > 1] <= B)
+    assert st["reps_retained"] == int(g["slot_nstar"].sum())
+
+
+def test_full_size_partition_and_determinism(ctx, full_run):
+    """Two launches over slot halves (global ids via slot_offset) sum to the one-launch buckets, and
+    a rerun is bit-identical: integer sums do not depend on the schedule."""
+    inst, stride, g = full_run
+    half = P_FULL // 2
+    a = _gpu_run(ctx, inst, slots=half, horizon=synth.budget_horizon(BUDGET, P_FULL), seed=20260)
+    b = _gpu_run(ctx, inst, slots=half, horizon=synth.budget_horizon(BUDGET, P_FULL), seed=20260,
+                 slot_offset=half)
+    assert np.array_equal(a["S1"] + b["S1"], g["S1"])
+    lo = a["S2_lo"] + b["S2_lo"]
+    carry = (lo < a["S2_lo"]).astype(np.uint64)
+    assert np.array_equal(lo, g["S2_lo"])
+    assert np.array_equal(a["S2_hi"] + b["S2_hi"] + carry, g["S2_hi"])
+    again = _gpu_run(ctx, inst, slots=P_FULL, budget_site_updates=BUDGET, seed=20260)
+    assert np.array_equal(again["S1"], g["S1"])
+    assert np.array_equal(again["est"], g["est"])
