@@ -176,6 +176,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slots", type=int, default=SLOTS,
+                    help="slots per GPU; the budget scales with it so the horizon B stays 38146 "
+                         "(smaller cases are for profiling captures)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -201,9 +204,11 @@ def main():
     lib_build.build()
 
     inst = synth.high_noise_config()
-    offset = rank * SLOTS
+    slots = args.slots
+    budget = BUDGET * slots / SLOTS
+    offset = rank * slots
     ctx = mcpd.Context(device)
-    plan = mcpd.Plan(ctx, inst, slots=SLOTS, budget_site_updates=BUDGET, seed=SEED,
+    plan = mcpd.Plan(ctx, inst, slots=slots, budget_site_updates=budget, seed=SEED,
                      slot_offset=offset)
     est = torch.empty(plan.n_active, dtype=torch.float64, device=f"cuda:{device}")
     se = torch.empty_like(est)
@@ -252,7 +257,7 @@ def main():
     for i in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        out = ctx.decode(inst, slots=SLOTS, budget_site_updates=BUDGET, seed=SEED, slot_offset=offset)
+        out = ctx.decode(inst, slots=slots, budget_site_updates=budget, seed=SEED, slot_offset=offset)
         e2e_times.append(time.perf_counter() - t0)
         assert out["status"] == 0
     na = plan.n_active
@@ -278,6 +283,7 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic",
             "config": workload_config({"parallelism": f"slot shards x{world}",
+                                       "slots_per_gpu": slots, "budget_site_updates_per_gpu": budget,
                                        "progress_units_per_step": pu_step,
                                        "site_updates_per_step": su_step,
                                        "replications_per_step": stats[-1]["reps_retained"],
