@@ -77,6 +77,9 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     uint32_t *st = reinterpret_cast<uint32_t *>(smem + p.smem_tables) +
                    static_cast<size_t>(warp) * 32 * p.wpp + lane;   // word w of this pair: st[w * 32]
     unsigned char *cbase = reinterpret_cast<unsigned char *>(st);
+    // The pair's state starts empty, and every replication leaves it empty again.
+    for (int w = 0; w < p.wpp; ++w) st[w * 32] = 0u;
+    st[p.dummy_word_index * 32] = p.dummy_word;
     __syncthreads();
 
     const long long gpair = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -85,22 +88,41 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     uint32_t *trep = p.touched_rep + gpair * p.W;
     uint32_t *tslot = p.touched_slot + gpair * p.W;
     const uint32_t k0 = static_cast<uint32_t>(p.seed), k1 = static_cast<uint32_t>(p.seed >> 32);
-    const uint32_t W = p.W, nwords = p.wpp;
+    const uint32_t W = p.W;
     const uint32_t B = static_cast<uint32_t>(p.B), unit = static_cast<uint32_t>(p.unit);
     const uint32_t ell = static_cast<uint32_t>(p.ell), step_limit = static_cast<uint32_t>(p.step_limit);
     const int deg = p.deg;
+    // Words that may hold a set bit or a touched clone are tracked in 64-bit register masks; one mask
+    // bit covers 2^gshift consecutive words.
+    uint32_t gshift = 0;
+    while (((W + (1u << gshift) - 1) >> gshift) > 64) ++gshift;
 
-    // slot / replication state
     bool alive = true;
     uint32_t slot_local = 0, slot_g = 0, r = 0, t = 0, S = 0, N = 0, tau = 0, D = 0;
     uint32_t abort_t = 0xFFFFFFFFu, sysI = 0, reps_in_slot = 0;
+    unsigned long long rep_words = 0, slot_words = 0;
     unsigned long long c_prog = 0, c_started = 0, c_retained = 0, c_aborted = 0, c_zero = 0,
                        c_limit = 0, c_sumtau = 0;
     uint32_t c_maxtau = 0;
 
+    // Add delta (mod 2^16; X count in the low byte, Y count in the high byte) to every pool of c.
+    auto bump_counts = [&](uint32_t c, uint32_t delta) {
+        const uint4 row = sRows[c];
+        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
+                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
+#pragma unroll
+        for (int l = 0; l < kRow; ++l) {
+            if (l >= deg || ent[l] == p.dummy_entry) continue;
+            uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
+            *cnt = static_cast<uint16_t>(*cnt + delta);
+        }
+    };
+
     auto start_rep = [&]() {
-        for (uint32_t w = 0; w < nwords; ++w) st[w * 32] = 0u;
-        st[p.dummy_word_index * 32] = p.dummy_word;
+        t = 0; D = 0; tau = 0; sysI = 0;
+        abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
+        ++c_started;
+        ++reps_in_slot;
         if (p.Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0
             for (int a = 0; a < na; a += 2) {
                 const uint4 b = philox10(make_uint4(static_cast<uint32_t>(a) >> 1, r, slot_g,
@@ -115,23 +137,12 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
                         const uint32_t q = c >> 5, bit = 1u << (c & 31);
                         st[(2 * q) * 32] |= bit;
                         if (COUPLED) st[(2 * q + 1) * 32] |= bit;
-                        const uint4 row = sRows[c];
-                        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
-                                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
-#pragma unroll
-                        for (int l = 0; l < kRow; ++l) {
-                            if (l >= deg || ent[l] == p.dummy_entry) continue;
-                            uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
-                            *cnt = static_cast<uint16_t>(*cnt + (COUPLED ? 0x0101u : 0x0001u));
-                        }
+                        bump_counts(c, COUPLED ? 0x0101u : 0x0001u);
+                        rep_words |= 1ull << (q >> gshift);
                     }
                 }
             }
         }
-        t = 0; D = 0; tau = 0; sysI = 0;
-        abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
-        ++c_started;
-        ++reps_in_slot;
     };
 
     auto start_slot = [&]() {
@@ -143,13 +154,48 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
         start_rep();
     };
 
-    auto clear_rep_acc = [&]() {
-        for (uint32_t q = 0; q < W; ++q) {
-            uint32_t tw = trep[q];
-            if (!tw) continue;
-            while (tw) { const int b = __ffs(tw) - 1; tw &= tw - 1; racc[q * 32 + b] = 0; }
-            trep[q] = 0;
+    // End of a replication: empty the pair's state and the replication's accumulators; when `move`,
+    // first close the open intervals at C and add the replication's G into the slot's sums.
+    auto finish_rep = [&](bool move, uint32_t C) {
+        const long long wX = move ? wprefix<COUPLED>(C, p) : 0;
+        const long long wY = (move && COUPLED) ? wprefix<COUPLED>(static_cast<long long>(C) - 1, p) : 0;
+        unsigned long long groups = rep_words;
+        while (groups) {
+            const int g = __ffsll(static_cast<long long>(groups)) - 1;
+            groups &= groups - 1;
+            const uint32_t q0 = static_cast<uint32_t>(g) << gshift;
+            const uint32_t q1 = min(W, q0 + (1u << gshift));
+            for (uint32_t q = q0; q < q1; ++q) {
+                const uint32_t xw = st[(2 * q) * 32];
+                const uint32_t yw = COUPLED ? st[(2 * q + 1) * 32] : 0u;
+                const uint32_t tw = trep[q];
+                uint32_t m = tw | xw | yw, moved = 0;
+                if (!m) continue;
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    const uint32_t bit = 1u << b;
+                    m &= m - 1;
+                    const uint32_t j = q * 32 + b;
+                    long long v = 0;
+                    if (tw & bit) { v = racc[j]; racc[j] = 0; }
+                    if (move) {
+                        if (xw & bit) v += wX;
+                        if (yw & bit) v -= wY;
+                        if (v != 0) {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(&sacc[j]), static_cast<unsigned long long>(v));
+                            moved |= bit;
+                        }
+                    }
+                    const uint32_t delta = ((xw & bit) ? 0xFFFFu : 0u) + ((yw & bit) ? 0xFF00u : 0u);
+                    if (delta) bump_counts(j, delta);
+                }
+                if (tw) trep[q] = 0u;
+                if (xw) st[(2 * q) * 32] = 0u;
+                if (yw) st[(2 * q + 1) * 32] = 0u;
+                if (moved) { atomicOr(&tslot[q], moved); slot_words |= 1ull << g; }
+            }
         }
+        rep_words = 0;
     };
 
     auto end_slot = [&](bool valid) {
@@ -157,21 +203,30 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
         long long *tr = nullptr;
         if (valid && p.trace_stride > 0 && (slot_local % p.trace_stride) == 0)
             tr = p.trace_G + (static_cast<long long>(slot_local) / p.trace_stride) * na;
-        for (uint32_t q = 0; q < W; ++q) {
-            uint32_t tw = tslot[q];
-            if (!tw) continue;
-            while (tw) {
-                const int b = __ffs(tw) - 1; tw &= tw - 1;
-                const int j = q * 32 + b;
-                const long long g = sacc[j];
-                sacc[j] = 0;
-                if (valid && g != 0) {
-                    bucket_add(p, bkt, j, g);
-                    if (tr) tr[j] = g;
+        unsigned long long groups = slot_words;
+        while (groups) {
+            const int g = __ffsll(static_cast<long long>(groups)) - 1;
+            groups &= groups - 1;
+            const uint32_t q0 = static_cast<uint32_t>(g) << gshift;
+            const uint32_t q1 = min(W, q0 + (1u << gshift));
+            for (uint32_t q = q0; q < q1; ++q) {
+                uint32_t tw = tslot[q];
+                if (!tw) continue;
+                while (tw) {
+                    const int b = __ffs(tw) - 1;
+                    tw &= tw - 1;
+                    const uint32_t j = q * 32 + b;
+                    const long long gsum = sacc[j];
+                    sacc[j] = 0;
+                    if (valid && gsum != 0) {
+                        bucket_add(p, bkt, static_cast<int>(j), gsum);
+                        if (tr) tr[j] = gsum;
+                    }
                 }
+                tslot[q] = 0u;
             }
-            tslot[q] = 0;
         }
+        slot_words = 0;
         if (valid) atomicAdd(&p.bcount[bkt], 1ull);
         if (p.slot_nstar) {
             p.slot_nstar[slot_local] = valid ? static_cast<int32_t>(N) : 0;
@@ -181,34 +236,13 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
         start_slot();
     };
 
-    // Replication completed at C = t: close the open intervals, move the replication's sums into
-    // the slot's sums (every completed replication is retained: a later one that could not finish
-    // within B is aborted before it completes), then refill or end the slot.
+    // Completed at C = t: every completed replication is retained (a later one that could not
+    // finish within B is aborted before it completes); then refill or end the slot.
     auto complete = [&]() {
         const uint32_t C = t;
         c_prog += C;
         if (COUPLED) { c_sumtau += tau; c_maxtau = max(c_maxtau, tau); }
-        const long long wX = wprefix<COUPLED>(C, p);
-        const long long wY = COUPLED ? wprefix<COUPLED>(static_cast<long long>(C) - 1, p) : 0;
-        for (uint32_t q = 0; q < W; ++q) {
-            const uint32_t xw = st[(2 * q) * 32];
-            const uint32_t yw = COUPLED ? st[(2 * q + 1) * 32] : 0u;
-            const uint32_t tw = trep[q];
-            uint32_t mask = tw | xw | yw, moved = 0;
-            while (mask) {
-                const int b = __ffs(mask) - 1;
-                const uint32_t bit = 1u << b;
-                mask &= mask - 1;
-                const int j = q * 32 + b;
-                long long v = 0;
-                if (tw & bit) { v = racc[j]; racc[j] = 0; }
-                if (xw & bit) v += wX;
-                if (yw & bit) v -= wY;
-                if (v != 0) { sacc[j] += v; moved |= bit; }
-            }
-            if (tw) trep[q] = 0;
-            if (moved) tslot[q] |= moved;
-        }
+        finish_rep(true, C);
         S += C;
         N += 1;
         ++c_retained;
@@ -220,7 +254,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     auto abort_rep = [&]() {                  // doomed: S_p(r) would exceed B; discard it
         c_prog += t;
         ++c_aborted;
-        clear_rep_acc();
+        finish_rep(false, 0);
         end_slot(true);
     };
 
@@ -228,70 +262,11 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
         c_prog += t;
         ++c_limit;
         atomicExch(p.error, 1);
-        clear_rep_acc();
+        finish_rep(false, 0);
         end_slot(false);
     };
 
-    // One step at time t with the draw words (ws: site, wu: high half of the uniform).
-    auto step = [&](uint32_t ws, uint32_t wu) -> bool {
-        uint32_t I;
-        if (SYSTEMATIC) {
-            I = sysI;
-        } else {
-            const unsigned long long prod = static_cast<unsigned long long>(ws) * static_cast<uint32_t>(na);
-            const uint32_t col = static_cast<uint32_t>(prod >> 32), coin = static_cast<uint32_t>(prod);
-            const unsigned long long e = sAlias[col];
-            I = coin < static_cast<uint32_t>(e) ? col : static_cast<uint32_t>(e >> 32);
-        }
-        const uint4 row = sRows[I];
-        const uint32_t q = I >> 5, bit = 1u << (I & 31);
-        uint32_t *px = st + (2 * q) * 32;
-        const uint32_t xw = px[0];
-        const uint32_t yw = COUPLED ? px[32] : 0u;
-        const uint32_t xI = (xw & bit) ? 1u : 0u, yI = (yw & bit) ? 1u : 0u;
-        const uint32_t xy = xI | (yI << 8);
-        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
-                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
-        uint32_t ix = 0, iy = 0;
-#pragma unroll
-        for (int l = 0; l < kRow; ++l) {
-            if (l < deg) {
-                const uint32_t e = ent[l];
-                const uint32_t v = *reinterpret_cast<const uint16_t *>(cbase + (e & ~1u));
-                const uint32_t code = (e & 1u) ? 9u : 1u;   // 9 n+ + n- indexes the table
-                const uint32_t d = v ^ xy;
-                if ((d & 0xFFu) == 0) ix += code;          // c_j - x_I = 0: pool j decides
-                if (COUPLED && (d & 0xFF00u) == 0) iy += code;
-            }
-        }
-        const unsigned long long TX = sT[ix];
-        const unsigned long long TY = COUPLED ? sT[iy] : 0ull;
-        const uint32_t thx = static_cast<uint32_t>(TX >> 32), thy = static_cast<uint32_t>(TY >> 32);
-        uint32_t nX = wu < thx ? 1u : 0u, nY = wu < thy ? 1u : 0u;
-        if (wu == thx || (COUPLED && wu == thy)) {   // the low half of U decides (p ~ 2^-32)
-            const uint32_t lo = philox10(make_uint4(t, r, slot_g, p.instance | (2u << 24)), k0, k1).x;
-            if (wu == thx) nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
-            if (COUPLED && wu == thy) nY = lo < static_cast<uint32_t>(TY) ? 1u : 0u;
-        }
-        const bool prelag = COUPLED && t == 0;       // X_1 = Phi(X_0, U_0): X only
-        if (!COUPLED || prelag) nY = yI;
-        const uint32_t fx = nX ^ xI, fy = nY ^ yI;
-        if (fx | fy) {
-            if (fx) px[0] = xw ^ bit;
-            if (fy) px[32] = yw ^ bit;
-            const uint32_t delta = (fx ? (nX ? 0x0001u : 0xFFFFu) : 0u) + (fy ? (nY ? 0x0100u : 0xFF00u) : 0u);
-#pragma unroll
-            for (int l = 0; l < kRow; ++l) {
-                if (l >= deg || ent[l] == p.dummy_entry) continue;
-                uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
-                *cnt = static_cast<uint16_t>(*cnt + delta);
-            }
-            long long ev = 0;
-            if (fx) { const long long w = wprefix<COUPLED>(t, p); ev += nX ? -w : w; }           // X_{t+1}
-            if (fy) { const long long w = wprefix<COUPLED>(static_cast<long long>(t) - 1, p); ev += nY ? w : -w; }  // Y_t
-            if (ev != 0) { racc[I] += ev; trep[q] |= bit; }
-            if (COUPLED) D = D + (nX ^ nY) - (xI ^ yI);
-        }
+    auto after_step = [&]() -> bool {
         ++t;
         if (SYSTEMATIC) { ++sysI; if (sysI == static_cast<uint32_t>(na)) sysI = 0; }
         if (COUPLED) {
@@ -308,11 +283,146 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
         return false;
     };
 
+    auto draw_site = [&](uint32_t ws) -> uint32_t {
+        if (SYSTEMATIC) return sysI;
+        const unsigned long long prod = static_cast<unsigned long long>(ws) * static_cast<uint32_t>(na);
+        const uint32_t col = static_cast<uint32_t>(prod >> 32), coin = static_cast<uint32_t>(prod);
+        const unsigned long long e = sAlias[col];
+        return coin < static_cast<uint32_t>(e) ? col : static_cast<uint32_t>(e >> 32);
+    };
+
+    // One step for a pair whose Y chain equals its X chain where it matters: the pre-lag update
+    // (t = 0, X only) or a pair that has met (X_t = Y_{t-1}, so Y_t = X_{t+1} and both flip
+    // together).  Uncoupled chains always take this path.
+    auto step_fast = [&](uint32_t ws, uint32_t wu) -> bool {
+        const uint32_t I = draw_site(ws);
+        const uint4 row = sRows[I];
+        const uint32_t q = I >> 5, bit = 1u << (I & 31);
+        uint32_t *px = st + (2 * q) * 32;
+        const uint32_t xw = px[0];
+        const uint32_t xI = (xw & bit) ? 1u : 0u;
+        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
+                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
+        uint32_t ix = 0;
+#pragma unroll
+        for (int l = 0; l < kRow; ++l) {
+            if (l < deg) {
+                const uint32_t e = ent[l];
+                const uint32_t c = cbase[e & ~1u];                 // X count of the pool
+                if (c == xI) ix += (e & 1u) ? 9u : 1u;           // c_j - x_I = 0: pool j decides
+            }
+        }
+        const unsigned long long TX = sT[ix];
+        const uint32_t thx = static_cast<uint32_t>(TX >> 32);
+        uint32_t nX = wu < thx ? 1u : 0u;
+        if (wu == thx) {                                        // the low half of U decides
+            const uint32_t lo = philox10(make_uint4(t, r, slot_g, p.instance | (2u << 24)), k0, k1).x;
+            nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
+        }
+        if (nX != xI) {
+            const bool both = COUPLED && t > 0;
+            px[0] = xw ^ bit;
+            if (both) px[32] ^= bit;
+            const uint32_t delta = nX ? (both ? 0x0101u : 0x0001u) : (both ? 0xFEFFu : 0xFFFFu);
+#pragma unroll
+            for (int l = 0; l < kRow; ++l) {
+                if (l >= deg || ent[l] == p.dummy_entry) continue;
+                uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
+                *cnt = static_cast<uint16_t>(*cnt + delta);
+            }
+            long long w;
+            if (COUPLED) {
+                if (both) {                                      // W(t) - W(t-1): X at t+1, Y at t
+                    const long long a = static_cast<long long>(t) - p.k + 1;
+                    w = a < 0 ? 0 : (a > p.L ? p.L : a);
+                } else {
+                    w = wprefix<true>(0, p);                     // X_1 only
+                    D = 1;
+                }
+            } else {
+                w = wprefix<false>(t, p);
+            }
+            if (w != 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]),
+                          static_cast<unsigned long long>(nX ? -w : w));
+                atomicOr(&trep[q], bit);
+            }
+            rep_words |= 1ull << (q >> gshift);
+        }
+        return after_step();
+    };
+
+    // One coupled step for a pair that has not met: both chains read their own state.
+    auto step_full = [&](uint32_t ws, uint32_t wu) -> bool {
+        const uint32_t I = draw_site(ws);
+        const uint4 row = sRows[I];
+        const uint32_t q = I >> 5, bit = 1u << (I & 31);
+        uint32_t *px = st + (2 * q) * 32;
+        const uint32_t xw = px[0], yw = px[32];
+        const uint32_t xI = (xw & bit) ? 1u : 0u, yI = (yw & bit) ? 1u : 0u;
+        const uint32_t xy = xI | (yI << 8);
+        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
+                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
+        uint32_t ix = 0, iy = 0;
+#pragma unroll
+        for (int l = 0; l < kRow; ++l) {
+            if (l < deg) {
+                const uint32_t e = ent[l];
+                const uint32_t v = *reinterpret_cast<const uint16_t *>(cbase + (e & ~1u));
+                const uint32_t code = (e & 1u) ? 9u : 1u;
+                const uint32_t d = v ^ xy;
+                if ((d & 0xFFu) == 0) ix += code;
+                if ((d & 0xFF00u) == 0) iy += code;
+            }
+        }
+        const unsigned long long TX = sT[ix], TY = sT[iy];
+        const uint32_t thx = static_cast<uint32_t>(TX >> 32), thy = static_cast<uint32_t>(TY >> 32);
+        uint32_t nX = wu < thx ? 1u : 0u, nY = wu < thy ? 1u : 0u;
+        if (wu == thx || wu == thy) {
+            const uint32_t lo = philox10(make_uint4(t, r, slot_g, p.instance | (2u << 24)), k0, k1).x;
+            if (wu == thx) nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
+            if (wu == thy) nY = lo < static_cast<uint32_t>(TY) ? 1u : 0u;
+        }
+        if (t == 0) nY = yI;                                    // pre-lag: X only
+        const uint32_t fx = nX ^ xI, fy = nY ^ yI;
+        if (fx | fy) {
+            if (fx) px[0] = xw ^ bit;
+            if (fy) px[32] = yw ^ bit;
+            const uint32_t delta = (fx ? (nX ? 0x0001u : 0xFFFFu) : 0u) + (fy ? (nY ? 0x0100u : 0xFF00u) : 0u);
+#pragma unroll
+            for (int l = 0; l < kRow; ++l) {
+                if (l >= deg || ent[l] == p.dummy_entry) continue;
+                uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
+                *cnt = static_cast<uint16_t>(*cnt + delta);
+            }
+            long long ev = 0;
+            if (fx) { const long long w = wprefix<true>(t, p); ev += nX ? -w : w; }             // X_{t+1}
+            if (fy) { const long long w = wprefix<true>(static_cast<long long>(t) - 1, p); ev += nY ? w : -w; }  // Y_t
+            if (ev != 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]), static_cast<unsigned long long>(ev));
+                atomicOr(&trep[q], bit);
+            }
+            rep_words |= 1ull << (q >> gshift);
+            D = D + (nX ^ nY) - (xI ^ yI);
+        }
+        return after_step();
+    };
+
     start_slot();
+    uint4 blk = philox10(make_uint4(t >> 1, r, slot_g, p.instance), k0, k1);
     while (alive) {
-        // one Philox block per pair of steps: words (0,1) at even t, (2,3) at odd t
-        const uint4 blk = philox10(make_uint4(t >> 1, r, slot_g, p.instance), k0, k1);
-        if (!step(blk.x, blk.y)) step(blk.z, blk.w);
+        // one Philox block per pair of steps, words (0,1) at even t and (2,3) at odd t; the next
+        // block is computed ahead and discarded if the replication ends
+        const uint4 nxt = philox10(make_uint4((t >> 1) + 1, r, slot_g, p.instance), k0, k1);
+        bool ended;
+        if (COUPLED && !__all_sync(__activemask(), t == 0 || D == 0)) ended = step_full(blk.x, blk.y);
+        else ended = step_fast(blk.x, blk.y);
+        if (!ended) {
+            if (COUPLED && !__all_sync(__activemask(), D == 0)) ended = step_full(blk.z, blk.w);
+            else ended = step_fast(blk.z, blk.w);
+        }
+        if (ended) blk = philox10(make_uint4(t >> 1, r, slot_g, p.instance), k0, k1);
+        else blk = nxt;
     }
 
     if (c_prog) atomicAdd(&p.counters[kProgress], c_prog);
