@@ -162,6 +162,24 @@ int mcpd_decode(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
 int mcpd_inspect(const mcpd_design *design, const uint8_t *y, const mcpd_params *params,
                  int64_t info[16], int32_t *active, double *w, uint64_t *alias, uint64_t *T);
 
+/* Decode without any device allocation.  The paper has no counterpart: this entry point exists for
+ * callers that may not call cudaMalloc or cudaFree themselves, such as a component running under
+ * a host application or server that owns all device memory through its own pool allocator and
+ * hands out fixed budgets, or a host loop that cannot afford the device-wide synchronisation those
+ * calls can imply.  The caller passes the host inputs (as for mcpd_decode) and two device arrays
+ * it owns, est_dev and se_dev, each [n_active] in active order (mcpd_inspect gives n_active and the
+ * active ids).  All other device memory comes from one 64 MiB array compiled into this library,
+ * held on every GPU that loads it until the process exits.  Problems whose tables, N*_p buckets
+ * and one warp of pair accumulators do not fit in it fail with MCPD_ETOO_LARGE; problems that fit
+ * run with as many resident pairs as fit and give the same results as mcpd_run_async.
+ * record_slots and trace_stride must be 0.  The first call on a device looks the array up (with
+ * that device current), so make it before any stream capture.  Every call clears and reuses the
+ * same array: calls whose GPU work overlaps on one device race, so serialise them.  Synchronous
+ * on the context's stream; stats may be NULL (kernel_ms is left 0). */
+int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
+                        const mcpd_params *params, double *est_dev, double *se_dev,
+                        mcpd_stats *stats);
+
 /* Philox4x32-10 blocks computed by the device generator the sampler uses: out[4 i .. 4 i + 3] =
  * Philox(ctr[4 i .. 4 i + 3], key).  ctr, out: device arrays of 4 n words. */
 int mcpd_philox_device(mcpd_ctx *ctx, const uint32_t *ctr_dev, uint32_t key0, uint32_t key1,

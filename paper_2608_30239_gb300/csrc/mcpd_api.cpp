@@ -14,14 +14,6 @@ namespace mcpd {
 int pairs_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm);
 }
 
-struct mcpd_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int sm_count = 0;
-    size_t smem_optin = 0;
-    std::string err;
-};
-
 struct mcpd_plan {
     mcpd_ctx *ctx = nullptr;
     mcpd::Tables t;

@@ -5,7 +5,19 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime_api.h>
+
 #include "../../include/mcpd.h"
+
+// A context: one device, one stream.  Defined here so every translation unit of the library
+// sees the same definition.
+struct mcpd_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    std::string err;
+};
 
 namespace mcpd {
 

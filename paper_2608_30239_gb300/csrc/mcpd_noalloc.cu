@@ -1,0 +1,189 @@
+// mcpd_decode_noalloc: the coupled decode without any device allocation.
+//
+// Who needs this: a caller whose device memory is owned by someone else and who therefore may not
+// call cudaMalloc / cudaFree itself, for example a plug-in inside an application or server that
+// gives every component a fixed memory budget up front through its own pool allocator, or a
+// latency-sensitive host loop that cannot afford the device-wide synchronisation cudaMalloc and
+// cudaFree can imply.  Such a caller passes the host inputs and two device output arrays it
+// already owns; everything else the sampling kernel needs (the staged tables, the per-pair
+// accumulators, the N*_p buckets and the counters) lives in one file-scope device array that is
+// part of the library image.
+//
+// Limits and sharing:
+//   - The array holds kNoAllocScratchBytes (64 MiB) on every GPU that loads this library, until
+//     the process exits.  A problem whose tables plus buckets plus one warp of pair accumulators do
+//     not fit is rejected with MCPD_ETOO_LARGE; a problem that fits runs with as many resident
+//     pairs as fit (fewer than the allocating path may use, same results).
+//   - Every call uses the same array and leaves its contents behind; each call clears what must
+//     start at zero.  Two calls whose work overlaps on the GPU (other streams, other host threads,
+//     on the same device) race on the array: serialise them.
+//   - The first call on a device, with that device current, looks up the array's device address
+//     with cudaGetSymbolAddress and caches it; make that first call before any stream capture.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "mcpd_internal.h"
+
+namespace mcpd {
+int pairs_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm);
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_setup_mutex;
+void *g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the array on `device` (current); looked up once per device.
+int scratch_address(int device, void **out, std::string *err) {
+    if (device < 0 || device >= kMaxDevices) { *err = "device index out of range"; return MCPD_EINVAL; }
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_addr[device]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return MCPD_ECUDA;
+        }
+        g_scratch_addr[device] = ptr;
+    }
+    *out = g_scratch_addr[device];
+    return MCPD_OK;
+}
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+}  // namespace
+}  // namespace mcpd
+
+namespace {
+int fail(mcpd_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+}  // namespace
+
+#define CUN(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return fail(ctx, MCPD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
+                                   const mcpd_params *params, double *est_dev, double *se_dev,
+                                   mcpd_stats *stats) {
+    using namespace mcpd;
+    if (!ctx || !est_dev || !se_dev) return MCPD_EINVAL;
+    Tables t;
+    std::string err;
+    int rc = build_tables(design, y, params, &t, &err);
+    if (rc != MCPD_OK) return fail(ctx, rc, err);
+    if (t.record_slots || t.trace_stride > 0)
+        return fail(ctx, MCPD_EINVAL, "no-alloc decode keeps no per-slot records or traces");
+    CUN(cudaSetDevice(ctx->device));
+    void *base = nullptr;
+    rc = scratch_address(ctx->device, &base, &err);
+    if (rc != MCPD_OK) return fail(ctx, rc, err);
+
+    // Fixed part of the layout: tables, buckets, counters.
+    const size_t na = static_cast<size_t>(t.na), nb = static_cast<size_t>(t.nb);
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t at = off; off += up256(bytes); return at; };
+    const size_t o_alias = take(na * 8), o_rows = take(na * 16), o_T = take(t.T.size() * 8);
+    const size_t o_Tnu = take(t.Tnu.size() * 8);
+    const size_t o_S1 = take(nb * na * 8), o_S2lo = take(nb * na * 8), o_S2hi = take(nb * na * 8);
+    const size_t o_bc = take(nb * 8), o_cnt = take(kNumCounters * 8), o_err = take(sizeof(int));
+    const size_t fixed = off;
+
+    // Launch shape as the allocating path would choose it, then as many whole warps as fit.
+    const size_t tables = ((na * 24 + kTSide * kTSide * 8) + 15) / 16 * 16;
+    const size_t per_warp_smem = static_cast<size_t>(t.wpp) * 128;
+    if (tables + per_warp_smem > ctx->smem_optin)
+        return fail(ctx, MCPD_ETOO_LARGE, "instance too large for the one-thread-per-pair layout");
+    int warps = static_cast<int>(std::min<size_t>(16, (ctx->smem_optin - tables) / per_warp_smem));
+    const size_t half = ctx->smem_optin / 2;
+    if (half > tables && (half - tables) / per_warp_smem >= 8)
+        warps = static_cast<int>(std::min<size_t>(warps, (half - tables) / per_warp_smem));
+    const size_t per_pair = na * 16 + static_cast<size_t>(t.W) * 8;   // rep/slot sums, touched sets
+    if (fixed >= kNoAllocScratchBytes)
+        return fail(ctx, MCPD_ETOO_LARGE, "tables and N*_p buckets exceed the 64 MiB no-alloc scratch");
+    const size_t fit_warps = (kNoAllocScratchBytes - fixed - 4 * 256) / (32 * per_pair);
+    if (fit_warps < 1)
+        return fail(ctx, MCPD_ETOO_LARGE, "not even one warp of pair accumulators fits the 64 MiB no-alloc scratch");
+    int per_sm = 1;
+    size_t smem = tables + per_warp_smem * warps;
+    if (set_pairs_smem(smem, t.coupled) != MCPD_OK) return fail(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
+    if (pairs_occupancy(t.coupled, t.scan, warps * 32, smem, &per_sm) != MCPD_OK || per_sm < 1) per_sm = 1;
+    warps = static_cast<int>(std::min<size_t>(warps, fit_warps));
+    smem = tables + per_warp_smem * warps;
+    const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(ctx->sm_count) * per_sm, fit_warps / warps));
+    const size_t pairs = static_cast<size_t>(grid) * warps * 32;
+    const size_t o_racc = take(pairs * na * 8), o_sacc = take(pairs * na * 8);
+    const size_t o_trep = take(pairs * t.W * 4), o_tslot = take(pairs * t.W * 4);
+    if (off > kNoAllocScratchBytes) return fail(ctx, MCPD_ETOO_LARGE, "no-alloc scratch layout overflow");
+
+    unsigned char *b = static_cast<unsigned char *>(base);
+    cudaStream_t s = ctx->stream;
+    CUN(cudaMemsetAsync(b, 0, off, s));     // the array keeps the previous call's contents
+    CUN(cudaMemcpyAsync(b + o_alias, t.alias.data(), na * 8, cudaMemcpyHostToDevice, s));
+    CUN(cudaMemcpyAsync(b + o_rows, t.rows.data(), t.rows.size() * 2, cudaMemcpyHostToDevice, s));
+    CUN(cudaMemcpyAsync(b + o_T, t.T.data(), t.T.size() * 8, cudaMemcpyHostToDevice, s));
+    if (!t.Tnu.empty()) CUN(cudaMemcpyAsync(b + o_Tnu, t.Tnu.data(), t.Tnu.size() * 8, cudaMemcpyHostToDevice, s));
+
+    KParams kp{};
+    kp.alias = reinterpret_cast<const uint64_t *>(b + o_alias);
+    kp.rows = reinterpret_cast<const uint16_t *>(b + o_rows);
+    kp.T = reinterpret_cast<const uint64_t *>(b + o_T);
+    kp.Tnu = t.Tnu.empty() ? nullptr : reinterpret_cast<const uint64_t *>(b + o_Tnu);
+    kp.rep_acc = reinterpret_cast<long long *>(b + o_racc);
+    kp.slot_acc = reinterpret_cast<long long *>(b + o_sacc);
+    kp.touched_rep = reinterpret_cast<uint32_t *>(b + o_trep);
+    kp.touched_slot = reinterpret_cast<uint32_t *>(b + o_tslot);
+    kp.S1 = reinterpret_cast<unsigned long long *>(b + o_S1);
+    kp.S2lo = reinterpret_cast<unsigned long long *>(b + o_S2lo);
+    kp.S2hi = reinterpret_cast<unsigned long long *>(b + o_S2hi);
+    kp.bcount = reinterpret_cast<unsigned long long *>(b + o_bc);
+    kp.counters = reinterpret_cast<unsigned long long *>(b + o_cnt);
+    kp.error = reinterpret_cast<int *>(b + o_err);
+    kp.na = t.na; kp.m = t.m; kp.W = t.W; kp.Mp = t.Mp; kp.wpp = t.wpp; kp.deg = t.deg_max;
+    kp.nb = static_cast<int32_t>(t.nb); kp.scan = t.scan;
+    kp.dummy_entry = t.dummy_entry; kp.dummy_word = t.dummy_word;
+    kp.dummy_word_index = t.dummy_word_index; kp.coupled = t.coupled ? 1 : 0;
+    kp.P = t.P; kp.B = t.B; kp.k = t.k; kp.ell = t.ell; kp.L = t.L; kp.burn = t.burn;
+    kp.length = t.length; kp.unit = t.unit; kp.step_limit = t.step_limit;
+    kp.slot_offset = t.slot_offset; kp.trace_stride = 0;
+    kp.seed = t.seed; kp.instance = t.instance; kp.warps = warps;
+    kp.smem_tables = static_cast<uint32_t>(tables);
+    if (launch_pairs(kp, grid, warps * 32, smem, s) != MCPD_OK)
+        return fail(ctx, MCPD_ECUDA, std::string("pairs kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
+    if (launch_finalize(kp.S1, kp.S2lo, kp.S2hi, t.na, static_cast<int>(t.nb), t.P, t.L, est_dev, se_dev, s) != MCPD_OK)
+        return fail(ctx, MCPD_ECUDA, "finalize kernel launch");
+    unsigned long long c[kNumCounters];
+    int error = 0;
+    CUN(cudaMemcpyAsync(c, kp.counters, sizeof(c), cudaMemcpyDeviceToHost, s));
+    CUN(cudaMemcpyAsync(&error, kp.error, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUN(cudaStreamSynchronize(s));
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->progress_units = static_cast<int64_t>(c[kProgress]);
+        stats->reps_started = static_cast<int64_t>(c[kRepsStarted]);
+        stats->reps_retained = static_cast<int64_t>(c[kRepsRetained]);
+        stats->reps_aborted = static_cast<int64_t>(c[kRepsAborted]);
+        stats->zero_completion_slots = static_cast<int64_t>(c[kZeroCompletion]);
+        stats->step_limit_hits = static_cast<int64_t>(c[kStepLimitHits]);
+        stats->max_tau = static_cast<int64_t>(c[kMaxTau]);
+        stats->sum_tau = static_cast<int64_t>(c[kSumTau]);
+        stats->site_updates = t.coupled ? 2 * stats->progress_units - stats->reps_started : stats->progress_units;
+        stats->n_buckets = t.nb;
+        stats->n_active = t.na;
+    }
+    if (error) return fail(ctx, MCPD_ESTEP_LIMIT, "a pair reached the step limit without meeting");
+    return MCPD_OK;
+}

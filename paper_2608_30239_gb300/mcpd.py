@@ -95,6 +95,8 @@ def lib(build_if_missing: bool = False):
             "mcpd_inspect": (C.c_int, [C.POINTER(mcpd_design), P, C.POINTER(mcpd_params), P, P,
                                        P, P, P]),
             "mcpd_philox_device": (C.c_int, [P, P, C.c_uint32, C.c_uint32, P, I64]),
+            "mcpd_decode_noalloc": (C.c_int, [P, C.POINTER(mcpd_design), P, C.POINTER(mcpd_params),
+                                              P, P, C.POINTER(mcpd_stats)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -231,6 +233,22 @@ class Context:
         if rc not in (MCPD_OK, MCPD_ESTEP_LIMIT):
             self.check(rc, "mcpd_decode")
         return dict(status=rc, est=est, se=se, active=act, stats=st.as_dict())
+
+
+    def decode_noalloc(self, inst, est_dev, se_dev, **params):
+        """mcpd_decode_noalloc: host inputs, caller-owned device outputs [n_active], and no device
+        allocation by the library (its scratch is a fixed 64 MiB array inside the library)."""
+        keep = _Keep()
+        d, y = make_design(inst, keep)
+        prm = make_params(inst, keep, **params)
+        st = mcpd_stats()
+        rc = lib().mcpd_decode_noalloc(self.h, C.byref(d), _ptr(y), C.byref(prm), _ptr(est_dev),
+                                       _ptr(se_dev), C.byref(st))
+        if rc not in (MCPD_OK, MCPD_ESTEP_LIMIT):
+            self.check(rc, "mcpd_decode_noalloc")
+        out = st.as_dict()
+        out["status"] = rc
+        return out
 
 
 class Plan:
