@@ -266,21 +266,20 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
         end_slot(false);
     };
 
-    auto after_step = [&]() -> bool {
+    // Advance the clock after a step; 0 = continue, 1 = completed, 2 = doomed, 3 = step limit.
+    auto after_step = [&]() -> int {
         ++t;
         if (SYSTEMATIC) { ++sysI; if (sysI == static_cast<uint32_t>(na)) sysI = 0; }
         if (COUPLED) {
             if (D == 0) {
                 if (tau == 0) tau = t;               // tau_1 = first t >= 1 with X_t = Y_{t-1}
-                if (t >= ell) { complete(); return true; }
+                if (t >= ell) return 1;
             }
-            if (t >= abort_t) { abort_rep(); return true; }
+            if (t >= abort_t) return 2;
         } else if (t >= unit) {
-            complete();
-            return true;
+            return 1;
         }
-        if (t >= step_limit) { limit_hit(); return true; }
-        return false;
+        return t >= step_limit ? 3 : 0;
     };
 
     auto draw_site = [&](uint32_t ws) -> uint32_t {
@@ -294,7 +293,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     // One step for a pair whose Y chain equals its X chain where it matters: the pre-lag update
     // (t = 0, X only) or a pair that has met (X_t = Y_{t-1}, so Y_t = X_{t+1} and both flip
     // together).  Uncoupled chains always take this path.
-    auto step_fast = [&](uint32_t ws, uint32_t wu) -> bool {
+    auto step_fast = [&](uint32_t ws, uint32_t wu) -> int {
         const uint32_t I = draw_site(ws);
         const uint4 row = sRows[I];
         const uint32_t q = I >> 5, bit = 1u << (I & 31);
@@ -353,7 +352,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     };
 
     // One coupled step for a pair that has not met: both chains read their own state.
-    auto step_full = [&](uint32_t ws, uint32_t wu) -> bool {
+    auto step_full = [&](uint32_t ws, uint32_t wu) -> int {
         const uint32_t I = draw_site(ws);
         const uint4 row = sRows[I];
         const uint32_t q = I >> 5, bit = 1u << (I & 31);
@@ -414,15 +413,21 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
         // one Philox block per pair of steps, words (0,1) at even t and (2,3) at odd t; the next
         // block is computed ahead and discarded if the replication ends
         const uint4 nxt = philox10(make_uint4((t >> 1) + 1, r, slot_g, p.instance), k0, k1);
-        bool ended;
-        if (COUPLED && !__all_sync(__activemask(), t == 0 || D == 0)) ended = step_full(blk.x, blk.y);
-        else ended = step_fast(blk.x, blk.y);
-        if (!ended) {
-            if (COUPLED && !__all_sync(__activemask(), D == 0)) ended = step_full(blk.z, blk.w);
-            else ended = step_fast(blk.z, blk.w);
+        int ended = 0;
+#pragma unroll 1
+        for (int h = 0; h < 2 && !ended; ++h) {
+            const uint32_t ws = h ? blk.z : blk.x, wu = h ? blk.w : blk.y;
+            if (COUPLED && !__all_sync(__activemask(), t == 0 || D == 0)) ended = step_full(ws, wu);
+            else ended = step_fast(ws, wu);
         }
-        if (ended) blk = philox10(make_uint4(t >> 1, r, slot_g, p.instance), k0, k1);
-        else blk = nxt;
+        if (ended) {
+            if (ended == 1) complete();
+            else if (ended == 2) abort_rep();
+            else limit_hit();
+            blk = philox10(make_uint4(t >> 1, r, slot_g, p.instance), k0, k1);
+        } else {
+            blk = nxt;
+        }
     }
 
     if (c_prog) atomicAdd(&p.counters[kProgress], c_prog);
