@@ -162,6 +162,51 @@ int mcpd_decode(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
 int mcpd_inspect(const mcpd_design *design, const uint8_t *y, const mcpd_params *params,
                  int64_t info[16], int32_t *active, double *w, uint64_t *alias, uint64_t *T);
 
+/* ---- Batched decoding: many instances of uneven size in one persistent launch ----------------
+ * Each instance i is its own problem (design, y, params[i]: rates, prior, window, slots P_i,
+ * horizon B_i, seed, instance_id) with its own theta_CT and standard errors; the instances share
+ * one launch of the sampling kernel, which hands out (instance, slot) work items instance-major
+ * from one device counter and reads each instance's tables through the read-only cache.  All
+ * instances must agree on `coupled` and on whether the scan is systematic; record_slots and
+ * trace_stride must be 0.  Outputs are concatenated in input order: instance i owns entries
+ * offsets[i] .. offsets[i+1]-1 of est / se (its retained clones, ascending original index). */
+typedef struct mcpd_batch mcpd_batch;
+
+/* Build the batch.  designs, ys, params: [n_inst] host arrays (borrowed).  order_mode 0 keeps the
+ * instances in input order in the work list; 1 puts the instances with the longest slots (largest
+ * horizon) first. */
+int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
+                      const uint8_t *const *ys, const mcpd_params *params, int32_t order_mode,
+                      mcpd_batch **out);
+void mcpd_batch_destroy(mcpd_batch *batch);
+/* info[0] total retained clones, [1] instances, [2] total slots, [3] largest n_active,
+ * [4] warps per block, [5] blocks, [6] resident pairs, [7] shared-memory bytes per block,
+ * [8] lanes per pair. */
+int mcpd_batch_info(const mcpd_batch *batch, int64_t info[16]);
+/* offsets: [n_inst + 1] host array receiving each instance's first output index. */
+int mcpd_batch_offsets(const mcpd_batch *batch, int64_t *offsets);
+/* Choose the launch shape: warps per block (0: as many as the largest instance's pair state
+ * allows, at most 16).  May reallocate the per-pair scratch; invalidates a captured graph. */
+int mcpd_batch_set_shape(mcpd_ctx *ctx, mcpd_batch *batch, int32_t warps_per_block);
+/* Enqueue one decode of every instance; est_dev, se_dev: device arrays [info[0]]. */
+int mcpd_batch_run_async(mcpd_ctx *ctx, mcpd_batch *batch, double *est_dev, double *se_dev);
+/* Capture one decode (scratch clears, sampling kernel, finalize) into a CUDA graph on the
+ * context's stream (which must not be the legacy default stream); replay it with
+ * mcpd_batch_launch_graph. */
+int mcpd_batch_capture_graph(mcpd_ctx *ctx, mcpd_batch *batch, double *est_dev, double *se_dev);
+int mcpd_batch_launch_graph(mcpd_ctx *ctx, mcpd_batch *batch);
+/* Wait for the last decode and read its counters (summed over instances). */
+int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *batch, mcpd_stats *stats);
+/* One instance's integer bucket sums (MCPD_FETCH_S1, _S2_LO, _S2_HI, _COUNT), sized as for a
+ * plan of that instance alone. */
+int mcpd_batch_fetch(mcpd_ctx *ctx, const mcpd_batch *batch, int32_t inst, int what,
+                     void *host_dst, size_t bytes);
+/* Autotuner: time each candidate warps-per-block (reps timed decodes after one warm-up each),
+ * keep the fastest; times[c] gets candidate c's mean milliseconds (-1 if it does not fit). */
+int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *batch, const int32_t *cand_warps,
+                        int32_t n_cand, int32_t reps, double *est_dev, double *se_dev,
+                        int32_t *best_warps, double *times);
+
 /* Decode without any device allocation.  The paper has no counterpart: this entry point exists for
  * callers that may not call cudaMalloc or cudaFree themselves, such as a component running under
  * a host application or server that owns all device memory through its own pool allocator and

@@ -361,3 +361,382 @@ int mcpd_philox_device(mcpd_ctx *ctx, const uint32_t *ctr_dev, uint32_t key0, ui
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Batched decoding: many instances of uneven size in one persistent launch.
+
+struct mcpd_batch {
+    mcpd_ctx *ctx = nullptr;
+    std::vector<mcpd::Tables> t;
+    std::vector<int32_t> order;            // launch order of instances (instance-major work list)
+    std::vector<int64_t> out_offset;       // [n + 1] offsets of each instance's clones in est/se
+    std::vector<int64_t> bucket_offset;    // [n] offsets of each instance's buckets (in nb*na units)
+    std::vector<int64_t> count_offset;     // [n]
+    mcpd::BParams bp{};
+    mcpd::InstDesc *d_insts = nullptr;
+    std::vector<mcpd::InstDesc> insts;     // in launch order
+    int32_t *d_clone_inst = nullptr, *d_clone_local = nullptr;
+    unsigned long long *d_buckets = nullptr;   // S1 | S2lo | S2hi, each total_bucket_words
+    unsigned long long *d_bcount = nullptr;
+    size_t total_bucket_words = 0, total_counts = 0;
+    int64_t total_active = 0, total_slots = 0;
+    int grid = 0, block = 0, warps = 0;
+    size_t smem = 0;
+    long long pairs = 0, scratch_pairs = 0;
+    bool dirty = true, ran = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<void *> allocs;            // tables, descriptors, buckets (fixed)
+    std::vector<void *> scratch;           // per-pair accumulators (resized by the tuner)
+};
+
+namespace {
+
+template <typename T>
+int balloc(mcpd_ctx *ctx, std::vector<void *> &list, T **ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) return MCPD_OK;
+    void *p = nullptr;
+    CU(cudaMalloc(&p, count * sizeof(T)));
+    list.push_back(p);
+    *ptr = static_cast<T *>(p);
+    return MCPD_OK;
+}
+
+void free_list(std::vector<void *> &list) {
+    for (void *p : list) cudaFree(p);
+    list.clear();
+}
+
+// Launch shape for `warps` per block (0: as many as fit, at most 16) and the scratch it needs.
+int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps) {
+    const size_t per_warp = static_cast<size_t>(b->bp.max_wpp) * 128;
+    const int fit = static_cast<int>(std::min<size_t>(16, ctx->smem_optin / per_warp));
+    if (fit < 1) return set_err(ctx, MCPD_ETOO_LARGE, "largest instance does not fit one warp of pair state");
+    if (warps <= 0) warps = fit;
+    if (warps > fit) return set_err(ctx, MCPD_EINVAL, "warps per block above what shared memory holds");
+    b->warps = warps;
+    b->block = warps * 32;
+    b->smem = per_warp * warps;
+    if (mcpd::set_batch_smem(b->smem) != MCPD_OK) return set_err(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
+    int per_sm = 1;
+    if (mcpd::batch_occupancy(b->bp.coupled, b->bp.scan, b->block, b->smem, &per_sm) != MCPD_OK || per_sm < 1)
+        per_sm = 1;
+    b->grid = ctx->sm_count * per_sm;
+    b->pairs = static_cast<long long>(b->grid) * b->block;
+    if (b->pairs > b->scratch_pairs) {
+        free_list(b->scratch);
+        const size_t pn = static_cast<size_t>(b->pairs) * b->bp.max_na, pw = static_cast<size_t>(b->pairs) * b->bp.max_W;
+        int rc;
+        if ((rc = balloc(ctx, b->scratch, &b->bp.rep_acc, pn)) != MCPD_OK) return rc;
+        if ((rc = balloc(ctx, b->scratch, &b->bp.slot_acc, pn)) != MCPD_OK) return rc;
+        if ((rc = balloc(ctx, b->scratch, &b->bp.touched_rep, pw)) != MCPD_OK) return rc;
+        if ((rc = balloc(ctx, b->scratch, &b->bp.touched_slot, pw)) != MCPD_OK) return rc;
+        b->scratch_pairs = b->pairs;
+        b->dirty = true;
+    }
+    if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    return MCPD_OK;
+}
+
+int batch_enqueue(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev, bool always_clear) {
+    const cudaStream_t s = ctx->stream;
+    CU(cudaMemsetAsync(b->d_buckets, 0, b->total_bucket_words * 3 * 8, s));
+    CU(cudaMemsetAsync(b->d_bcount, 0, b->total_counts * 8, s));
+    CU(cudaMemsetAsync(b->bp.counters, 0, mcpd::kNumCounters * 8, s));
+    CU(cudaMemsetAsync(b->bp.error, 0, sizeof(int), s));
+    if (b->dirty || always_clear) {
+        const size_t pn = static_cast<size_t>(b->pairs) * b->bp.max_na, pw = static_cast<size_t>(b->pairs) * b->bp.max_W;
+        CU(cudaMemsetAsync(b->bp.rep_acc, 0, pn * 8, s));
+        CU(cudaMemsetAsync(b->bp.slot_acc, 0, pn * 8, s));
+        CU(cudaMemsetAsync(b->bp.touched_rep, 0, pw * 4, s));
+        CU(cudaMemsetAsync(b->bp.touched_slot, 0, pw * 4, s));
+    }
+    if (mcpd::launch_batch(b->bp, b->grid, b->block, b->smem, s) != MCPD_OK)
+        return set_err(ctx, MCPD_ECUDA, std::string("batch kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
+    if (mcpd::launch_finalize_batch(b->d_insts, b->bp.n_inst, b->d_clone_inst, b->d_clone_local,
+                                    b->total_active, est_dev, se_dev, s) != MCPD_OK)
+        return set_err(ctx, MCPD_ECUDA, "batch finalize launch");
+    return MCPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mcpd_batch_destroy(mcpd_batch *b) {
+    if (!b) return;
+    if (b->ctx) cudaSetDevice(b->ctx->device);
+    if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    free_list(b->allocs);
+    free_list(b->scratch);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    delete b;
+}
+
+int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
+                      const uint8_t *const *ys, const mcpd_params *params, int32_t order_mode,
+                      mcpd_batch **out) {
+    if (!ctx || !out || n_inst < 1 || !designs || !ys || !params) return MCPD_EINVAL;
+    *out = nullptr;
+    mcpd_batch *b = new (std::nothrow) mcpd_batch();
+    if (!b) return set_err(ctx, MCPD_ENOMEM, "host allocation");
+    b->ctx = ctx;
+    b->t.resize(n_inst);
+    for (int32_t i = 0; i < n_inst; ++i) {
+        std::string err;
+        const int rc = mcpd::build_tables(&designs[i], ys[i], &params[i], &b->t[i], &err);
+        if (rc != MCPD_OK) { mcpd_batch_destroy(b); return set_err(ctx, rc, "instance " + std::to_string(i) + ": " + err); }
+        if (b->t[i].coupled != b->t[0].coupled || (b->t[i].scan == MCPD_SCAN_SYSTEMATIC) != (b->t[0].scan == MCPD_SCAN_SYSTEMATIC)) {
+            mcpd_batch_destroy(b);
+            return set_err(ctx, MCPD_EINVAL, "all instances of a batch must share coupled and systematic settings");
+        }
+        if (b->t[i].record_slots || b->t[i].trace_stride) {
+            mcpd_batch_destroy(b);
+            return set_err(ctx, MCPD_EINVAL, "batches keep no per-slot records or traces");
+        }
+    }
+    // Launch order: 0 = as given; 1 = costliest slots (horizon) first, so long slots start early.
+    b->order.resize(n_inst);
+    for (int32_t i = 0; i < n_inst; ++i) b->order[i] = i;
+    if (order_mode == 1)
+        std::stable_sort(b->order.begin(), b->order.end(), [&](int32_t a, int32_t c) {
+            return std::max(b->t[a].B, b->t[a].unit) > std::max(b->t[c].B, b->t[c].unit);
+        });
+    if (cudaSetDevice(ctx->device) != cudaSuccess) { mcpd_batch_destroy(b); return set_err(ctx, MCPD_ECUDA, "cudaSetDevice"); }
+    // Sizes.
+    size_t table_bytes = 0;
+    int32_t max_na = 0, max_W = 0, max_wpp = 0;
+    b->out_offset.assign(n_inst + 1, 0);
+    b->bucket_offset.assign(n_inst, 0);
+    b->count_offset.assign(n_inst, 0);
+    auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
+    for (int32_t i = 0; i < n_inst; ++i) {
+        const mcpd::Tables &t = b->t[i];
+        table_bytes += up16(t.alias.size() * 8) + up16(t.rows.size() * 2) + up16(t.T.size() * 8) + up16(t.Tnu.size() * 8);
+        max_na = std::max(max_na, t.na); max_W = std::max(max_W, t.W); max_wpp = std::max(max_wpp, t.wpp);
+        b->out_offset[i + 1] = b->out_offset[i] + t.na;
+        b->bucket_offset[i] = static_cast<int64_t>(b->total_bucket_words);
+        b->total_bucket_words += static_cast<size_t>(t.nb) * t.na;
+        b->count_offset[i] = static_cast<int64_t>(b->total_counts);
+        b->total_counts += static_cast<size_t>(t.nb);
+    }
+    b->total_active = b->out_offset[n_inst];
+    unsigned char *d_tables = nullptr;
+    int rc;
+#define BALLOC(ptr, n) do { if ((rc = balloc(ctx, b->allocs, &(ptr), (n))) != MCPD_OK) { mcpd_batch_destroy(b); return rc; } } while (0)
+    BALLOC(d_tables, table_bytes);
+    BALLOC(b->d_buckets, b->total_bucket_words * 3);
+    BALLOC(b->d_bcount, b->total_counts);
+    BALLOC(b->d_insts, static_cast<size_t>(n_inst));
+    BALLOC(b->d_clone_inst, static_cast<size_t>(b->total_active));
+    BALLOC(b->d_clone_local, static_cast<size_t>(b->total_active));
+    BALLOC(b->bp.counters, static_cast<size_t>(mcpd::kNumCounters));
+    BALLOC(b->bp.error, 1);
+#undef BALLOC
+    // Tables (host staging buffer, one copy) and descriptors in launch order.
+    std::vector<unsigned char> host(table_bytes, 0);
+    size_t off = 0;
+    b->insts.resize(n_inst);
+    long long work = 0;
+    for (int32_t pos = 0; pos < n_inst; ++pos) {
+        const int32_t i = b->order[pos];
+        const mcpd::Tables &t = b->t[i];
+        mcpd::InstDesc &d = b->insts[pos];
+        std::memset(&d, 0, sizeof(d));
+        auto put = [&](const void *src, size_t bytes) -> const void * {
+            if (bytes == 0) return nullptr;
+            std::memcpy(host.data() + off, src, bytes);
+            const void *dev = d_tables + off;
+            off += up16(bytes);
+            return dev;
+        };
+        d.alias = static_cast<const uint64_t *>(put(t.alias.data(), t.alias.size() * 8));
+        d.rows = static_cast<const uint16_t *>(put(t.rows.data(), t.rows.size() * 2));
+        d.T = static_cast<const uint64_t *>(put(t.T.data(), t.T.size() * 8));
+        d.Tnu = static_cast<const uint64_t *>(put(t.Tnu.data(), t.Tnu.size() * 8));
+        d.S1 = b->d_buckets + b->bucket_offset[i];
+        d.S2lo = b->d_buckets + b->total_bucket_words + b->bucket_offset[i];
+        d.S2hi = b->d_buckets + 2 * b->total_bucket_words + b->bucket_offset[i];
+        d.bcount = b->d_bcount + b->count_offset[i];
+        d.na = t.na; d.W = t.W; d.wpp = t.wpp; d.deg = t.deg_max; d.nb = static_cast<int32_t>(t.nb);
+        d.dummy_word_index = t.dummy_word_index; d.dummy_entry = t.dummy_entry; d.dummy_word = t.dummy_word;
+        d.P = t.P; d.B = t.B; d.k = t.k; d.ell = t.ell; d.L = t.L; d.burn = t.burn; d.length = t.length;
+        d.unit = t.unit; d.step_limit = t.step_limit; d.slot_offset = t.slot_offset;
+        d.work_begin = work; work += t.P;
+        d.seed = t.seed; d.instance = t.instance;
+    }
+    b->total_slots = work;
+    std::vector<int32_t> ci(b->total_active), cl(b->total_active);
+    for (int32_t i = 0; i < n_inst; ++i) {
+        int32_t pos = static_cast<int32_t>(std::find(b->order.begin(), b->order.end(), i) - b->order.begin());
+        for (int32_t a = 0; a < b->t[i].na; ++a) { ci[b->out_offset[i] + a] = pos; cl[b->out_offset[i] + a] = a; }
+    }
+    CU(cudaMemcpyAsync(d_tables, host.data(), table_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(b->d_insts, b->insts.data(), sizeof(mcpd::InstDesc) * n_inst, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(b->d_clone_inst, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(b->d_clone_local, cl.data(), cl.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    b->bp.insts = b->d_insts;
+    b->bp.n_inst = n_inst;
+    b->bp.coupled = b->t[0].coupled ? 1 : 0;
+    b->bp.scan = b->t[0].scan;
+    b->bp.max_wpp = max_wpp; b->bp.max_na = max_na; b->bp.max_W = max_W;
+    b->bp.total_work = work;
+    if ((rc = batch_shape(ctx, b, 0)) != MCPD_OK) { mcpd_batch_destroy(b); return rc; }
+    CU(cudaEventCreate(&b->ev0));
+    CU(cudaEventCreate(&b->ev1));
+    CU(cudaStreamSynchronize(ctx->stream));
+    *out = b;
+    return MCPD_OK;
+}
+
+int mcpd_batch_info(const mcpd_batch *b, int64_t info[16]) {
+    if (!b || !info) return MCPD_EINVAL;
+    std::memset(info, 0, 16 * sizeof(int64_t));
+    info[0] = b->total_active; info[1] = b->bp.n_inst; info[2] = b->total_slots; info[3] = b->bp.max_na;
+    info[4] = b->warps; info[5] = b->grid; info[6] = b->pairs; info[7] = static_cast<int64_t>(b->smem);
+    info[8] = 1;   // lanes per pair
+    return MCPD_OK;
+}
+
+int mcpd_batch_offsets(const mcpd_batch *b, int64_t *offsets) {
+    if (!b || !offsets) return MCPD_EINVAL;
+    std::memcpy(offsets, b->out_offset.data(), b->out_offset.size() * sizeof(int64_t));
+    return MCPD_OK;
+}
+
+int mcpd_batch_set_shape(mcpd_ctx *ctx, mcpd_batch *b, int32_t warps_per_block) {
+    if (!ctx || !b) return MCPD_EINVAL;
+    CU(cudaSetDevice(ctx->device));
+    return batch_shape(ctx, b, warps_per_block);
+}
+
+int mcpd_batch_run_async(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev) {
+    if (!ctx || !b || !est_dev || !se_dev) return MCPD_EINVAL;
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaEventRecord(b->ev0, ctx->stream));
+    const int rc = batch_enqueue(ctx, b, est_dev, se_dev, false);
+    if (rc != MCPD_OK) return rc;
+    CU(cudaEventRecord(b->ev1, ctx->stream));
+    b->dirty = true;
+    b->ran = true;
+    return MCPD_OK;
+}
+
+int mcpd_batch_capture_graph(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev) {
+    if (!ctx || !b || !est_dev || !se_dev) return MCPD_EINVAL;
+    CU(cudaSetDevice(ctx->device));
+    if (!ctx->stream) return set_err(ctx, MCPD_EINVAL, "graph capture needs a non-default stream");
+    if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = batch_enqueue(ctx, b, est_dev, se_dev, true);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (rc != MCPD_OK) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return set_err(ctx, MCPD_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    b->graph = g;
+    CU(cudaGraphInstantiate(&b->graph_exec, g, 0));
+    return MCPD_OK;
+}
+
+int mcpd_batch_launch_graph(mcpd_ctx *ctx, mcpd_batch *b) {
+    if (!ctx || !b || !b->graph_exec) return MCPD_EINVAL;
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaEventRecord(b->ev0, ctx->stream));
+    CU(cudaGraphLaunch(b->graph_exec, ctx->stream));
+    CU(cudaEventRecord(b->ev1, ctx->stream));
+    b->dirty = true;
+    b->ran = true;
+    return MCPD_OK;
+}
+
+int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *b, mcpd_stats *stats) {
+    if (!ctx || !b) return MCPD_EINVAL;
+    if (!b->ran) return set_err(ctx, MCPD_EINVAL, "no run to collect");
+    CU(cudaSetDevice(ctx->device));
+    unsigned long long c[mcpd::kNumCounters];
+    int error = 0;
+    CU(cudaMemcpyAsync(c, b->bp.counters, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(&error, b->bp.error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->progress_units = static_cast<int64_t>(c[mcpd::kProgress]);
+        stats->reps_started = static_cast<int64_t>(c[mcpd::kRepsStarted]);
+        stats->reps_retained = static_cast<int64_t>(c[mcpd::kRepsRetained]);
+        stats->reps_aborted = static_cast<int64_t>(c[mcpd::kRepsAborted]);
+        stats->zero_completion_slots = static_cast<int64_t>(c[mcpd::kZeroCompletion]);
+        stats->step_limit_hits = static_cast<int64_t>(c[mcpd::kStepLimitHits]);
+        stats->max_tau = static_cast<int64_t>(c[mcpd::kMaxTau]);
+        stats->sum_tau = static_cast<int64_t>(c[mcpd::kSumTau]);
+        stats->site_updates = b->bp.coupled ? 2 * stats->progress_units - stats->reps_started : stats->progress_units;
+        stats->n_buckets = static_cast<int64_t>(b->total_counts);
+        stats->n_active = b->total_active;
+        stats->kernel_ms = ms;
+    }
+    if (error) return set_err(ctx, MCPD_ESTEP_LIMIT, "a pair reached the step limit without meeting");
+    b->dirty = false;
+    return MCPD_OK;
+}
+
+int mcpd_batch_fetch(mcpd_ctx *ctx, const mcpd_batch *b, int32_t inst, int what, void *host_dst,
+                     size_t bytes) {
+    if (!ctx || !b || !host_dst || inst < 0 || inst >= b->bp.n_inst) return MCPD_EINVAL;
+    const mcpd::Tables &t = b->t[inst];
+    const size_t words = static_cast<size_t>(t.nb) * t.na;
+    const unsigned long long *src = nullptr;
+    size_t need = words * 8;
+    switch (what) {
+        case MCPD_FETCH_S1: src = b->d_buckets + b->bucket_offset[inst]; break;
+        case MCPD_FETCH_S2_LO: src = b->d_buckets + b->total_bucket_words + b->bucket_offset[inst]; break;
+        case MCPD_FETCH_S2_HI: src = b->d_buckets + 2 * b->total_bucket_words + b->bucket_offset[inst]; break;
+        case MCPD_FETCH_COUNT: src = b->d_bcount + b->count_offset[inst]; need = static_cast<size_t>(t.nb) * 8; break;
+        default: return set_err(ctx, MCPD_EINVAL, "batch fetch: buckets and counts only");
+    }
+    if (bytes != need) return set_err(ctx, MCPD_EINVAL, "batch fetch: wrong size");
+    CU(cudaSetDevice(ctx->device));
+    CU(cudaMemcpyAsync(host_dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    return MCPD_OK;
+}
+
+// Time each candidate launch shape on the batch itself (reps runs each after one warm-up run)
+// and keep the fastest.  times[c] receives the mean milliseconds of candidate c.
+int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *b, const int32_t *cand_warps, int32_t n_cand,
+                        int32_t reps, double *est_dev, double *se_dev, int32_t *best_warps,
+                        double *times) {
+    if (!ctx || !b || !cand_warps || n_cand < 1 || reps < 1 || !est_dev || !se_dev) return MCPD_EINVAL;
+    CU(cudaSetDevice(ctx->device));
+    const size_t per_warp = static_cast<size_t>(b->bp.max_wpp) * 128;
+    const int fit = static_cast<int>(std::min<size_t>(16, ctx->smem_optin / per_warp));
+    double best = 1e300;
+    int32_t best_w = 0;
+    for (int32_t c = 0; c < n_cand; ++c) {
+        const int w = cand_warps[c];
+        if (w < 1 || w > fit) { if (times) times[c] = -1.0; continue; }
+        int rc = batch_shape(ctx, b, w);
+        if (rc != MCPD_OK) return rc;
+        double total = 0.0;
+        for (int32_t r = 0; r <= reps; ++r) {
+            if ((rc = mcpd_batch_run_async(ctx, b, est_dev, se_dev)) != MCPD_OK) return rc;
+            mcpd_stats st;
+            if ((rc = mcpd_batch_collect(ctx, b, &st)) != MCPD_OK) return rc;
+            if (r > 0) total += st.kernel_ms;
+        }
+        const double mean = total / reps;
+        if (times) times[c] = mean;
+        if (mean < best) { best = mean; best_w = w; }
+    }
+    if (best_w == 0) return set_err(ctx, MCPD_EINVAL, "no candidate shape fits");
+    if (best_warps) *best_warps = best_w;
+    return batch_shape(ctx, b, best_w);
+}
+
+}  // extern "C"

@@ -93,7 +93,43 @@ struct KParams {
     uint32_t smem_tables;             // bytes of staged tables at the start of shared memory
 };
 
+// One instance of a batched launch (plain types; read by the kernels from global memory).
+struct InstDesc {
+    const uint64_t *alias;            // [na]
+    const uint16_t *rows;             // [na * kRow] count offsets for the interleaved pair layout
+    const uint64_t *T;                // [kTSide * kTSide]
+    const uint64_t *Tnu;              // [na] or null
+    unsigned long long *S1, *S2lo, *S2hi, *bcount;   // this instance's N*_p buckets
+    int32_t na, W, wpp, deg, nb, dummy_word_index;
+    uint32_t dummy_entry, dummy_word;
+    long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset;
+    long long work_begin;             // global index of this instance's first slot in the launch
+    unsigned long long seed;
+    uint32_t instance;
+    int32_t pad;
+};
+
+// Arguments of a batched launch.
+struct BParams {
+    const InstDesc *insts;
+    int32_t n_inst, coupled, scan, max_wpp;
+    long long total_work;
+    long long *rep_acc;               // [pairs][max_na]
+    long long *slot_acc;              // [pairs][max_na]
+    uint32_t *touched_rep;            // [pairs][max_W]
+    uint32_t *touched_slot;           // [pairs][max_W]
+    unsigned long long *counters;
+    int *error;
+    int32_t max_na, max_W;
+};
+
 // Launchers (mcpd_kernels.cu).
+int launch_batch(const BParams &bp, int grid, int block, size_t smem, void *stream);
+int set_batch_smem(size_t bytes);
+int batch_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm);
+int launch_finalize_batch(const InstDesc *insts, int n_inst, const int32_t *clone_inst,
+                          const int32_t *clone_local, long long total_clones, double *est,
+                          double *se, void *stream);
 int launch_pairs(const KParams &kp, int grid, int block, size_t smem, void *stream);
 int launch_finalize(const unsigned long long *S1, const unsigned long long *S2lo,
                     const unsigned long long *S2hi, int na, int nb, long long P, long long L,

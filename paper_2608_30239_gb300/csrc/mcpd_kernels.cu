@@ -33,69 +33,120 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
     return c;
 }
 
-// Prefix sums of the per-time weights of the estimator.  Swapping the sums in
+// The estimator's integer bookkeeping.  Swapping the sums in
 // L H_{k:l} = sum_{r=k}^{l} [X_r + sum_{s>=1} (X_{r+s} - Y_{r+s-1})] gives
 //   G_j = sum_{t=0}^{C} w(t) X_t[j] - sum_{t=0}^{C-1} w(t) Y_t[j],  w(t) = clamp(t - k + 1, 0, L),
 // so a chain whose bit j is 1 on the time interval [s, e] contributes +-(W(e) - W(s-1)) with
-// W(u) = sum_{v<=u} w(v).  Uncoupled (Algorithms 1/2) uses w(t) = 1{b <= t <= b + T - 1}.
-template <bool COUPLED>
-__device__ __forceinline__ long long wprefix(long long u, const KParams &p) {
-    if (COUPLED) {
-        if (u < p.k) return 0;
-        if (u <= p.ell) { const long long a = u - p.k + 1; return a * (a + 1) / 2; }
-        return p.L * (p.L + 1) / 2 + (u - p.ell) * p.L;
-    } else {
-        const long long v = u - p.burn + 1;
-        return v < 0 ? 0 : (v > p.length ? p.length : v);
-    }
-}
+// W(u) = sum_{v<=u} w(v) (quadratic, then linear).  Uncoupled chains (Algorithms 1/2) use
+// w(t) = 1{b <= t <= b + T - 1}.  The kernel adds -+W at every flip and closes the open intervals
+// at the end of a replication.
 
-__device__ __forceinline__ void bucket_add(const KParams &p, int bkt, int j, long long g) {
-    const size_t idx = static_cast<size_t>(bkt) * p.na + j;
-    atomicAdd(&p.S1[idx], static_cast<unsigned long long>(g));
+// Add G and G^2 (128-bit, carried into the high word) of one slot to bucket N*_p - 1.
+__device__ __forceinline__ void bucket_add(unsigned long long *S1, unsigned long long *S2lo,
+                                           unsigned long long *S2hi, int na, int bkt, int j, long long g) {
+    const size_t idx = static_cast<size_t>(bkt) * na + j;
+    atomicAdd(&S1[idx], static_cast<unsigned long long>(g));
     const unsigned long long a = static_cast<unsigned long long>(g < 0 ? -g : g);
     const unsigned long long lo = a * a, hi = __umul64hi(a, a);
-    const unsigned long long old = atomicAdd(&p.S2lo[idx], lo);
+    const unsigned long long old = atomicAdd(&S2lo[idx], lo);
     const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-    if (hi + carry) atomicAdd(&p.S2hi[idx], hi + carry);
+    if (hi + carry) atomicAdd(&S2hi[idx], hi + carry);
 }
 
-template <bool COUPLED, bool SYSTEMATIC>
-__global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
+// One persistent kernel for a single instance (BATCH = false: tables staged in shared memory,
+// parameters from KParams) or for many instances in one launch (BATCH = true: tables read through
+// the read-only cache from per-instance descriptors, work items (instance, slot) handed out
+// instance-major from one counter).
+template <bool COUPLED, bool SYSTEMATIC, bool BATCH>
+__global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int na = p.na;
-    uint4 *sRows = reinterpret_cast<uint4 *>(smem);
-    unsigned long long *sAlias = reinterpret_cast<unsigned long long *>(smem + static_cast<size_t>(na) * 16);
-    unsigned long long *sT = sAlias + na;
-    for (int i = threadIdx.x; i < na; i += blockDim.x) {
-        sRows[i] = reinterpret_cast<const uint4 *>(p.rows)[i];
-        sAlias[i] = p.alias[i];
-    }
-    for (int i = threadIdx.x; i < kTSide * kTSide; i += blockDim.x) sT[i] = p.T[i];
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *st = reinterpret_cast<uint32_t *>(smem + p.smem_tables) +
-                   static_cast<size_t>(warp) * 32 * p.wpp + lane;   // word w of this pair: st[w * 32]
-    unsigned char *cbase = reinterpret_cast<unsigned char *>(st);
-    // The pair's state starts empty, and every replication leaves it empty again.
-    for (int w = 0; w < p.wpp; ++w) st[w * 32] = 0u;
-    st[p.dummy_word_index * 32] = p.dummy_word;
+    uint4 *sRows = reinterpret_cast<uint4 *>(smem);
+    unsigned long long *sAlias = nullptr, *sT = nullptr;
+    uint32_t *st;
+    int wpp;
+    if constexpr (!BATCH) {
+        sAlias = reinterpret_cast<unsigned long long *>(smem + static_cast<size_t>(p.na) * 16);
+        sT = sAlias + p.na;
+        for (int i = threadIdx.x; i < p.na; i += blockDim.x) {
+            sRows[i] = reinterpret_cast<const uint4 *>(p.rows)[i];
+            sAlias[i] = p.alias[i];
+        }
+        for (int i = threadIdx.x; i < kTSide * kTSide; i += blockDim.x) sT[i] = p.T[i];
+        wpp = p.wpp;
+        st = reinterpret_cast<uint32_t *>(smem + p.smem_tables) + static_cast<size_t>(warp) * 32 * wpp + lane;
+    } else {
+        wpp = bp.max_wpp;
+        st = reinterpret_cast<uint32_t *>(smem) + static_cast<size_t>(warp) * 32 * wpp + lane;
+    }
+    unsigned char *cbase = reinterpret_cast<unsigned char *>(st);   // word w of this pair: st[w * 32]
+    for (int w = 0; w < wpp; ++w) st[w * 32] = 0u;                  // the pair's state starts empty
+    if constexpr (!BATCH) st[p.dummy_word_index * 32] = p.dummy_word;
     __syncthreads();
 
     const long long gpair = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-    long long *racc = p.rep_acc + gpair * na;
-    long long *sacc = p.slot_acc + gpair * na;
-    uint32_t *trep = p.touched_rep + gpair * p.W;
-    uint32_t *tslot = p.touched_slot + gpair * p.W;
-    const uint32_t k0 = static_cast<uint32_t>(p.seed), k1 = static_cast<uint32_t>(p.seed >> 32);
-    const uint32_t W = p.W;
-    const uint32_t B = static_cast<uint32_t>(p.B), unit = static_cast<uint32_t>(p.unit);
-    const uint32_t ell = static_cast<uint32_t>(p.ell), step_limit = static_cast<uint32_t>(p.step_limit);
-    const int deg = p.deg;
-    // Words that may hold a set bit or a touched clone are tracked in 64-bit register masks; one mask
-    // bit covers 2^gshift consecutive words.
-    uint32_t gshift = 0;
-    while (((W + (1u << gshift) - 1) >> gshift) > 64) ++gshift;
+    const int stride_na = BATCH ? bp.max_na : p.na, stride_W = BATCH ? bp.max_W : p.W;
+    long long *racc = (BATCH ? bp.rep_acc : p.rep_acc) + gpair * stride_na;
+    long long *sacc = (BATCH ? bp.slot_acc : p.slot_acc) + gpair * stride_na;
+    uint32_t *trep = (BATCH ? bp.touched_rep : p.touched_rep) + gpair * stride_W;
+    uint32_t *tslot = (BATCH ? bp.touched_slot : p.touched_slot) + gpair * stride_W;
+    unsigned long long *counters = BATCH ? bp.counters : p.counters;
+
+    // Per-instance values (fixed for a single instance, reloaded when a batched slot changes
+    // instance).
+    const uint4 *gRows = nullptr;
+    const unsigned long long *gAlias = nullptr, *gT = nullptr, *Tnu = nullptr;
+    unsigned long long *bS1 = nullptr, *bS2lo = nullptr, *bS2hi = nullptr, *bCount = nullptr;
+    int na = 0, deg = 0, dummy_word_index = 0;
+    uint32_t W = 0, B = 0, unit = 0, ell = 0, step_limit = 0, instance = 0, k0 = 0, k1 = 0;
+    uint32_t dummy_entry = 0, dummy_word = 0, gshift = 0;
+    long long kk = 0, LL = 0, burn = 0, length = 0, P = 0, slot_offset = 0, work_begin = 0, work_end = 0;
+    int cur = -1;
+    auto load_instance = [&](const InstDesc &d) {
+        gRows = reinterpret_cast<const uint4 *>(d.rows); gAlias = reinterpret_cast<const unsigned long long *>(d.alias);
+        gT = reinterpret_cast<const unsigned long long *>(d.T); Tnu = reinterpret_cast<const unsigned long long *>(d.Tnu);
+        bS1 = d.S1; bS2lo = d.S2lo; bS2hi = d.S2hi; bCount = d.bcount;
+        na = d.na; deg = d.deg; W = d.W; dummy_word_index = d.dummy_word_index;
+        dummy_entry = d.dummy_entry; dummy_word = d.dummy_word;
+        B = static_cast<uint32_t>(d.B); unit = static_cast<uint32_t>(d.unit); ell = static_cast<uint32_t>(d.ell);
+        step_limit = static_cast<uint32_t>(d.step_limit); instance = d.instance;
+        k0 = static_cast<uint32_t>(d.seed); k1 = static_cast<uint32_t>(d.seed >> 32);
+        kk = d.k; LL = d.L; burn = d.burn; length = d.length; P = d.P; slot_offset = d.slot_offset;
+        work_begin = d.work_begin; work_end = d.work_begin + d.P;
+        gshift = 0;
+        while (((W + (1u << gshift) - 1) >> gshift) > 64) ++gshift;
+    };
+    if constexpr (!BATCH) {
+        Tnu = reinterpret_cast<const unsigned long long *>(p.Tnu);
+        bS1 = p.S1; bS2lo = p.S2lo; bS2hi = p.S2hi; bCount = p.bcount;
+        na = p.na; deg = p.deg; W = p.W; dummy_word_index = p.dummy_word_index;
+        dummy_entry = p.dummy_entry; dummy_word = p.dummy_word;
+        B = static_cast<uint32_t>(p.B); unit = static_cast<uint32_t>(p.unit); ell = static_cast<uint32_t>(p.ell);
+        step_limit = static_cast<uint32_t>(p.step_limit); instance = p.instance;
+        k0 = static_cast<uint32_t>(p.seed); k1 = static_cast<uint32_t>(p.seed >> 32);
+        kk = p.k; LL = p.L; burn = p.burn; length = p.length; P = p.P; slot_offset = p.slot_offset;
+        while (((W + (1u << gshift) - 1) >> gshift) > 64) ++gshift;
+    }
+    auto rowAt = [&](uint32_t c) -> uint4 {
+        if constexpr (BATCH) return __ldg(gRows + c); else return sRows[c];
+    };
+    auto aliasAt = [&](uint32_t c) -> unsigned long long {
+        if constexpr (BATCH) return __ldg(gAlias + c); else return sAlias[c];
+    };
+    auto tAt = [&](uint32_t i) -> unsigned long long {
+        if constexpr (BATCH) return __ldg(gT + i); else return sT[i];
+    };
+    // Prefix sums of the estimator's per-time weights (see the comment on wprefix).
+    auto wpre = [&](long long u) -> long long {
+        if (COUPLED) {
+            if (u < kk) return 0;
+            if (u <= static_cast<long long>(ell)) { const long long a = u - kk + 1; return a * (a + 1) / 2; }
+            return LL * (LL + 1) / 2 + (u - static_cast<long long>(ell)) * LL;
+        } else {
+            const long long v = u - burn + 1;
+            return v < 0 ? 0 : (v > length ? length : v);
+        }
+    };
 
     bool alive = true;
     uint32_t slot_local = 0, slot_g = 0, r = 0, t = 0, S = 0, N = 0, tau = 0, D = 0;
@@ -107,12 +158,12 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
 
     // Add delta (mod 2^16; X count in the low byte, Y count in the high byte) to every pool of c.
     auto bump_counts = [&](uint32_t c, uint32_t delta) {
-        const uint4 row = sRows[c];
+        const uint4 row = rowAt(c);
         const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
                                  row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
 #pragma unroll
         for (int l = 0; l < kRow; ++l) {
-            if (l >= deg || ent[l] == p.dummy_entry) continue;
+            if (l >= deg || ent[l] == dummy_entry) continue;
             uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
             *cnt = static_cast<uint16_t>(*cnt + delta);
         }
@@ -123,17 +174,17 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
         abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
         ++c_started;
         ++reps_in_slot;
-        if (p.Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0
+        if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0
             for (int a = 0; a < na; a += 2) {
                 const uint4 b = philox10(make_uint4(static_cast<uint32_t>(a) >> 1, r, slot_g,
-                                                    p.instance | (1u << 24)), k0, k1);
+                                                    instance | (1u << 24)), k0, k1);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int c = a + h;
                     if (c >= na) break;
                     const unsigned long long u = h ? ((static_cast<unsigned long long>(b.z) << 32) | b.w)
                                                    : ((static_cast<unsigned long long>(b.x) << 32) | b.y);
-                    if (u < p.Tnu[c]) {
+                    if (u < Tnu[c]) {
                         const uint32_t q = c >> 5, bit = 1u << (c & 31);
                         st[(2 * q) * 32] |= bit;
                         if (COUPLED) st[(2 * q + 1) * 32] |= bit;
@@ -146,10 +197,27 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     };
 
     auto start_slot = [&]() {
-        const unsigned long long s = atomicAdd(&p.counters[kWork], 1ull);
-        if (s >= static_cast<unsigned long long>(p.P)) { alive = false; return; }
-        slot_local = static_cast<uint32_t>(s);
-        slot_g = static_cast<uint32_t>(p.slot_offset + static_cast<long long>(s));
+        const unsigned long long s = atomicAdd(&counters[kWork], 1ull);
+        if constexpr (BATCH) {
+            if (s >= static_cast<unsigned long long>(bp.total_work)) { alive = false; return; }
+            const long long w = static_cast<long long>(s);
+            if (cur < 0 || w < work_begin || w >= work_end) {
+                int lo = 0, hi = bp.n_inst - 1;             // last instance with work_begin <= w
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (bp.insts[mid].work_begin <= w) lo = mid; else hi = mid - 1;
+                }
+                if (cur >= 0) st[dummy_word_index * 32] = 0u;   // the old layout's padding pool
+                cur = lo;
+                load_instance(bp.insts[cur]);
+                st[dummy_word_index * 32] = dummy_word;
+            }
+            slot_local = static_cast<uint32_t>(w - work_begin);
+        } else {
+            if (s >= static_cast<unsigned long long>(P)) { alive = false; return; }
+            slot_local = static_cast<uint32_t>(s);
+        }
+        slot_g = static_cast<uint32_t>(slot_offset + static_cast<long long>(slot_local));
         S = 0; N = 0; r = 0; reps_in_slot = 0;
         start_rep();
     };
@@ -157,8 +225,8 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     // End of a replication: empty the pair's state and the replication's accumulators; when `move`,
     // first close the open intervals at C and add the replication's G into the slot's sums.
     auto finish_rep = [&](bool move, uint32_t C) {
-        const long long wX = move ? wprefix<COUPLED>(C, p) : 0;
-        const long long wY = (move && COUPLED) ? wprefix<COUPLED>(static_cast<long long>(C) - 1, p) : 0;
+        const long long wX = move ? wpre(C) : 0;
+        const long long wY = (move && COUPLED) ? wpre(static_cast<long long>(C) - 1) : 0;
         unsigned long long groups = rep_words;
         while (groups) {
             const int g = __ffsll(static_cast<long long>(groups)) - 1;
@@ -201,8 +269,10 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     auto end_slot = [&](bool valid) {
         const int bkt = static_cast<int>(N) - 1;
         long long *tr = nullptr;
-        if (valid && p.trace_stride > 0 && (slot_local % p.trace_stride) == 0)
-            tr = p.trace_G + (static_cast<long long>(slot_local) / p.trace_stride) * na;
+        if constexpr (!BATCH) {
+            if (valid && p.trace_stride > 0 && (slot_local % p.trace_stride) == 0)
+                tr = p.trace_G + (static_cast<long long>(slot_local) / p.trace_stride) * na;
+        }
         unsigned long long groups = slot_words;
         while (groups) {
             const int g = __ffsll(static_cast<long long>(groups)) - 1;
@@ -219,7 +289,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
                     const long long gsum = sacc[j];
                     sacc[j] = 0;
                     if (valid && gsum != 0) {
-                        bucket_add(p, bkt, static_cast<int>(j), gsum);
+                        bucket_add(bS1, bS2lo, bS2hi, na, bkt, static_cast<int>(j), gsum);
                         if (tr) tr[j] = gsum;
                     }
                 }
@@ -227,11 +297,13 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
             }
         }
         slot_words = 0;
-        if (valid) atomicAdd(&p.bcount[bkt], 1ull);
-        if (p.slot_nstar) {
-            p.slot_nstar[slot_local] = valid ? static_cast<int32_t>(N) : 0;
-            p.slot_S[slot_local] = S;
-            p.slot_reps[slot_local] = static_cast<int32_t>(reps_in_slot);
+        if (valid) atomicAdd(&bCount[bkt], 1ull);
+        if constexpr (!BATCH) {
+            if (p.slot_nstar) {
+                p.slot_nstar[slot_local] = valid ? static_cast<int32_t>(N) : 0;
+                p.slot_S[slot_local] = S;
+                p.slot_reps[slot_local] = static_cast<int32_t>(reps_in_slot);
+            }
         }
         start_slot();
     };
@@ -261,7 +333,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     auto limit_hit = [&]() {
         c_prog += t;
         ++c_limit;
-        atomicExch(p.error, 1);
+        atomicExch(BATCH ? bp.error : p.error, 1);
         finish_rep(false, 0);
         end_slot(false);
     };
@@ -286,7 +358,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
         if (SYSTEMATIC) return sysI;
         const unsigned long long prod = static_cast<unsigned long long>(ws) * static_cast<uint32_t>(na);
         const uint32_t col = static_cast<uint32_t>(prod >> 32), coin = static_cast<uint32_t>(prod);
-        const unsigned long long e = sAlias[col];
+        const unsigned long long e = aliasAt(col);
         return coin < static_cast<uint32_t>(e) ? col : static_cast<uint32_t>(e >> 32);
     };
 
@@ -295,7 +367,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     // together).  Uncoupled chains always take this path.
     auto step_fast = [&](uint32_t ws, uint32_t wu) -> int {
         const uint32_t I = draw_site(ws);
-        const uint4 row = sRows[I];
+        const uint4 row = rowAt(I);
         const uint32_t q = I >> 5, bit = 1u << (I & 31);
         uint32_t *px = st + (2 * q) * 32;
         const uint32_t xw = px[0];
@@ -311,11 +383,11 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
                 if (c == xI) ix += (e & 1u) ? 9u : 1u;           // c_j - x_I = 0: pool j decides
             }
         }
-        const unsigned long long TX = sT[ix];
+        const unsigned long long TX = tAt(ix);
         const uint32_t thx = static_cast<uint32_t>(TX >> 32);
         uint32_t nX = wu < thx ? 1u : 0u;
         if (wu == thx) {                                        // the low half of U decides
-            const uint32_t lo = philox10(make_uint4(t, r, slot_g, p.instance | (2u << 24)), k0, k1).x;
+            const uint32_t lo = philox10(make_uint4(t, r, slot_g, instance | (2u << 24)), k0, k1).x;
             nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
         }
         if (nX != xI) {
@@ -325,21 +397,21 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
             const uint32_t delta = nX ? (both ? 0x0101u : 0x0001u) : (both ? 0xFEFFu : 0xFFFFu);
 #pragma unroll
             for (int l = 0; l < kRow; ++l) {
-                if (l >= deg || ent[l] == p.dummy_entry) continue;
+                if (l >= deg || ent[l] == dummy_entry) continue;
                 uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
                 *cnt = static_cast<uint16_t>(*cnt + delta);
             }
             long long w;
             if (COUPLED) {
                 if (both) {                                      // W(t) - W(t-1): X at t+1, Y at t
-                    const long long a = static_cast<long long>(t) - p.k + 1;
-                    w = a < 0 ? 0 : (a > p.L ? p.L : a);
+                    const long long a = static_cast<long long>(t) - kk + 1;
+                    w = a < 0 ? 0 : (a > LL ? LL : a);
                 } else {
-                    w = wprefix<true>(0, p);                     // X_1 only
+                    w = wpre(0);                                 // X_1 only
                     D = 1;
                 }
             } else {
-                w = wprefix<false>(t, p);
+                w = wpre(t);
             }
             if (w != 0) {
                 atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]),
@@ -354,7 +426,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     // One coupled step for a pair that has not met: both chains read their own state.
     auto step_full = [&](uint32_t ws, uint32_t wu) -> int {
         const uint32_t I = draw_site(ws);
-        const uint4 row = sRows[I];
+        const uint4 row = rowAt(I);
         const uint32_t q = I >> 5, bit = 1u << (I & 31);
         uint32_t *px = st + (2 * q) * 32;
         const uint32_t xw = px[0], yw = px[32];
@@ -374,11 +446,11 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
                 if ((d & 0xFF00u) == 0) iy += code;
             }
         }
-        const unsigned long long TX = sT[ix], TY = sT[iy];
+        const unsigned long long TX = tAt(ix), TY = tAt(iy);
         const uint32_t thx = static_cast<uint32_t>(TX >> 32), thy = static_cast<uint32_t>(TY >> 32);
         uint32_t nX = wu < thx ? 1u : 0u, nY = wu < thy ? 1u : 0u;
         if (wu == thx || wu == thy) {
-            const uint32_t lo = philox10(make_uint4(t, r, slot_g, p.instance | (2u << 24)), k0, k1).x;
+            const uint32_t lo = philox10(make_uint4(t, r, slot_g, instance | (2u << 24)), k0, k1).x;
             if (wu == thx) nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
             if (wu == thy) nY = lo < static_cast<uint32_t>(TY) ? 1u : 0u;
         }
@@ -390,13 +462,13 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
             const uint32_t delta = (fx ? (nX ? 0x0001u : 0xFFFFu) : 0u) + (fy ? (nY ? 0x0100u : 0xFF00u) : 0u);
 #pragma unroll
             for (int l = 0; l < kRow; ++l) {
-                if (l >= deg || ent[l] == p.dummy_entry) continue;
+                if (l >= deg || ent[l] == dummy_entry) continue;
                 uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
                 *cnt = static_cast<uint16_t>(*cnt + delta);
             }
             long long ev = 0;
-            if (fx) { const long long w = wprefix<true>(t, p); ev += nX ? -w : w; }             // X_{t+1}
-            if (fy) { const long long w = wprefix<true>(static_cast<long long>(t) - 1, p); ev += nY ? w : -w; }  // Y_t
+            if (fx) { const long long w = wpre(t); ev += nX ? -w : w; }                           // X_{t+1}
+            if (fy) { const long long w = wpre(static_cast<long long>(t) - 1); ev += nY ? w : -w; }  // Y_t
             if (ev != 0) {
                 atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]), static_cast<unsigned long long>(ev));
                 atomicOr(&trep[q], bit);
@@ -408,11 +480,11 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
     };
 
     start_slot();
-    uint4 blk = philox10(make_uint4(t >> 1, r, slot_g, p.instance), k0, k1);
+    uint4 blk = philox10(make_uint4(t >> 1, r, slot_g, instance), k0, k1);
     while (alive) {
         // one Philox block per pair of steps, words (0,1) at even t and (2,3) at odd t; the next
         // block is computed ahead and discarded if the replication ends
-        const uint4 nxt = philox10(make_uint4((t >> 1) + 1, r, slot_g, p.instance), k0, k1);
+        const uint4 nxt = philox10(make_uint4((t >> 1) + 1, r, slot_g, instance), k0, k1);
         int ended = 0;
 #pragma unroll 1
         for (int h = 0; h < 2 && !ended; ++h) {
@@ -424,30 +496,28 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p) {
             if (ended == 1) complete();
             else if (ended == 2) abort_rep();
             else limit_hit();
-            blk = philox10(make_uint4(t >> 1, r, slot_g, p.instance), k0, k1);
+            blk = philox10(make_uint4(t >> 1, r, slot_g, instance), k0, k1);
         } else {
             blk = nxt;
         }
     }
 
-    if (c_prog) atomicAdd(&p.counters[kProgress], c_prog);
-    if (c_started) atomicAdd(&p.counters[kRepsStarted], c_started);
-    if (c_retained) atomicAdd(&p.counters[kRepsRetained], c_retained);
-    if (c_aborted) atomicAdd(&p.counters[kRepsAborted], c_aborted);
-    if (c_zero) atomicAdd(&p.counters[kZeroCompletion], c_zero);
-    if (c_limit) atomicAdd(&p.counters[kStepLimitHits], c_limit);
-    if (c_sumtau) atomicAdd(&p.counters[kSumTau], c_sumtau);
-    if (c_maxtau) atomicMax(&p.counters[kMaxTau], static_cast<unsigned long long>(c_maxtau));
+    if (c_prog) atomicAdd(&counters[kProgress], c_prog);
+    if (c_started) atomicAdd(&counters[kRepsStarted], c_started);
+    if (c_retained) atomicAdd(&counters[kRepsRetained], c_retained);
+    if (c_aborted) atomicAdd(&counters[kRepsAborted], c_aborted);
+    if (c_zero) atomicAdd(&counters[kZeroCompletion], c_zero);
+    if (c_limit) atomicAdd(&counters[kStepLimitHits], c_limit);
+    if (c_sumtau) atomicAdd(&counters[kSumTau], c_sumtau);
+    if (c_maxtau) atomicMax(&counters[kMaxTau], static_cast<unsigned long long>(c_maxtau));
 }
 
 // theta_j = (sum_{n ascending} S1[n][j] / n) / (P L);  Q_j = (sum_n S2[n][j] / n^2) / L^2;
 // se_j = sqrt(max(0, (Q_j - (P theta_j) theta_j) / (P (P - 1)))).  Every operation is an
 // explicitly rounded IEEE double operation, in this order.
-__global__ void finalize_kernel(const unsigned long long *S1, const unsigned long long *S2lo,
-                                const unsigned long long *S2hi, int na, int nb, long long P,
-                                long long L, double *est, double *se) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= na) return;
+__device__ __forceinline__ void finalize_one(const unsigned long long *S1, const unsigned long long *S2lo,
+                                             const unsigned long long *S2hi, int na, int nb, long long P,
+                                             long long L, int j, double *est, double *se) {
     const double dP = static_cast<double>(P), dL = static_cast<double>(L);
     double s1 = 0.0, s2 = 0.0;
     for (int b = 0; b < nb; ++b) {
@@ -459,12 +529,30 @@ __global__ void finalize_kernel(const unsigned long long *S1, const unsigned lon
         s2 = __dadd_rn(s2, __ddiv_rn(sq, __dmul_rn(n, n)));
     }
     const double th = __ddiv_rn(s1, __dmul_rn(dP, dL));
-    est[j] = th;
-    if (P < 2) { se[j] = __longlong_as_double(0x7FF8000000000000LL); return; }
+    *est = th;
+    if (P < 2) { *se = __longlong_as_double(0x7FF8000000000000LL); return; }
     const double Q = __ddiv_rn(s2, __dmul_rn(dL, dL));
     const double var = __ddiv_rn(__dsub_rn(Q, __dmul_rn(__dmul_rn(dP, th), th)),
                                  __dmul_rn(dP, __dsub_rn(dP, 1.0)));
-    se[j] = var > 0.0 ? __dsqrt_rn(var) : 0.0;
+    *se = var > 0.0 ? __dsqrt_rn(var) : 0.0;
+}
+
+__global__ void finalize_kernel(const unsigned long long *S1, const unsigned long long *S2lo,
+                                const unsigned long long *S2hi, int na, int nb, long long P,
+                                long long L, double *est, double *se) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= na) return;
+    finalize_one(S1, S2lo, S2hi, na, nb, P, L, j, &est[j], &se[j]);
+}
+
+// Batched finalize: one thread per (instance, clone), outputs concatenated in instance order.
+__global__ void finalize_batch_kernel(const InstDesc *insts, const int32_t *clone_inst,
+                                      const int32_t *clone_local, long long total, double *est,
+                                      double *se) {
+    const long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const InstDesc &d = insts[clone_inst[g]];
+    finalize_one(d.S1, d.S2lo, d.S2hi, d.na, d.nb, d.P, d.L, clone_local[g], &est[g], &se[g]);
 }
 
 __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, long long n) {
@@ -475,23 +563,36 @@ __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uin
     out[4 * i] = o.x; out[4 * i + 1] = o.y; out[4 * i + 2] = o.z; out[4 * i + 3] = o.w;
 }
 
-using PairsFn = void (*)(const KParams);
+using PairsFn = void (*)(const KParams, const BParams);
 
-PairsFn pick(int coupled, int scan) {
-    if (coupled) return pairs_kernel<true, false>;
-    return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true> : pairs_kernel<false, false>;
+PairsFn pick(int coupled, int scan, bool batch) {
+    if (batch) {
+        if (coupled) return pairs_kernel<true, false, true>;
+        return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true, true> : pairs_kernel<false, false, true>;
+    }
+    if (coupled) return pairs_kernel<true, false, false>;
+    return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true, false> : pairs_kernel<false, false, false>;
+}
+
+int set_smem(size_t bytes, bool batch) {
+    for (int c = 0; c < 2; ++c)
+        for (int sc : {MCPD_SCAN_SCORE, MCPD_SCAN_SYSTEMATIC}) {
+            if (c && sc == MCPD_SCAN_SYSTEMATIC) continue;
+            if (cudaFuncSetAttribute(pick(c, sc, batch), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(bytes)) != cudaSuccess)
+                return MCPD_ECUDA;
+        }
+    return MCPD_OK;
 }
 
 }  // namespace
 
 int set_pairs_smem(size_t bytes, int coupled) {
-    const PairsFn fns[3] = {pairs_kernel<true, false>, pairs_kernel<false, true>, pairs_kernel<false, false>};
     (void)coupled;
-    for (PairsFn f : fns)
-        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes)) != cudaSuccess)
-            return MCPD_ECUDA;
-    return MCPD_OK;
+    return set_smem(bytes, false);
 }
+
+int set_batch_smem(size_t bytes) { return set_smem(bytes, true); }
 
 int pairs_max_smem(int device, size_t *bytes) {
     int v = 0;
@@ -502,8 +603,24 @@ int pairs_max_smem(int device, size_t *bytes) {
 }
 
 int launch_pairs(const KParams &kp, int grid, int block, size_t smem, void *stream) {
-    PairsFn f = pick(kp.coupled, kp.scan);
-    f<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(kp);
+    const BParams none{};
+    pick(kp.coupled, kp.scan, false)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(kp, none);
+    return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
+}
+
+int launch_batch(const BParams &bp, int grid, int block, size_t smem, void *stream) {
+    const KParams none{};
+    pick(bp.coupled, bp.scan, true)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(none, bp);
+    return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
+}
+
+int launch_finalize_batch(const InstDesc *insts, int n_inst, const int32_t *clone_inst,
+                          const int32_t *clone_local, long long total_clones, double *est,
+                          double *se, void *stream) {
+    (void)n_inst;
+    if (total_clones <= 0) return MCPD_OK;
+    finalize_batch_kernel<<<static_cast<unsigned>((total_clones + 127) / 128), 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        insts, clone_inst, clone_local, total_clones, est, se);
     return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
 }
 
@@ -521,7 +638,12 @@ int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, 
 }
 
 int pairs_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(coupled, scan), block, smem) == cudaSuccess
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(coupled, scan, false), block, smem) == cudaSuccess
+               ? MCPD_OK : MCPD_ECUDA;
+}
+
+int batch_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(coupled, scan, true), block, smem) == cudaSuccess
                ? MCPD_OK : MCPD_ECUDA;
 }
 

@@ -97,6 +97,17 @@ def lib(build_if_missing: bool = False):
             "mcpd_philox_device": (C.c_int, [P, P, C.c_uint32, C.c_uint32, P, I64]),
             "mcpd_decode_noalloc": (C.c_int, [P, C.POINTER(mcpd_design), P, C.POINTER(mcpd_params),
                                               P, P, C.POINTER(mcpd_stats)]),
+            "mcpd_batch_create": (C.c_int, [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(P)]),
+            "mcpd_batch_destroy": (None, [P]),
+            "mcpd_batch_info": (C.c_int, [P, P]),
+            "mcpd_batch_offsets": (C.c_int, [P, P]),
+            "mcpd_batch_set_shape": (C.c_int, [P, P, C.c_int32]),
+            "mcpd_batch_run_async": (C.c_int, [P, P, P, P]),
+            "mcpd_batch_capture_graph": (C.c_int, [P, P, P, P]),
+            "mcpd_batch_launch_graph": (C.c_int, [P, P]),
+            "mcpd_batch_collect": (C.c_int, [P, P, C.POINTER(mcpd_stats)]),
+            "mcpd_batch_fetch": (C.c_int, [P, P, C.c_int32, C.c_int, P, C.c_size_t]),
+            "mcpd_batch_autotune": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -306,6 +317,98 @@ class Plan:
     def close(self):
         if getattr(self, "h", None):
             lib().mcpd_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """mcpd_batch: many instances (each with its own parameters) decoded in one persistent launch.
+
+    `instances` is a list of synth-like instances; `params` a list of keyword dicts (one per
+    instance) or one dict for all.  Outputs of run()/fetch are concatenated in input order;
+    `offsets[i]:offsets[i+1]` belong to instance i."""
+
+    def __init__(self, ctx: Context, instances, params, order_mode=0):
+        self.ctx = ctx
+        n = len(instances)
+        if isinstance(params, dict):
+            params = [params] * n
+        self._keep = _Keep()
+        designs = (mcpd_design * n)()
+        ys = (C.c_void_p * n)()
+        prms = (mcpd_params * n)()
+        for i, (inst, kw) in enumerate(zip(instances, params)):
+            d, y = make_design(inst, self._keep)
+            designs[i] = d
+            ys[i] = _ptr(y).value
+            prms[i] = make_params(inst, self._keep, **kw)
+        h = C.c_void_p()
+        ctx.check(lib().mcpd_batch_create(ctx.h, n, designs, ys, prms, int(order_mode), C.byref(h)),
+                  "mcpd_batch_create")
+        self.h = h
+        self.n_inst = n
+        self.info = self._info()
+        self.total_active = int(self.info[0])
+        self.offsets = np.zeros(n + 1, np.int64)
+        lib().mcpd_batch_offsets(h, _ptr(self.offsets))
+        self.nb = [int(mcpd_inspect(inst, **kw)["info"][1]) for inst, kw in zip(instances, params)]
+        self.na = [int(v) for v in np.diff(self.offsets)]
+
+    def _info(self):
+        info = np.zeros(16, np.int64)
+        lib().mcpd_batch_info(self.h, _ptr(info))
+        return info
+
+    def set_shape(self, warps_per_block):
+        self.ctx.check(lib().mcpd_batch_set_shape(self.ctx.h, self.h, int(warps_per_block)),
+                       "mcpd_batch_set_shape")
+        self.info = self._info()
+
+    def run_async(self, est_dev, se_dev):
+        self.ctx.check(lib().mcpd_batch_run_async(self.ctx.h, self.h, _ptr(est_dev), _ptr(se_dev)),
+                       "mcpd_batch_run_async")
+
+    def capture_graph(self, est_dev, se_dev):
+        self.ctx.check(lib().mcpd_batch_capture_graph(self.ctx.h, self.h, _ptr(est_dev), _ptr(se_dev)),
+                       "mcpd_batch_capture_graph")
+
+    def launch_graph(self):
+        self.ctx.check(lib().mcpd_batch_launch_graph(self.ctx.h, self.h), "mcpd_batch_launch_graph")
+
+    def collect(self):
+        st = mcpd_stats()
+        self.ctx.check(lib().mcpd_batch_collect(self.ctx.h, self.h, C.byref(st)), "mcpd_batch_collect")
+        return st.as_dict()
+
+    def buckets(self, i):
+        out = {}
+        for key, what, dt in (("S1", MCPD_FETCH_S1, np.int64), ("S2_lo", MCPD_FETCH_S2_LO, np.uint64),
+                              ("S2_hi", MCPD_FETCH_S2_HI, np.uint64), ("count", MCPD_FETCH_COUNT, np.int64)):
+            n = self.nb[i] * (1 if what == MCPD_FETCH_COUNT else self.na[i])
+            a = np.zeros(n, dt)
+            self.ctx.check(lib().mcpd_batch_fetch(self.ctx.h, self.h, i, what, _ptr(a), a.nbytes),
+                           "mcpd_batch_fetch")
+            out[key] = a if what == MCPD_FETCH_COUNT else a.reshape(self.nb[i], self.na[i])
+        return out
+
+    def autotune(self, est_dev, se_dev, candidates=(4, 6, 8, 12, 16), reps=1):
+        cand = np.asarray(candidates, np.int32)
+        times = np.zeros(len(cand))
+        best = C.c_int32()
+        self.ctx.check(lib().mcpd_batch_autotune(self.ctx.h, self.h, _ptr(cand), len(cand), int(reps),
+                                                 _ptr(est_dev), _ptr(se_dev), C.byref(best), _ptr(times)),
+                       "mcpd_batch_autotune")
+        self.info = self._info()
+        return int(best.value), dict(zip((int(c) for c in cand), (float(t) for t in times)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mcpd_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

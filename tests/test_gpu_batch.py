@@ -1,0 +1,163 @@
+"""Batched decoding (many instances of uneven size in one launch) vs the CPU oracle, through the
+C ABI (needs a GB300).  Each instance's integer bucket sums and finalized doubles must equal the
+oracle's for that instance alone; graph replay, other launch shapes and another work order must
+not change a bit."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+THREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2608_30239_gb300 import build, mcpd
+    build.build()
+    stream = torch.cuda.Stream()
+    c = mcpd.Context(0, stream=stream)
+    c.torch_stream = stream
+    yield c
+    c.close()
+
+
+def _uneven(count=7, seed=3):
+    rng = synth.SplitMix64(seed)
+    out = []
+    for i in range(count):
+        n = int(30 + rng.below(1, 570)[0])
+        m = max(6, int(n / 13 + 0.5))
+        k = int(3 + rng.below(1, 6)[0])
+        npos = int(1 + rng.below(1, 4)[0])
+        fp = 0.02 + 0.08 * float(rng.uniform(1)[0])
+        fn = 0.05 + 0.15 * float(rng.uniform(1)[0])
+        out.append(synth.make_instance(n, m, min(k, m), npos, fp, fn, npos / n, 900 + i, 950 + i))
+    return out
+
+
+def _params(insts, coupled=True):
+    ps = []
+    for i, inst in enumerate(insts):
+        k, ell = oracle.window_defaults(inst.n, 1)
+        if coupled:
+            ps.append(dict(slots=300 + 97 * i, k=k, ell=ell, horizon=3 * ell + 11 * i, seed=77 + i,
+                           instance_id=i))
+        else:
+            ps.append(dict(slots=200 + 31 * i, coupled=False, burn=k - 1, length=ell - k + 1,
+                           horizon=4 * ell, seed=5 + i, instance_id=i))
+    return ps
+
+
+def _oracle(inst, kw):
+    M = oracle.Model(inst)
+    if kw.get("coupled", True):
+        run = oracle.coupled_run(kw["k"], kw["ell"], kw["horizon"], kw["seed"], instance=kw["instance_id"])
+        L = kw["ell"] - kw["k"] + 1
+    else:
+        run = oracle.uncoupled_run(kw["burn"], kw["length"], kw["horizon"], kw["seed"],
+                                   instance=kw["instance_id"])
+        L = kw["length"]
+    res = M.run_slots(run, 0, kw["slots"], THREADS)
+    res["est"], res["se"] = M.finalize(res, kw["slots"], L)
+    return res
+
+
+def _run(ctx, batch):
+    import torch
+    est = torch.empty(batch.total_active, dtype=torch.float64, device="cuda:0")
+    se = torch.empty_like(est)
+    with torch.cuda.stream(ctx.torch_stream):
+        batch.run_async(est, se)
+        st = batch.collect()
+    return est.cpu().numpy(), se.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("coupled", [True, False])
+def test_batch_matches_oracle_per_instance(ctx, coupled):
+    from paper_2608_30239_gb300 import mcpd
+    insts = _uneven()
+    ps = _params(insts, coupled)
+    batch = mcpd.Batch(ctx, insts, ps)
+    est, se, st = _run(ctx, batch)
+    assert st["reps_retained"] > 0
+    for i, (inst, kw) in enumerate(zip(insts, ps)):
+        ref = _oracle(inst, kw)
+        got = batch.buckets(i)
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(est[a:b], ref["est"]), i
+        assert np.array_equal(se[a:b], ref["se"]), i
+    batch.close()
+
+
+def test_graph_shapes_and_order_do_not_change_results(ctx):
+    import torch
+    from paper_2608_30239_gb300 import mcpd
+    insts = _uneven(5, seed=9)
+    ps = _params(insts)
+    batch = mcpd.Batch(ctx, insts, ps)
+    e0, s0, _ = _run(ctx, batch)
+    est = torch.empty(batch.total_active, dtype=torch.float64, device="cuda:0")
+    se = torch.empty_like(est)
+    with torch.cuda.stream(ctx.torch_stream):
+        batch.capture_graph(est, se)
+        for _ in range(2):
+            est.zero_()
+            batch.launch_graph()
+            batch.collect()
+            assert np.array_equal(est.cpu().numpy(), e0)
+            assert np.array_equal(se.cpu().numpy(), s0)
+        best, times = batch.autotune(est, se, candidates=(2, 4, 8), reps=1)
+    assert best in (2, 4, 8) and all(t > 0 for t in times.values())
+    e1, s1, _ = _run(ctx, batch)
+    assert np.array_equal(e1, e0) and np.array_equal(s1, s0)
+    other = mcpd.Batch(ctx, insts, ps, order_mode=1)
+    e2, s2, _ = _run(ctx, other)
+    assert np.array_equal(e2, e0) and np.array_equal(s2, s0)
+    batch.close()
+    other.close()
+
+
+def test_batch_of_one_equals_single_instance_plan(ctx):
+    import torch
+    from paper_2608_30239_gb300 import mcpd
+    inst = synth.high_noise_config()
+    kw = dict(slots=2000, budget_site_updates=4e10 * 2000 / 524288, seed=20260)
+    batch = mcpd.Batch(ctx, [inst], [kw])
+    e, s, st = _run(ctx, batch)
+    plan = mcpd.Plan(ctx, inst, **kw)
+    pe = torch.empty(plan.n_active, dtype=torch.float64, device="cuda:0")
+    ps = torch.empty_like(pe)
+    with torch.cuda.stream(ctx.torch_stream):
+        plan.run_async(pe, ps)
+        pst = plan.collect()
+    assert np.array_equal(pe.cpu().numpy(), e) and np.array_equal(ps.cpu().numpy(), s)
+    assert pst["site_updates"] == st["site_updates"]
+    batch.close()
+    plan.close()
+
+
+def test_paper_sized_batch_runs(ctx):
+    """32 instances drawn like the 512-instance workload (n in [200, 5000]), 256 slots each, 20
+    sweeps of horizon: completes, every instance finite, sampled instances match the oracle."""
+    from paper_2608_30239_gb300 import mcpd
+    insts = synth.batched_configs(32, seed=11)
+    ps = [dict(slots=256, horizon=20 * inst.n, seed=1000 + i, instance_id=i) for i, inst in enumerate(insts)]
+    batch = mcpd.Batch(ctx, insts, ps, order_mode=1)
+    est, se, st = _run(ctx, batch)
+    assert np.all(np.isfinite(est)) and np.all(se >= 0)
+    for i in (0, 7):
+        inst = insts[i]
+        k, ell = oracle.window_defaults(inst.n, 1)
+        ref = _oracle(inst, dict(ps[i], k=k, ell=ell))
+        got = batch.buckets(i)
+        assert np.array_equal(got["S1"], ref["S1"]) and np.array_equal(got["count"], ref["count"])
+    batch.close()
