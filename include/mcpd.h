@@ -207,6 +207,44 @@ int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *batch, const int32_t *cand_wa
                         int32_t n_cand, int32_t reps, double *est_dev, double *se_dev,
                         int32_t *best_warps, double *times);
 
+/* ---- Learned scan weights and initial marginals ----------------------------------------------
+ * Not in the paper, which proves that any fixed positive scan weights keep pi invariant
+ * (Proposition 1) and that the coupled estimator is unbiased from any initial distribution
+ * (Theorem 1).  These calls compute 16 per-clone features of a design, run a 16-64-64-2 MLP
+ * (ReLU; parameters stored as bf16, arithmetic in fp32) and train it with Adam; its two heads give
+ * scan weights w = 0.5 softmax(o_1) + 0.5/n per instance and initial marginals
+ * nu = clamp(sigmoid(o_2), 1e-6, 1 - 1e-6), which mcpd_params.scan_weights / init_marginals
+ * accept.  Parameter layout (mcpd_mlp_num_params() = 5378 values): W1 [64][16], b1 [64],
+ * W2 [64][64], b2 [64], W3 [2][64], b3 [2].  All arrays are device arrays; work is enqueued on the
+ * context's stream (mcpd_features_batch synchronises). */
+int mcpd_mlp_num_params(void);
+/* Features of every clone of every instance (no pruning), rows concatenated in instance order.
+ * rates: [n_inst][3] host (fp, fn, prior_q); feat_dev: [sum n_clones][16] float.  Temporary
+ * device buffers are allocated and freed inside. */
+int mcpd_features_batch(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
+                        const uint8_t *const *ys, const double *rates, float *feat_dev);
+/* Out[r][2] = MLP(X[r][16]) for n_rows rows; W: [5378] bf16 bit patterns. */
+int mcpd_mlp_forward(mcpd_ctx *ctx, int64_t n_rows, const float *X, const uint16_t *W, float *Out);
+/* Per segment s (rows seg[s] .. seg[s+1]-1, one instance): loss_seg[s] = (cross-entropy of
+ * softmax(o_1) to target_w + mean binary cross-entropy of sigmoid(o_2) to target_p) / n_seg and
+ * dOut = its gradient.  seg_dev: [n_seg + 1] int64; loss_seg_dev: [n_seg] double. */
+int mcpd_mlp_loss(mcpd_ctx *ctx, int32_t n_seg, const int64_t *seg_dev, const float *Out,
+                  const float *target_w, const float *target_p, float *dOut, double *loss_seg_dev);
+/* grad[5378] = gradient of sum(dOut * Out) with respect to the parameters (activations recomputed;
+ * the row sum is taken in fixed chunks, so it is reproducible).  work: float workspace of at least
+ * mcpd_mlp_backward_workspace(n_rows) values. */
+int mcpd_mlp_backward(mcpd_ctx *ctx, int64_t n_rows, const float *X, const uint16_t *W,
+                      const float *dOut, float *work, int64_t work_floats, float *grad);
+int64_t mcpd_mlp_backward_workspace(int64_t n_rows);
+/* One Adam step (step >= 1) on the fp32 master parameters; W receives them rounded to bf16. */
+int mcpd_mlp_adam(mcpd_ctx *ctx, int32_t step, float lr, float beta1, float beta2, float eps,
+                  float *master, float *m, float *v, const float *grad, uint16_t *W);
+/* W = bf16(master), round to nearest even. */
+int mcpd_mlp_cast(mcpd_ctx *ctx, const float *master, uint16_t *W);
+/* Heads per segment: w_dev, nu_dev [seg[n_seg]] doubles. */
+int mcpd_mlp_heads(mcpd_ctx *ctx, int32_t n_seg, const int64_t *seg_dev, const float *Out,
+                   double *w_dev, double *nu_dev);
+
 /* Decode without any device allocation.  The paper has no counterpart: this entry point exists for
  * callers that may not call cudaMalloc or cudaFree themselves, such as a component running under
  * a host application or server that owns all device memory through its own pool allocator and

@@ -129,6 +129,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     mcpd::KParams &kp = pl->kp;
     uint64_t *d_alias = nullptr, *d_T = nullptr, *d_Tnu = nullptr;
     uint16_t *d_rows = nullptr;
+    uint32_t *d_init = nullptr;
 #define ALLOC(ptr, n)                                                        \
     do {                                                                     \
         int r_ = dev_alloc(ctx, pl, &(ptr), (n));                            \
@@ -138,6 +139,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     ALLOC(d_rows, t.rows.size());
     ALLOC(d_T, t.T.size());
     ALLOC(d_Tnu, t.Tnu.size());
+    ALLOC(d_init, t.init_pairs.size());
     ALLOC(kp.rep_acc, static_cast<size_t>(pl->pairs) * t.na);
     ALLOC(kp.slot_acc, static_cast<size_t>(pl->pairs) * t.na);
     ALLOC(kp.touched_rep, static_cast<size_t>(pl->pairs) * t.W);
@@ -165,7 +167,10 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     CU(cudaMemcpyAsync(d_T, t.T.data(), t.T.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     if (!t.Tnu.empty())
         CU(cudaMemcpyAsync(d_Tnu, t.Tnu.data(), t.Tnu.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    if (!t.init_pairs.empty())
+        CU(cudaMemcpyAsync(d_init, t.init_pairs.data(), t.init_pairs.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     kp.alias = d_alias; kp.rows = d_rows; kp.T = d_T; kp.Tnu = t.Tnu.empty() ? nullptr : d_Tnu;
+    kp.init_pairs = d_init; kp.n_init_pairs = static_cast<int32_t>(t.init_pairs.size());
     kp.na = t.na; kp.m = t.m; kp.W = t.W; kp.Mp = t.Mp; kp.wpp = t.wpp; kp.deg = t.deg_max;
     kp.nb = static_cast<int32_t>(t.nb); kp.scan = t.scan;
     kp.dummy_entry = t.dummy_entry; kp.dummy_word = t.dummy_word;
@@ -517,7 +522,8 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     auto up16 = [](size_t x) { return (x + 15) / 16 * 16; };
     for (int32_t i = 0; i < n_inst; ++i) {
         const mcpd::Tables &t = b->t[i];
-        table_bytes += up16(t.alias.size() * 8) + up16(t.rows.size() * 2) + up16(t.T.size() * 8) + up16(t.Tnu.size() * 8);
+        table_bytes += up16(t.alias.size() * 8) + up16(t.rows.size() * 2) + up16(t.T.size() * 8) + up16(t.Tnu.size() * 8) +
+                       up16(t.init_pairs.size() * 4);
         max_na = std::max(max_na, t.na); max_W = std::max(max_W, t.W); max_wpp = std::max(max_wpp, t.wpp);
         b->out_offset[i + 1] = b->out_offset[i] + t.na;
         b->bucket_offset[i] = static_cast<int64_t>(b->total_bucket_words);
@@ -559,6 +565,8 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         d.rows = static_cast<const uint16_t *>(put(t.rows.data(), t.rows.size() * 2));
         d.T = static_cast<const uint64_t *>(put(t.T.data(), t.T.size() * 8));
         d.Tnu = static_cast<const uint64_t *>(put(t.Tnu.data(), t.Tnu.size() * 8));
+        d.init_pairs = static_cast<const uint32_t *>(put(t.init_pairs.data(), t.init_pairs.size() * 4));
+        d.n_init_pairs = static_cast<int32_t>(t.init_pairs.size());
         d.S1 = b->d_buckets + b->bucket_offset[i];
         d.S2lo = b->d_buckets + b->total_bucket_words + b->bucket_offset[i];
         d.S2hi = b->d_buckets + 2 * b->total_bucket_words + b->bucket_offset[i];

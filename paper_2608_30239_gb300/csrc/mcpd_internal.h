@@ -44,6 +44,7 @@ struct Tables {
     std::vector<uint16_t> rows;       // [na * kRow] byte offsets of pool counts | y bit
     std::vector<uint64_t> T;          // [kTSide * kTSide]
     std::vector<uint64_t> Tnu;        // [na] or empty
+    std::vector<uint32_t> init_pairs; // even clone ids a with Tnu[a] or Tnu[a+1] nonzero
     std::vector<double> w;            // [na] scan weights
     // shared-memory layout of one pair (32-bit words, interleaved over the 32 lanes of a warp)
     int32_t W = 0;                    // bit-set words per chain
@@ -69,6 +70,8 @@ struct KParams {
     const uint16_t *rows;
     const uint64_t *T;
     const uint64_t *Tnu;
+    const uint32_t *init_pairs;       // [n_init_pairs]
+    int32_t n_init_pairs;
     long long *rep_acc;               // [pairs][na]
     long long *slot_acc;              // [pairs][na]
     uint32_t *touched_rep;            // [pairs][W]
@@ -99,7 +102,9 @@ struct InstDesc {
     const uint16_t *rows;             // [na * kRow] count offsets for the interleaved pair layout
     const uint64_t *T;                // [kTSide * kTSide]
     const uint64_t *Tnu;              // [na] or null
+    const uint32_t *init_pairs;       // [n_init_pairs] even clone ids with a nonzero threshold
     unsigned long long *S1, *S2lo, *S2hi, *bcount;   // this instance's N*_p buckets
+    int32_t n_init_pairs, pad0;
     int32_t na, W, wpp, deg, nb, dummy_word_index;
     uint32_t dummy_entry, dummy_word;
     long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset;

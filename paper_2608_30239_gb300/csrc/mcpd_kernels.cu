@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
     // instance).
     const uint4 *gRows = nullptr;
     const unsigned long long *gAlias = nullptr, *gT = nullptr, *Tnu = nullptr;
+    const uint32_t *init_pairs = nullptr;
+    int n_init_pairs = 0;
     unsigned long long *bS1 = nullptr, *bS2lo = nullptr, *bS2hi = nullptr, *bCount = nullptr;
     int na = 0, deg = 0, dummy_word_index = 0;
     uint32_t W = 0, B = 0, unit = 0, ell = 0, step_limit = 0, instance = 0, k0 = 0, k1 = 0;
@@ -105,6 +107,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
     auto load_instance = [&](const InstDesc &d) {
         gRows = reinterpret_cast<const uint4 *>(d.rows); gAlias = reinterpret_cast<const unsigned long long *>(d.alias);
         gT = reinterpret_cast<const unsigned long long *>(d.T); Tnu = reinterpret_cast<const unsigned long long *>(d.Tnu);
+        init_pairs = d.init_pairs; n_init_pairs = d.n_init_pairs;
         bS1 = d.S1; bS2lo = d.S2lo; bS2hi = d.S2hi; bCount = d.bcount;
         na = d.na; deg = d.deg; W = d.W; dummy_word_index = d.dummy_word_index;
         dummy_entry = d.dummy_entry; dummy_word = d.dummy_word;
@@ -118,6 +121,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
     };
     if constexpr (!BATCH) {
         Tnu = reinterpret_cast<const unsigned long long *>(p.Tnu);
+        init_pairs = p.init_pairs; n_init_pairs = p.n_init_pairs;
         bS1 = p.S1; bS2lo = p.S2lo; bS2hi = p.S2hi; bCount = p.bcount;
         na = p.na; deg = p.deg; W = p.W; dummy_word_index = p.dummy_word_index;
         dummy_entry = p.dummy_entry; dummy_word = p.dummy_word;
@@ -174,8 +178,9 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
         abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
         ++c_started;
         ++reps_in_slot;
-        if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0
-            for (int a = 0; a < na; a += 2) {
+        if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0 (clones with nu_i = 0 stay 0)
+            for (int e = 0; e < n_init_pairs; ++e) {
+                const int a = static_cast<int>(init_pairs[e]);
                 const uint4 b = philox10(make_uint4(static_cast<uint32_t>(a) >> 1, r, slot_g,
                                                     instance | (1u << 24)), k0, k1);
 #pragma unroll

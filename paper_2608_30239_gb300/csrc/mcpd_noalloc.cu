@@ -97,7 +97,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t at = off; off += up256(bytes); return at; };
     const size_t o_alias = take(na * 8), o_rows = take(na * 16), o_T = take(t.T.size() * 8);
-    const size_t o_Tnu = take(t.Tnu.size() * 8);
+    const size_t o_Tnu = take(t.Tnu.size() * 8), o_init = take(t.init_pairs.size() * 4);
     const size_t o_S1 = take(nb * na * 8), o_S2lo = take(nb * na * 8), o_S2hi = take(nb * na * 8);
     const size_t o_bc = take(nb * 8), o_cnt = take(kNumCounters * 8), o_err = take(sizeof(int));
     const size_t fixed = off;
@@ -136,12 +136,16 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     CUN(cudaMemcpyAsync(b + o_rows, t.rows.data(), t.rows.size() * 2, cudaMemcpyHostToDevice, s));
     CUN(cudaMemcpyAsync(b + o_T, t.T.data(), t.T.size() * 8, cudaMemcpyHostToDevice, s));
     if (!t.Tnu.empty()) CUN(cudaMemcpyAsync(b + o_Tnu, t.Tnu.data(), t.Tnu.size() * 8, cudaMemcpyHostToDevice, s));
+    if (!t.init_pairs.empty())
+        CUN(cudaMemcpyAsync(b + o_init, t.init_pairs.data(), t.init_pairs.size() * 4, cudaMemcpyHostToDevice, s));
 
     KParams kp{};
     kp.alias = reinterpret_cast<const uint64_t *>(b + o_alias);
     kp.rows = reinterpret_cast<const uint16_t *>(b + o_rows);
     kp.T = reinterpret_cast<const uint64_t *>(b + o_T);
     kp.Tnu = t.Tnu.empty() ? nullptr : reinterpret_cast<const uint64_t *>(b + o_Tnu);
+    kp.init_pairs = reinterpret_cast<const uint32_t *>(b + o_init);
+    kp.n_init_pairs = static_cast<int32_t>(t.init_pairs.size());
     kp.rep_acc = reinterpret_cast<long long *>(b + o_racc);
     kp.slot_acc = reinterpret_cast<long long *>(b + o_sacc);
     kp.touched_rep = reinterpret_cast<uint32_t *>(b + o_trep);

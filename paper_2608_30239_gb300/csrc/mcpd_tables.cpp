@@ -193,6 +193,8 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
             if (!(v >= 0.0 && v <= 1.0)) return fail(err, "init marginals must lie in [0, 1]", MCPD_EINVAL);
             t.Tnu[a] = scaled_threshold(v);
         }
+        for (int32_t a = 0; a < na; a += 2)
+            if (t.Tnu[a] || (a + 1 < na && t.Tnu[a + 1])) t.init_pairs.push_back(static_cast<uint32_t>(a));
     }
 
     // Shared-memory layout of one pair: W words of X bits and W of Y bits interleaved, then the
