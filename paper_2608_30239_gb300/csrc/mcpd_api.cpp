@@ -171,7 +171,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
         CU(cudaMemcpyAsync(d_init, t.init_pairs.data(), t.init_pairs.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     kp.alias = d_alias; kp.rows = d_rows; kp.T = d_T; kp.Tnu = t.Tnu.empty() ? nullptr : d_Tnu;
     kp.init_pairs = d_init; kp.n_init_pairs = static_cast<int32_t>(t.init_pairs.size());
-    kp.na = t.na; kp.m = t.m; kp.W = t.W; kp.Mp = t.Mp; kp.wpp = t.wpp; kp.deg = t.deg_max;
+    kp.na = t.na; kp.m = t.m; kp.W = t.W; kp.Mp = t.Mp; kp.wpp = t.wpp; kp.deg = t.deg_max; kp.udeg = t.udeg;
     kp.nb = static_cast<int32_t>(t.nb); kp.scan = t.scan;
     kp.dummy_entry = t.dummy_entry; kp.dummy_word = t.dummy_word;
     kp.dummy_word_index = t.dummy_word_index; kp.coupled = t.coupled ? 1 : 0;

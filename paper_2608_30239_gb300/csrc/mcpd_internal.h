@@ -47,6 +47,7 @@ struct Tables {
     std::vector<uint32_t> init_pairs; // even clone ids a with Tnu[a] or Tnu[a+1] nonzero
     std::vector<double> w;            // [na] scan weights
     // shared-memory layout of one pair (32-bit words, interleaved over the 32 lanes of a warp)
+    int32_t udeg = 0;                 // d if every active clone sits in exactly d pools, else 0
     int32_t W = 0;                    // bit-set words per chain
     int32_t Mp = 0;                   // count words (two pools per word, the padding pool included)
     int32_t wpp = 0;                  // words per pair = 2 W + Mp
@@ -87,6 +88,7 @@ struct KParams {
     int32_t *slot_reps;
     long long *trace_G;
     int32_t na, m, W, Mp, wpp, deg, nb, scan;
+    int32_t udeg, pad1;               // uniform degree (0: mixed)
     uint32_t dummy_entry, dummy_word;
     int32_t dummy_word_index, coupled;
     long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset, trace_stride;

@@ -57,7 +57,9 @@ __device__ __forceinline__ void bucket_add(unsigned long long *S1, unsigned long
 // parameters from KParams) or for many instances in one launch (BATCH = true: tables read through
 // the read-only cache from per-instance descriptors, work items (instance, slot) handed out
 // instance-major from one counter).
-template <bool COUPLED, bool SYSTEMATIC, bool BATCH>
+// DEG > 0: every clone of the (single) instance sits in exactly DEG pools, so the pool loops have
+// a compile-time trip count and rows hold no padding entries; DEG = 0 handles any degree <= 8.
+template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG>
 __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
                                  row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
 #pragma unroll
         for (int l = 0; l < kRow; ++l) {
-            if (l >= deg || ent[l] == dummy_entry) continue;
+            if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
             uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
             *cnt = static_cast<uint16_t>(*cnt + delta);
         }
@@ -382,7 +384,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
         uint32_t ix = 0;
 #pragma unroll
         for (int l = 0; l < kRow; ++l) {
-            if (l < deg) {
+            if (l < (DEG > 0 ? DEG : deg)) {
                 const uint32_t e = ent[l];
                 const uint32_t c = cbase[e & ~1u];                 // X count of the pool
                 if (c == xI) ix += (e & 1u) ? 9u : 1u;           // c_j - x_I = 0: pool j decides
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
             const uint32_t delta = nX ? (both ? 0x0101u : 0x0001u) : (both ? 0xFEFFu : 0xFFFFu);
 #pragma unroll
             for (int l = 0; l < kRow; ++l) {
-                if (l >= deg || ent[l] == dummy_entry) continue;
+                if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
                 uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
                 *cnt = static_cast<uint16_t>(*cnt + delta);
             }
@@ -442,7 +444,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
         uint32_t ix = 0, iy = 0;
 #pragma unroll
         for (int l = 0; l < kRow; ++l) {
-            if (l < deg) {
+            if (l < (DEG > 0 ? DEG : deg)) {
                 const uint32_t e = ent[l];
                 const uint32_t v = *reinterpret_cast<const uint16_t *>(cbase + (e & ~1u));
                 const uint32_t code = (e & 1u) ? 9u : 1u;
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
             const uint32_t delta = (fx ? (nX ? 0x0001u : 0xFFFFu) : 0u) + (fy ? (nY ? 0x0100u : 0xFF00u) : 0u);
 #pragma unroll
             for (int l = 0; l < kRow; ++l) {
-                if (l >= deg || ent[l] == dummy_entry) continue;
+                if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
                 uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
                 *cnt = static_cast<uint16_t>(*cnt + delta);
             }
@@ -570,22 +572,35 @@ __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uin
 
 using PairsFn = void (*)(const KParams, const BParams);
 
-PairsFn pick(int coupled, int scan, bool batch) {
+PairsFn pick(int coupled, int scan, bool batch, int udeg = 0) {
     if (batch) {
-        if (coupled) return pairs_kernel<true, false, true>;
-        return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true, true> : pairs_kernel<false, false, true>;
+        if (coupled) return pairs_kernel<true, false, true, 0>;
+        return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true, true, 0> : pairs_kernel<false, false, true, 0>;
     }
-    if (coupled) return pairs_kernel<true, false, false>;
-    return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true, false> : pairs_kernel<false, false, false>;
+    if (coupled) {
+        switch (udeg) {
+            case 3: return pairs_kernel<true, false, false, 3>;
+            case 4: return pairs_kernel<true, false, false, 4>;
+            case 5: return pairs_kernel<true, false, false, 5>;
+            case 6: return pairs_kernel<true, false, false, 6>;
+            case 7: return pairs_kernel<true, false, false, 7>;
+            case 8: return pairs_kernel<true, false, false, 8>;
+            default: return pairs_kernel<true, false, false, 0>;
+        }
+    }
+    return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true, false, 0> : pairs_kernel<false, false, false, 0>;
 }
 
 int set_smem(size_t bytes, bool batch) {
     for (int c = 0; c < 2; ++c)
         for (int sc : {MCPD_SCAN_SCORE, MCPD_SCAN_SYSTEMATIC}) {
             if (c && sc == MCPD_SCAN_SYSTEMATIC) continue;
-            if (cudaFuncSetAttribute(pick(c, sc, batch), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(bytes)) != cudaSuccess)
-                return MCPD_ECUDA;
+            for (int ud = 0; ud <= 8; ++ud) {
+                if (ud && (batch || !c || ud < 3)) continue;
+                if (cudaFuncSetAttribute(pick(c, sc, batch, ud), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(bytes)) != cudaSuccess)
+                    return MCPD_ECUDA;
+            }
         }
     return MCPD_OK;
 }
@@ -609,7 +624,7 @@ int pairs_max_smem(int device, size_t *bytes) {
 
 int launch_pairs(const KParams &kp, int grid, int block, size_t smem, void *stream) {
     const BParams none{};
-    pick(kp.coupled, kp.scan, false)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(kp, none);
+    pick(kp.coupled, kp.scan, false, kp.udeg)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(kp, none);
     return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
 }
 
@@ -643,7 +658,7 @@ int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, 
 }
 
 int pairs_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(coupled, scan, false), block, smem) == cudaSuccess
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(coupled, scan, false, 0), block, smem) == cudaSuccess
                ? MCPD_OK : MCPD_ECUDA;
 }
 

@@ -156,7 +156,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     kp.bcount = reinterpret_cast<unsigned long long *>(b + o_bc);
     kp.counters = reinterpret_cast<unsigned long long *>(b + o_cnt);
     kp.error = reinterpret_cast<int *>(b + o_err);
-    kp.na = t.na; kp.m = t.m; kp.W = t.W; kp.Mp = t.Mp; kp.wpp = t.wpp; kp.deg = t.deg_max;
+    kp.na = t.na; kp.m = t.m; kp.W = t.W; kp.Mp = t.Mp; kp.wpp = t.wpp; kp.deg = t.deg_max; kp.udeg = t.udeg;
     kp.nb = static_cast<int32_t>(t.nb); kp.scan = t.scan;
     kp.dummy_entry = t.dummy_entry; kp.dummy_word = t.dummy_word;
     kp.dummy_word_index = t.dummy_word_index; kp.coupled = t.coupled ? 1 : 0;

@@ -104,6 +104,11 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
         t.deg_max = std::max(t.deg_max, deg);
         for (int32_t e = d->clone_ptr[i]; e < d->clone_ptr[i + 1]; ++e) dA[d->clone_pools[e]]++;
     }
+    t.udeg = t.deg_max;
+    for (int32_t a = 0; a < na; ++a) {
+        const int32_t i = t.active[a];
+        if (d->clone_ptr[i + 1] - d->clone_ptr[i] != t.deg_max) { t.udeg = 0; break; }
+    }
     for (int32_t j = 0; j < m; ++j)
         if (dA[j] > kMaxPoolSize) return fail(err, "a pool holds more than 255 active clones", MCPD_ETOO_LARGE);
 
