@@ -104,12 +104,13 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
 
     // Launch shape: tables first in shared memory, then one 32-lane region per warp.
     const size_t tables = ((static_cast<size_t>(t.na) * 24 + mcpd::kTSide * mcpd::kTSide * 8) + 15) / 16 * 16;
-    const size_t per_warp = static_cast<size_t>(t.wpp) * 128;
+    const size_t per_warp = static_cast<size_t>(t.wpp) * (128 + 4 * mcpd::kYSlots) + 4;
     if (tables + per_warp > ctx->smem_optin) {
         delete pl;
         return set_err(ctx, MCPD_ETOO_LARGE, "instance too large for the one-thread-per-pair layout");
     }
-    int warps = static_cast<int>(std::min<size_t>(16, (ctx->smem_optin - tables) / per_warp));
+    const int max_warps = mcpd::pairs_max_threads(t.coupled, t.scan, t.udeg, false) / 32;
+    int warps = static_cast<int>(std::min<size_t>(max_warps, (ctx->smem_optin - tables) / per_warp));
     // Prefer several blocks per SM when the pair state is small: cap a block at what half of the
     // shared memory holds, so two blocks fit, when that still leaves 8 warps per block.
     const size_t half = ctx->smem_optin / 2;
@@ -144,6 +145,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     ALLOC(kp.slot_acc, static_cast<size_t>(pl->pairs) * t.na);
     ALLOC(kp.touched_rep, static_cast<size_t>(pl->pairs) * t.W);
     ALLOC(kp.touched_slot, static_cast<size_t>(pl->pairs) * t.W);
+    ALLOC(kp.y_state, static_cast<size_t>(pl->pairs) * t.wpp);
     ALLOC(kp.S1, static_cast<size_t>(t.nb) * t.na);
     ALLOC(kp.S2lo, static_cast<size_t>(t.nb) * t.na);
     ALLOC(kp.S2hi, static_cast<size_t>(t.nb) * t.na);
@@ -222,6 +224,7 @@ int mcpd_run_async(mcpd_ctx *ctx, mcpd_plan *pl, double *est_dev, double *se_dev
         CU(cudaMemsetAsync(kp.slot_acc, 0, pn * 8, ctx->stream));
         CU(cudaMemsetAsync(kp.touched_rep, 0, static_cast<size_t>(pl->pairs) * t.W * 4, ctx->stream));
         CU(cudaMemsetAsync(kp.touched_slot, 0, static_cast<size_t>(pl->pairs) * t.W * 4, ctx->stream));
+        CU(cudaMemsetAsync(kp.y_state, 0, static_cast<size_t>(pl->pairs) * t.wpp * 4, ctx->stream));
     }
     if (kp.trace_G) CU(cudaMemsetAsync(kp.trace_G, 0, static_cast<size_t>(pl->n_trace) * t.na * 8, ctx->stream));
     if (kp.slot_nstar) {
@@ -416,8 +419,9 @@ void free_list(std::vector<void *> &list) {
 
 // Launch shape for `warps` per block (0: as many as fit, at most 16) and the scratch it needs.
 int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps) {
-    const size_t per_warp = static_cast<size_t>(b->bp.max_wpp) * 128;
-    const int fit = static_cast<int>(std::min<size_t>(16, ctx->smem_optin / per_warp));
+    const size_t per_warp = static_cast<size_t>(b->bp.max_wpp) * (128 + 4 * mcpd::kYSlots) + 4;
+    const int cap = mcpd::pairs_max_threads(b->bp.coupled, b->bp.scan, 0, true) / 32;
+    const int fit = static_cast<int>(std::min<size_t>(cap, ctx->smem_optin / per_warp));
     if (fit < 1) return set_err(ctx, MCPD_ETOO_LARGE, "largest instance does not fit one warp of pair state");
     if (warps <= 0) warps = fit;
     if (warps > fit) return set_err(ctx, MCPD_EINVAL, "warps per block above what shared memory holds");
@@ -438,6 +442,7 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps) {
         if ((rc = balloc(ctx, b->scratch, &b->bp.slot_acc, pn)) != MCPD_OK) return rc;
         if ((rc = balloc(ctx, b->scratch, &b->bp.touched_rep, pw)) != MCPD_OK) return rc;
         if ((rc = balloc(ctx, b->scratch, &b->bp.touched_slot, pw)) != MCPD_OK) return rc;
+        if ((rc = balloc(ctx, b->scratch, &b->bp.y_state, static_cast<size_t>(b->pairs) * b->bp.max_wpp)) != MCPD_OK) return rc;
         b->scratch_pairs = b->pairs;
         b->dirty = true;
     }
@@ -458,6 +463,7 @@ int batch_enqueue(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev,
         CU(cudaMemsetAsync(b->bp.slot_acc, 0, pn * 8, s));
         CU(cudaMemsetAsync(b->bp.touched_rep, 0, pw * 4, s));
         CU(cudaMemsetAsync(b->bp.touched_slot, 0, pw * 4, s));
+        CU(cudaMemsetAsync(b->bp.y_state, 0, static_cast<size_t>(b->pairs) * b->bp.max_wpp * 4, s));
     }
     if (mcpd::launch_batch(b->bp, b->grid, b->block, b->smem, s) != MCPD_OK)
         return set_err(ctx, MCPD_ECUDA, std::string("batch kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
@@ -722,8 +728,9 @@ int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *b, const int32_t *cand_warps,
                         double *times) {
     if (!ctx || !b || !cand_warps || n_cand < 1 || reps < 1 || !est_dev || !se_dev) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
-    const size_t per_warp = static_cast<size_t>(b->bp.max_wpp) * 128;
-    const int fit = static_cast<int>(std::min<size_t>(16, ctx->smem_optin / per_warp));
+    const size_t per_warp = static_cast<size_t>(b->bp.max_wpp) * (128 + 4 * mcpd::kYSlots) + 4;
+    const int cap = mcpd::pairs_max_threads(b->bp.coupled, b->bp.scan, 0, true) / 32;
+    const int fit = static_cast<int>(std::min<size_t>(cap, ctx->smem_optin / per_warp));
     double best = 1e300;
     int32_t best_w = 0;
     for (int32_t c = 0; c < n_cand; ++c) {

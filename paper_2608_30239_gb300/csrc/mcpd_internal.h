@@ -23,6 +23,7 @@ namespace mcpd {
 
 constexpr int kRow = 8;              // pool entries per clone row (one 16-byte shared load)
 constexpr int kTSide = kRow + 1;     // acceptance table is kTSide x kTSide, indexed 9 n+ + n-
+constexpr int kYSlots = 4;           // shared-memory Y-chain slots per warp (pairs not yet met)
 constexpr int kMaxClones = 65535;
 constexpr int kMaxPools = 1022;      // pool byte offsets must fit 16 bits
 constexpr int kMaxPoolSize = 255;    // per-pool counts are bytes
@@ -41,7 +42,7 @@ struct Tables {
     bool coupled = true;
     std::vector<int32_t> active;      // [na] original index of active clone a, ascending
     std::vector<uint64_t> alias;      // [na] prob (low 32) | alias index (high 32)
-    std::vector<uint16_t> rows;       // [na * kRow] byte offsets of pool counts | y bit
+    std::vector<uint16_t> rows;       // [na * kRow] byte offset of the pool's count | y << 15
     std::vector<uint64_t> T;          // [kTSide * kTSide]
     std::vector<uint64_t> Tnu;        // [na] or empty
     std::vector<uint32_t> init_pairs; // even clone ids a with Tnu[a] or Tnu[a+1] nonzero
@@ -49,8 +50,8 @@ struct Tables {
     // shared-memory layout of one pair (32-bit words, interleaved over the 32 lanes of a warp)
     int32_t udeg = 0;                 // d if every active clone sits in exactly d pools, else 0
     int32_t W = 0;                    // bit-set words per chain
-    int32_t Mp = 0;                   // count words (two pools per word, the padding pool included)
-    int32_t wpp = 0;                  // words per pair = 2 W + Mp
+    int32_t Mp = 0;                   // count words (four pools per word, the padding pool included)
+    int32_t wpp = 0;                  // words per pair = W + Mp (X chain; Y lives in global memory)
     uint16_t dummy_entry = 0;         // row entry of the padding pool
     uint32_t dummy_word = 0;          // initial value of the word holding the padding pool
     int32_t dummy_word_index = 0;
@@ -77,6 +78,7 @@ struct KParams {
     long long *slot_acc;              // [pairs][na]
     uint32_t *touched_rep;            // [pairs][W]
     uint32_t *touched_slot;           // [pairs][W]
+    uint32_t *y_state;                // [pairs][wpp] Y chain of pairs that have not met
     unsigned long long *S1;           // [nb][na]
     unsigned long long *S2lo;         // [nb][na]
     unsigned long long *S2hi;         // [nb][na]
@@ -125,6 +127,7 @@ struct BParams {
     long long *slot_acc;              // [pairs][max_na]
     uint32_t *touched_rep;            // [pairs][max_W]
     uint32_t *touched_slot;           // [pairs][max_W]
+    uint32_t *y_state;                // [pairs][max_wpp]
     unsigned long long *counters;
     int *error;
     int32_t max_na, max_W;
@@ -133,6 +136,7 @@ struct BParams {
 // Launchers (mcpd_kernels.cu).
 int launch_batch(const BParams &bp, int grid, int block, size_t smem, void *stream);
 int set_batch_smem(size_t bytes);
+int pairs_max_threads(int coupled, int scan, int udeg, bool batch);
 int batch_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm);
 int launch_finalize_batch(const InstDesc *insts, int n_inst, const int32_t *clone_inst,
                           const int32_t *clone_local, long long total_clones, double *est,

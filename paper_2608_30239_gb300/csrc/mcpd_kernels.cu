@@ -60,7 +60,7 @@ __device__ __forceinline__ void bucket_add(unsigned long long *S1, unsigned long
 // DEG > 0: every clone of the (single) instance sits in exactly DEG pools, so the pool loops have
 // a compile-time trip count and rows hold no padding entries; DEG = 0 handles any degree <= 8.
 template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG>
-__global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BParams bp) {
+__global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs_kernel(const KParams p, const BParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint4 *sRows = reinterpret_cast<uint4 *>(smem);
@@ -83,6 +83,14 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
     }
     unsigned char *cbase = reinterpret_cast<unsigned char *>(st);   // word w of this pair: st[w * 32]
     for (int w = 0; w < wpp; ++w) st[w * 32] = 0u;                  // the pair's state starts empty
+    // kYSlots Y-chain slots per warp follow the warps' regions, then one free-slot mask per warp.
+    const int nwarps = blockDim.x >> 5;
+    uint32_t *ySlots = reinterpret_cast<uint32_t *>(smem + (BATCH ? 0 : p.smem_tables)) +
+                       static_cast<size_t>(nwarps) * 32 * wpp + static_cast<size_t>(warp) * kYSlots * wpp;
+    uint32_t *ymask = reinterpret_cast<uint32_t *>(smem + (BATCH ? 0 : p.smem_tables)) +
+                      static_cast<size_t>(nwarps) * (32 + kYSlots) * wpp + warp;
+    for (int w = lane; w < kYSlots * wpp; w += 32) ySlots[w] = 0u;
+    if (lane == 0) *ymask = (1u << kYSlots) - 1u;
     if constexpr (!BATCH) st[p.dummy_word_index * 32] = p.dummy_word;
     __syncthreads();
 
@@ -93,6 +101,9 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
     uint32_t *trep = (BATCH ? bp.touched_rep : p.touched_rep) + gpair * stride_W;
     uint32_t *tslot = (BATCH ? bp.touched_slot : p.touched_slot) + gpair * stride_W;
     unsigned long long *counters = BATCH ? bp.counters : p.counters;
+    uint32_t *const yglob = (BATCH ? bp.y_state : p.y_state) + gpair * wpp;
+    uint32_t *ybase = yglob;          // the Y state in use: a shared-memory slot or the global fallback
+    int yslot = -1;
 
     // Per-instance values (fixed for a single instance, reloaded when a batched slot changes
     // instance).
@@ -162,16 +173,72 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
                        c_limit = 0, c_sumtau = 0;
     uint32_t c_maxtau = 0;
 
-    // Add delta (mod 2^16; X count in the low byte, Y count in the high byte) to every pool of c.
-    auto bump_counts = [&](uint32_t c, uint32_t delta) {
+    // X counts are bytes in the interleaved pair region; a row entry holds the byte offset of the
+    // pool's count (bits 0-14) and the pool's outcome y (bit 15).  The Y chain's state lives in
+    // global memory (ybase: W bit words, then one count byte per pool) and is touched only while
+    // the pair has not met; it is all zero whenever the pair has met.
+    auto ycnt = [&](uint32_t e) -> uint8_t * {
+        const uint32_t off = e & 0x7FFFu;
+        return reinterpret_cast<uint8_t *>(ybase + W) + (((off >> 7) - W) * 4 + (off & 3u));
+    };
+    // Add delta (mod 256) to the X count (or, with Y, the global Y count) of every pool of c.
+    auto bump_counts = [&](uint32_t c, uint32_t delta, bool y) {
         const uint4 row = rowAt(c);
         const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
                                  row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
 #pragma unroll
         for (int l = 0; l < kRow; ++l) {
             if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
-            uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
-            *cnt = static_cast<uint16_t>(*cnt + delta);
+            uint8_t *cnt = y ? ycnt(ent[l]) : cbase + (ent[l] & 0x7FFFu);
+            *cnt = static_cast<uint8_t>(*cnt + delta);
+        }
+    };
+    // A pair that stops being met takes a free Y slot of its warp (bounded retries; the global
+    // region is the fallback) and returns it, emptied, when it meets again.
+    auto acquire_y = [&]() {
+        for (int tries = 0; tries <= kYSlots; ++tries) {
+            const uint32_t fm = *reinterpret_cast<volatile uint32_t *>(ymask);
+            if (!fm) break;
+            const int sl = __ffs(fm) - 1;
+            if (atomicAnd(ymask, ~(1u << sl)) & (1u << sl)) { yslot = sl; ybase = ySlots + sl * wpp; return; }
+        }
+        yslot = -1;
+        ybase = yglob;
+    };
+    auto release_y = [&]() {
+        if (yslot >= 0) atomicOr(ymask, 1u << yslot);
+        yslot = -1;
+        ybase = yglob;
+    };
+    // Empty the Y state in use (every Y bit lies in a word marked in rep_words).
+    auto clear_y = [&]() {
+        unsigned long long groups = rep_words;
+        while (groups) {
+            const int g = __ffsll(static_cast<long long>(groups)) - 1;
+            groups &= groups - 1;
+            const uint32_t q0 = static_cast<uint32_t>(g) << gshift, q1 = min(W, q0 + (1u << gshift));
+            for (uint32_t q = q0; q < q1; ++q) {
+                uint32_t yw = ybase[q];
+                if (!yw) continue;
+                ybase[q] = 0u;
+                while (yw) { const int b = __ffs(yw) - 1; yw &= yw - 1; bump_counts(q * 32 + b, 0xFFu, true); }
+            }
+        }
+    };
+    // The pre-lag update just flipped site I of X_0 and the start was random: Y_0 = X_0 goes to the
+    // global Y state (X_1 with bit I restored).
+    auto copy_y0 = [&](uint32_t qI, uint32_t bitI) {
+        unsigned long long groups = rep_words;
+        while (groups) {
+            const int g = __ffsll(static_cast<long long>(groups)) - 1;
+            groups &= groups - 1;
+            const uint32_t q0 = static_cast<uint32_t>(g) << gshift, q1 = min(W, q0 + (1u << gshift));
+            for (uint32_t q = q0; q < q1; ++q) {
+                uint32_t yw = st[q * 32] ^ (q == qI ? bitI : 0u);
+                if (!yw) continue;
+                ybase[q] = yw;
+                while (yw) { const int b = __ffs(yw) - 1; yw &= yw - 1; bump_counts(q * 32 + b, 1u, true); }
+            }
         }
     };
 
@@ -192,10 +259,9 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
                     const unsigned long long u = h ? ((static_cast<unsigned long long>(b.z) << 32) | b.w)
                                                    : ((static_cast<unsigned long long>(b.x) << 32) | b.y);
                     if (u < Tnu[c]) {
-                        const uint32_t q = c >> 5, bit = 1u << (c & 31);
-                        st[(2 * q) * 32] |= bit;
-                        if (COUPLED) st[(2 * q + 1) * 32] |= bit;
-                        bump_counts(c, COUPLED ? 0x0101u : 0x0001u);
+                        const uint32_t q = c >> 5;
+                        st[q * 32] |= 1u << (c & 31);
+                        bump_counts(c, 1u, false);
                         rep_words |= 1ull << (q >> gshift);
                     }
                 }
@@ -229,11 +295,13 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
         start_rep();
     };
 
-    // End of a replication: empty the pair's state and the replication's accumulators; when `move`,
-    // first close the open intervals at C and add the replication's G into the slot's sums.
+    // End of a replication: empty the pair's state and the replication's accumulators; when `move`
+    // (completed, so X_C = Y_{C-1}), first close the open intervals at C, which for a bit set in
+    // X_C adds W(C) - W(C-1) (coupled) or W(C) (uncoupled), and add the replication's G into the
+    // slot's sums.
     auto finish_rep = [&](bool move, uint32_t C) {
-        const long long wX = move ? wpre(C) : 0;
-        const long long wY = (move && COUPLED) ? wpre(static_cast<long long>(C) - 1) : 0;
+        const long long wX = move ? (COUPLED ? wpre(C) - wpre(static_cast<long long>(C) - 1) : wpre(C)) : 0;
+        if (COUPLED && D != 0) { clear_y(); release_y(); }
         unsigned long long groups = rep_words;
         while (groups) {
             const int g = __ffsll(static_cast<long long>(groups)) - 1;
@@ -241,10 +309,9 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
             const uint32_t q0 = static_cast<uint32_t>(g) << gshift;
             const uint32_t q1 = min(W, q0 + (1u << gshift));
             for (uint32_t q = q0; q < q1; ++q) {
-                const uint32_t xw = st[(2 * q) * 32];
-                const uint32_t yw = COUPLED ? st[(2 * q + 1) * 32] : 0u;
+                const uint32_t xw = st[q * 32];
                 const uint32_t tw = trep[q];
-                uint32_t m = tw | xw | yw, moved = 0;
+                uint32_t m = tw | xw, moved = 0;
                 if (!m) continue;
                 while (m) {
                     const int b = __ffs(m) - 1;
@@ -255,18 +322,15 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
                     if (tw & bit) { v = racc[j]; racc[j] = 0; }
                     if (move) {
                         if (xw & bit) v += wX;
-                        if (yw & bit) v -= wY;
                         if (v != 0) {
                             atomicAdd(reinterpret_cast<unsigned long long *>(&sacc[j]), static_cast<unsigned long long>(v));
                             moved |= bit;
                         }
                     }
-                    const uint32_t delta = ((xw & bit) ? 0xFFFFu : 0u) + ((yw & bit) ? 0xFF00u : 0u);
-                    if (delta) bump_counts(j, delta);
+                    if (xw & bit) bump_counts(j, 0xFFu, false);
                 }
                 if (tw) trep[q] = 0u;
-                if (xw) st[(2 * q) * 32] = 0u;
-                if (yw) st[(2 * q + 1) * 32] = 0u;
+                if (xw) st[q * 32] = 0u;
                 if (moved) { atomicOr(&tslot[q], moved); slot_words |= 1ull << g; }
             }
         }
@@ -369,15 +433,46 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
         return coin < static_cast<uint32_t>(e) ? col : static_cast<uint32_t>(e >> 32);
     };
 
+    // X's update; on a flip, its counts, the accumulator event of the pair and D.  `met` means the
+    // pair has met (t >= 1, X_t = Y_{t-1}): Y_t = X_{t+1} flips with it and the two events add to
+    // W(t) - W(t-1); at t = 0 (pre-lag) X alone moves.
+    auto apply_x_flip = [&](uint32_t I, uint32_t q, uint32_t bit, uint32_t xw, uint32_t nX,
+                            const uint32_t *ent, bool met) {
+        st[q * 32] = xw ^ bit;
+        const uint32_t delta = nX ? 1u : 0xFFu;
+#pragma unroll
+        for (int l = 0; l < kRow; ++l) {
+            if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
+            uint8_t *cnt = cbase + (ent[l] & 0x7FFFu);
+            *cnt = static_cast<uint8_t>(*cnt + delta);
+        }
+        long long w;
+        if (COUPLED) {
+            if (met) {
+                const long long a = static_cast<long long>(t) - kk + 1;
+                w = a < 0 ? 0 : (a > LL ? LL : a);
+            } else {
+                w = wpre(0);                                     // X_1 only
+                D = 1;
+                acquire_y();
+                if (Tnu) copy_y0(q, bit);
+            }
+        } else {
+            w = wpre(t);
+        }
+        if (w != 0) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]), static_cast<unsigned long long>(nX ? -w : w));
+            atomicOr(&trep[q], bit);
+        }
+    };
+
     // One step for a pair whose Y chain equals its X chain where it matters: the pre-lag update
-    // (t = 0, X only) or a pair that has met (X_t = Y_{t-1}, so Y_t = X_{t+1} and both flip
-    // together).  Uncoupled chains always take this path.
+    // (t = 0, X only) or a pair that has met.  Uncoupled chains always take this path.
     auto step_fast = [&](uint32_t ws, uint32_t wu) -> int {
         const uint32_t I = draw_site(ws);
         const uint4 row = rowAt(I);
         const uint32_t q = I >> 5, bit = 1u << (I & 31);
-        uint32_t *px = st + (2 * q) * 32;
-        const uint32_t xw = px[0];
+        const uint32_t xw = st[q * 32];
         const uint32_t xI = (xw & bit) ? 1u : 0u;
         const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
                                  row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
@@ -386,8 +481,8 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
         for (int l = 0; l < kRow; ++l) {
             if (l < (DEG > 0 ? DEG : deg)) {
                 const uint32_t e = ent[l];
-                const uint32_t c = cbase[e & ~1u];                 // X count of the pool
-                if (c == xI) ix += (e & 1u) ? 9u : 1u;           // c_j - x_I = 0: pool j decides
+                const uint32_t c = cbase[e & 0x7FFFu];             // X count of the pool
+                if (c == xI) ix += (e >> 15) ? 9u : 1u;           // c_j - x_I = 0: pool j decides
             }
         }
         const unsigned long long TX = tAt(ix);
@@ -398,47 +493,22 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
             nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
         }
         if (nX != xI) {
-            const bool both = COUPLED && t > 0;
-            px[0] = xw ^ bit;
-            if (both) px[32] ^= bit;
-            const uint32_t delta = nX ? (both ? 0x0101u : 0x0001u) : (both ? 0xFEFFu : 0xFFFFu);
-#pragma unroll
-            for (int l = 0; l < kRow; ++l) {
-                if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
-                uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
-                *cnt = static_cast<uint16_t>(*cnt + delta);
-            }
-            long long w;
-            if (COUPLED) {
-                if (both) {                                      // W(t) - W(t-1): X at t+1, Y at t
-                    const long long a = static_cast<long long>(t) - kk + 1;
-                    w = a < 0 ? 0 : (a > LL ? LL : a);
-                } else {
-                    w = wpre(0);                                 // X_1 only
-                    D = 1;
-                }
-            } else {
-                w = wpre(t);
-            }
-            if (w != 0) {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]),
-                          static_cast<unsigned long long>(nX ? -w : w));
-                atomicOr(&trep[q], bit);
-            }
+            apply_x_flip(I, q, bit, xw, nX, ent, COUPLED && t > 0);
             rep_words |= 1ull << (q >> gshift);
         }
         return after_step();
     };
 
-    // One coupled step for a pair that has not met: both chains read their own state.
+    // One coupled step for a warp holding a pair that has not met: such a pair reads its Y chain
+    // from the global Y state; pairs that have met (or are at t = 0) use X for Y.
     auto step_full = [&](uint32_t ws, uint32_t wu) -> int {
         const uint32_t I = draw_site(ws);
         const uint4 row = rowAt(I);
         const uint32_t q = I >> 5, bit = 1u << (I & 31);
-        uint32_t *px = st + (2 * q) * 32;
-        const uint32_t xw = px[0], yw = px[32];
+        const uint32_t xw = st[q * 32];
+        const bool own_y = t > 0 && D != 0;
+        const uint32_t yw = own_y ? ybase[q] : xw;
         const uint32_t xI = (xw & bit) ? 1u : 0u, yI = (yw & bit) ? 1u : 0u;
-        const uint32_t xy = xI | (yI << 8);
         const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
                                  row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
         uint32_t ix = 0, iy = 0;
@@ -446,11 +516,11 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
         for (int l = 0; l < kRow; ++l) {
             if (l < (DEG > 0 ? DEG : deg)) {
                 const uint32_t e = ent[l];
-                const uint32_t v = *reinterpret_cast<const uint16_t *>(cbase + (e & ~1u));
-                const uint32_t code = (e & 1u) ? 9u : 1u;
-                const uint32_t d = v ^ xy;
-                if ((d & 0xFFu) == 0) ix += code;
-                if ((d & 0xFF00u) == 0) iy += code;
+                const uint32_t code = (e >> 15) ? 9u : 1u;
+                const uint32_t cx = cbase[e & 0x7FFFu];
+                const uint32_t cy = own_y ? static_cast<uint32_t>(*ycnt(e)) : cx;
+                if (cx == xI) ix += code;
+                if (cy == yI) iy += code;
             }
         }
         const unsigned long long TX = tAt(ix), TY = tAt(iy);
@@ -461,27 +531,47 @@ __global__ void __launch_bounds__(512, 1) pairs_kernel(const KParams p, const BP
             if (wu == thx) nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
             if (wu == thy) nY = lo < static_cast<uint32_t>(TY) ? 1u : 0u;
         }
-        if (t == 0) nY = yI;                                    // pre-lag: X only
+        if (!own_y) {                                           // pre-lag, or met: as the fast path
+            if (nX != xI) {
+                apply_x_flip(I, q, bit, xw, nX, ent, t > 0);
+                rep_words |= 1ull << (q >> gshift);
+            }
+            return after_step();
+        }
         const uint32_t fx = nX ^ xI, fy = nY ^ yI;
         if (fx | fy) {
-            if (fx) px[0] = xw ^ bit;
-            if (fy) px[32] = yw ^ bit;
-            const uint32_t delta = (fx ? (nX ? 0x0001u : 0xFFFFu) : 0u) + (fy ? (nY ? 0x0100u : 0xFF00u) : 0u);
-#pragma unroll
-            for (int l = 0; l < kRow; ++l) {
-                if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
-                uint16_t *cnt = reinterpret_cast<uint16_t *>(cbase + (ent[l] & ~1u));
-                *cnt = static_cast<uint16_t>(*cnt + delta);
-            }
             long long ev = 0;
-            if (fx) { const long long w = wpre(t); ev += nX ? -w : w; }                           // X_{t+1}
-            if (fy) { const long long w = wpre(static_cast<long long>(t) - 1); ev += nY ? w : -w; }  // Y_t
+            if (fx) {
+                st[q * 32] = xw ^ bit;
+                const uint32_t delta = nX ? 1u : 0xFFu;
+#pragma unroll
+                for (int l = 0; l < kRow; ++l) {
+                    if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
+                    uint8_t *cnt = cbase + (ent[l] & 0x7FFFu);
+                    *cnt = static_cast<uint8_t>(*cnt + delta);
+                }
+                const long long w = wpre(t);                     // X_{t+1}
+                ev += nX ? -w : w;
+            }
+            if (fy) {
+                ybase[q] = yw ^ bit;
+                const uint32_t delta = nY ? 1u : 0xFFu;
+#pragma unroll
+                for (int l = 0; l < kRow; ++l) {
+                    if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
+                    uint8_t *cnt = ycnt(ent[l]);
+                    *cnt = static_cast<uint8_t>(*cnt + delta);
+                }
+                const long long w = wpre(static_cast<long long>(t) - 1);   // Y_t
+                ev += nY ? w : -w;
+            }
             if (ev != 0) {
                 atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]), static_cast<unsigned long long>(ev));
                 atomicOr(&trep[q], bit);
             }
             rep_words |= 1ull << (q >> gshift);
             D = D + (nX ^ nY) - (xI ^ yI);
+            if (D == 0) { clear_y(); release_y(); }             // met: Y is X from now on
         }
         return after_step();
     };
@@ -660,6 +750,12 @@ int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, 
 int pairs_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(coupled, scan, false, 0), block, smem) == cudaSuccess
                ? MCPD_OK : MCPD_ECUDA;
+}
+
+int pairs_max_threads(int coupled, int scan, int udeg, bool batch) {
+    cudaFuncAttributes a{};
+    if (cudaFuncGetAttributes(&a, pick(coupled, scan, batch, batch ? 0 : udeg)) != cudaSuccess) return 512;
+    return a.maxThreadsPerBlock;
 }
 
 int batch_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm) {

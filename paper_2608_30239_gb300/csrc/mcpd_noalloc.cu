@@ -104,17 +104,18 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
 
     // Launch shape as the allocating path would choose it, then as many whole warps as fit.
     const size_t tables = ((na * 24 + kTSide * kTSide * 8) + 15) / 16 * 16;
-    const size_t per_warp_smem = static_cast<size_t>(t.wpp) * 128;
+    const size_t per_warp_smem = static_cast<size_t>(t.wpp) * (128 + 4 * kYSlots) + 4;
     if (tables + per_warp_smem > ctx->smem_optin)
         return fail(ctx, MCPD_ETOO_LARGE, "instance too large for the one-thread-per-pair layout");
-    int warps = static_cast<int>(std::min<size_t>(16, (ctx->smem_optin - tables) / per_warp_smem));
+    const int max_warps = pairs_max_threads(t.coupled, t.scan, t.udeg, false) / 32;
+    int warps = static_cast<int>(std::min<size_t>(max_warps, (ctx->smem_optin - tables) / per_warp_smem));
     const size_t half = ctx->smem_optin / 2;
     if (half > tables && (half - tables) / per_warp_smem >= 8)
         warps = static_cast<int>(std::min<size_t>(warps, (half - tables) / per_warp_smem));
-    const size_t per_pair = na * 16 + static_cast<size_t>(t.W) * 8;   // rep/slot sums, touched sets
+    const size_t per_pair = na * 16 + static_cast<size_t>(t.W) * 8 + static_cast<size_t>(t.wpp) * 4;   // sums, touched sets, Y state
     if (fixed >= kNoAllocScratchBytes)
         return fail(ctx, MCPD_ETOO_LARGE, "tables and N*_p buckets exceed the 64 MiB no-alloc scratch");
-    const size_t fit_warps = (kNoAllocScratchBytes - fixed - 4 * 256) / (32 * per_pair);
+    const size_t fit_warps = (kNoAllocScratchBytes - fixed - 5 * 256) / (32 * per_pair);
     if (fit_warps < 1)
         return fail(ctx, MCPD_ETOO_LARGE, "not even one warp of pair accumulators fits the 64 MiB no-alloc scratch");
     int per_sm = 1;
@@ -127,6 +128,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     const size_t pairs = static_cast<size_t>(grid) * warps * 32;
     const size_t o_racc = take(pairs * na * 8), o_sacc = take(pairs * na * 8);
     const size_t o_trep = take(pairs * t.W * 4), o_tslot = take(pairs * t.W * 4);
+    const size_t o_y = take(pairs * t.wpp * 4);
     if (off > kNoAllocScratchBytes) return fail(ctx, MCPD_ETOO_LARGE, "no-alloc scratch layout overflow");
 
     unsigned char *b = static_cast<unsigned char *>(base);
@@ -150,6 +152,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     kp.slot_acc = reinterpret_cast<long long *>(b + o_sacc);
     kp.touched_rep = reinterpret_cast<uint32_t *>(b + o_trep);
     kp.touched_slot = reinterpret_cast<uint32_t *>(b + o_tslot);
+    kp.y_state = reinterpret_cast<uint32_t *>(b + o_y);
     kp.S1 = reinterpret_cast<unsigned long long *>(b + o_S1);
     kp.S2lo = reinterpret_cast<unsigned long long *>(b + o_S2lo);
     kp.S2hi = reinterpret_cast<unsigned long long *>(b + o_S2hi);

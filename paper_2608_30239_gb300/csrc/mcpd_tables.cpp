@@ -202,26 +202,27 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
             if (t.Tnu[a] || (a + 1 < na && t.Tnu[a + 1])) t.init_pairs.push_back(static_cast<uint32_t>(a));
     }
 
-    // Shared-memory layout of one pair: W words of X bits and W of Y bits interleaved, then the
-    // pool counts two pools per word (X count in the low byte, Y count in the high byte), the
-    // padding pool m last.  Word w of a pair lives at word (w * 32 + lane) of the warp's region.
+    // Shared-memory layout of one pair (the X chain): W words of bits, then one count byte per
+    // pool, the padding pool m last.  Word w of a pair lives at word (w * 32 + lane) of its warp's
+    // region, so the byte of pool j sits at (W + j / 4) * 128 + j % 4 from the lane's base.  The Y
+    // chain uses the same layout, contiguous, in global memory while the pair has not met.
     t.W = (na + 31) / 32;
-    t.Mp = (m + 1 + 1) / 2;
-    t.wpp = 2 * t.W + t.Mp;
+    t.Mp = (m + 1 + 3) / 4;
+    t.wpp = t.W + t.Mp;
     auto count_offset = [&](int32_t j) -> uint32_t {
-        return static_cast<uint32_t>((2 * t.W + (j >> 1)) * 128 + (j & 1) * 2);
+        return static_cast<uint32_t>((t.W + (j >> 2)) * 128 + (j & 3));
     };
-    if (count_offset(m) > 0xFFFEu) return fail(err, "pair state too large for 16-bit offsets", MCPD_ETOO_LARGE);
+    if (count_offset(m) > 0x7FFFu) return fail(err, "pair state too large for 15-bit offsets", MCPD_ETOO_LARGE);
     t.dummy_entry = static_cast<uint16_t>(count_offset(m));
-    t.dummy_word_index = 2 * t.W + (m >> 1);
-    t.dummy_word = (m & 1) ? 0x02020000u : 0x00000202u;
+    t.dummy_word_index = t.W + (m >> 2);
+    t.dummy_word = 2u << (8 * (m & 3));
     t.rows.assign(static_cast<size_t>(na) * kRow, t.dummy_entry);
     for (int32_t a = 0; a < na; ++a) {
         int32_t i = t.active[a];
         int32_t l = 0;
         for (int32_t e = d->clone_ptr[i]; e < d->clone_ptr[i + 1]; ++e, ++l) {
             int32_t j = d->clone_pools[e];
-            t.rows[static_cast<size_t>(a) * kRow + l] = static_cast<uint16_t>(count_offset(j) | (y[j] ? 1u : 0u));
+            t.rows[static_cast<size_t>(a) * kRow + l] = static_cast<uint16_t>(count_offset(j) | (y[j] ? 0x8000u : 0u));
         }
     }
 
