@@ -111,11 +111,13 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     }
     const int max_warps = mcpd::pairs_max_threads(t.coupled, t.scan, t.udeg, false) / 32;
     int warps = static_cast<int>(std::min<size_t>(max_warps, (ctx->smem_optin - tables) / per_warp));
-    // Prefer several blocks per SM when the pair state is small: cap a block at what half of the
-    // shared memory holds, so two blocks fit, when that still leaves 8 warps per block.
+    // Two blocks per SM (each with its own copy of the tables) when that holds more warps in
+    // total than one block does.
     const size_t half = ctx->smem_optin / 2;
-    if (half > tables && (half - tables) / per_warp >= 8)
-        warps = static_cast<int>(std::min<size_t>(warps, (half - tables) / per_warp));
+    if (half > tables) {
+        const int w2 = static_cast<int>(std::min<size_t>(max_warps, (half - tables) / per_warp));
+        if (2 * w2 > warps) warps = w2;
+    }
     pl->block = warps * 32;
     pl->smem = tables + per_warp * warps;
     if (mcpd::set_pairs_smem(pl->smem, t.coupled) != MCPD_OK) {

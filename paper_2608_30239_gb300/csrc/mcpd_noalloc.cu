@@ -110,8 +110,10 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     const int max_warps = pairs_max_threads(t.coupled, t.scan, t.udeg, false) / 32;
     int warps = static_cast<int>(std::min<size_t>(max_warps, (ctx->smem_optin - tables) / per_warp_smem));
     const size_t half = ctx->smem_optin / 2;
-    if (half > tables && (half - tables) / per_warp_smem >= 8)
-        warps = static_cast<int>(std::min<size_t>(warps, (half - tables) / per_warp_smem));
+    if (half > tables) {
+        const int w2 = static_cast<int>(std::min<size_t>(max_warps, (half - tables) / per_warp_smem));
+        if (2 * w2 > warps) warps = w2;
+    }
     const size_t per_pair = na * 16 + static_cast<size_t>(t.W) * 8 + static_cast<size_t>(t.wpp) * 4;   // sums, touched sets, Y state
     if (fixed >= kNoAllocScratchBytes)
         return fail(ctx, MCPD_ETOO_LARGE, "tables and N*_p buckets exceed the 64 MiB no-alloc scratch");
