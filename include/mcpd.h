@@ -185,9 +185,12 @@ void mcpd_batch_destroy(mcpd_batch *batch);
 int mcpd_batch_info(const mcpd_batch *batch, int64_t info[16]);
 /* offsets: [n_inst + 1] host array receiving each instance's first output index. */
 int mcpd_batch_offsets(const mcpd_batch *batch, int64_t *offsets);
-/* Choose the launch shape: warps per block (0: as many as the largest instance's pair state
- * allows, at most 16).  May reallocate the per-pair scratch; invalidates a captured graph. */
-int mcpd_batch_set_shape(mcpd_ctx *ctx, mcpd_batch *batch, int32_t warps_per_block);
+/* Choose the launch shape: lanes per pair (1: one thread per pair; 8, 16 or 32: a lane group per
+ * pair, coupled batches only; all give identical results) and warps per block (0: as many as the
+ * kernel and the largest instance's pair state allow).  May reallocate the per-pair scratch;
+ * invalidates a captured graph. */
+int mcpd_batch_set_shape(mcpd_ctx *ctx, mcpd_batch *batch, int32_t lanes_per_pair,
+                         int32_t warps_per_block);
 /* Enqueue one decode of every instance; est_dev, se_dev: device arrays [info[0]]. */
 int mcpd_batch_run_async(mcpd_ctx *ctx, mcpd_batch *batch, double *est_dev, double *se_dev);
 /* Capture one decode (scratch clears, sampling kernel, finalize) into a CUDA graph on the
@@ -201,11 +204,12 @@ int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *batch, mcpd_stats *stats);
  * plan of that instance alone. */
 int mcpd_batch_fetch(mcpd_ctx *ctx, const mcpd_batch *batch, int32_t inst, int what,
                      void *host_dst, size_t bytes);
-/* Autotuner: time each candidate warps-per-block (reps timed decodes after one warm-up each),
- * keep the fastest; times[c] gets candidate c's mean milliseconds (-1 if it does not fit). */
-int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *batch, const int32_t *cand_warps,
-                        int32_t n_cand, int32_t reps, double *est_dev, double *se_dev,
-                        int32_t *best_warps, double *times);
+/* Autotuner: time each candidate shape (cand_lanes[c] lanes per pair, cand_warps[c] warps per
+ * block; reps timed decodes after one warm-up each) and keep the fastest; best_index receives its
+ * index, times[c] candidate c's mean milliseconds (-1 if it does not fit). */
+int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *batch, const int32_t *cand_lanes,
+                        const int32_t *cand_warps, int32_t n_cand, int32_t reps, double *est_dev,
+                        double *se_dev, int32_t *best_index, double *times);
 
 /* ---- Learned scan weights and initial marginals ----------------------------------------------
  * Not in the paper, which proves that any fixed positive scan weights keep pi invariant

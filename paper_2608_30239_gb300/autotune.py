@@ -1,7 +1,7 @@
 """Persisted launch-shape choices for batched decoding.
 
-The tuner itself is native (mcpd_batch_autotune times candidate warps-per-block on the batch);
-this module remembers its choice in a JSON cache keyed by GPU name and a coarse shape bucket
+The tuner itself is native (mcpd_batch_autotune times candidate launch shapes on the batch);
+this module remembers its choice (lanes per pair, warps per block) in a JSON cache keyed by GPU name and a coarse shape bucket
 (instance count, largest n_active, total slots, coupled), so a batch of the same shape reuses it.
 """
 from __future__ import annotations
@@ -29,16 +29,20 @@ def load():
         return {}
 
 
-def tuned_shape(batch, est_dev, se_dev, gpu_name: str, candidates=(4, 6, 8, 12, 16), reps=1,
+DEFAULT_CANDIDATES = ((1, 0), (1, 6), (8, 0), (8, 12), (16, 0), (32, 0))
+
+
+def tuned_shape(batch, est_dev, se_dev, gpu_name: str, candidates=DEFAULT_CANDIDATES, reps=1,
                 retune=False):
-    """Apply the cached warps-per-block for this shape, or tune, store and apply it."""
+    """Apply the cached (lanes per pair, warps per block) for this shape, or tune, store, apply."""
     cache = load()
     key = shape_key(gpu_name, batch)
     if not retune and key in cache:
-        batch.set_shape(int(cache[key]["warps"]))
-        return int(cache[key]["warps"]), cache[key].get("times_ms", {}), True
+        lanes, warps = cache[key]["shape"]
+        batch.set_shape(int(warps), int(lanes))
+        return (int(lanes), int(warps)), cache[key].get("times_ms", {}), True
     best, times = batch.autotune(est_dev, se_dev, candidates, reps)
-    cache[key] = {"warps": best, "times_ms": times}
+    cache[key] = {"shape": list(best), "times_ms": {f"{a}x{b}": t for (a, b), t in times.items()}}
     os.makedirs(os.path.dirname(CACHE), exist_ok=True)
     tmp = CACHE + f".tmp{os.getpid()}"
     with open(tmp, "w") as f:

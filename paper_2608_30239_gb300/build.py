@@ -33,7 +33,8 @@ def _cuda_home() -> str:
 
 def sources():
     return [os.path.join(SRC, f) for f in ("mcpd_tables.cpp", "mcpd_api.cpp", "mcpd_kernels.cu",
-                                           "mcpd_noalloc.cu", "mcpd_mlp.cu", "mcpd_internal.h")] + \
+                                           "mcpd_noalloc.cu", "mcpd_mlp.cu", "mcpd_group.cu", "mcpd_internal.h",
+                                           "mcpd_device.cuh")] + \
         [os.path.join(INCLUDE, "mcpd.h")]
 
 
@@ -51,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     inc = ["-I" + INCLUDE, "-I" + SRC, "-I" + os.path.join(cuda, "include")]
-    objs = {name: os.path.join(BUILD, name + ".o") for name in ("tables", "api", "kernels", "noalloc", "mlp")}
+    objs = {name: os.path.join(BUILD, name + ".o") for name in ("tables", "api", "kernels", "noalloc", "mlp", "group")}
     cxx = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-Wall"]
     jobs = [
         cxx + inc + ["-c", os.path.join(SRC, "mcpd_tables.cpp"), "-o", objs["tables"]],
@@ -63,6 +64,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         + inc + ["-c", os.path.join(SRC, "mcpd_noalloc.cu"), "-o", objs["noalloc"]],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
         + inc + ["-c", os.path.join(SRC, "mcpd_mlp.cu"), "-o", objs["mlp"]],
+        [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
+        + (["-Xptxas", "-v"] if ptxas_info else []) + inc
+        + ["-c", os.path.join(SRC, "mcpd_group.cu"), "-o", objs["group"]],
     ]
     procs = [subprocess.Popen(j, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for j in jobs]
     logs = []
@@ -75,7 +79,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         sys.stdout.write("".join(logs))
     tmp = LIB + f".tmp{os.getpid()}"
     link = [nvcc, ARCH, "-shared", "-o", tmp, objs["tables"], objs["api"], objs["kernels"],
-            objs["noalloc"], objs["mlp"], "-cudart", "static"]
+            objs["noalloc"], objs["mlp"], objs["group"], "-cudart", "static"]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
     return LIB

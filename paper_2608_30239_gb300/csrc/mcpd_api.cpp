@@ -419,23 +419,35 @@ void free_list(std::vector<void *> &list) {
     list.clear();
 }
 
-// Launch shape for `warps` per block (0: as many as fit, at most 16) and the scratch it needs.
-int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps) {
-    const size_t per_warp = static_cast<size_t>(b->bp.max_wpp) * (128 + 4 * mcpd::kYSlots) + 4;
-    const int cap = mcpd::pairs_max_threads(b->bp.coupled, b->bp.scan, 0, true) / 32;
+// Launch shape: `lanes` per pair (1: one thread per pair; 8, 16, 32: a lane group per pair) and
+// `warps` per block (0: as many as fit), and the per-pair scratch it needs.
+int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
+    if (lanes != 1 && lanes != 8 && lanes != 16 && lanes != 32)
+        return set_err(ctx, MCPD_EINVAL, "lanes per pair must be 1, 8, 16 or 32");
+    if (lanes > 1 && !b->bp.coupled) return set_err(ctx, MCPD_EINVAL, "lane groups run coupled batches only");
+    const size_t per_warp = lanes == 1 ? static_cast<size_t>(b->bp.max_wpp) * (128 + 4 * mcpd::kYSlots) + 4
+                                       : static_cast<size_t>(32 / lanes) * 2 * b->bp.max_wpp * 4;
+    const int cap = (lanes == 1 ? mcpd::pairs_max_threads(b->bp.coupled, b->bp.scan, 0, true)
+                                : mcpd::group_max_threads(lanes)) / 32;
     const int fit = static_cast<int>(std::min<size_t>(cap, ctx->smem_optin / per_warp));
     if (fit < 1) return set_err(ctx, MCPD_ETOO_LARGE, "largest instance does not fit one warp of pair state");
     if (warps <= 0) warps = fit;
-    if (warps > fit) return set_err(ctx, MCPD_EINVAL, "warps per block above what shared memory holds");
+    if (warps > fit) return set_err(ctx, MCPD_EINVAL, "warps per block above what the kernel allows");
     b->warps = warps;
     b->block = warps * 32;
     b->smem = per_warp * warps;
-    if (mcpd::set_batch_smem(b->smem) != MCPD_OK) return set_err(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
+    b->bp.lanes = lanes;
     int per_sm = 1;
-    if (mcpd::batch_occupancy(b->bp.coupled, b->bp.scan, b->block, b->smem, &per_sm) != MCPD_OK || per_sm < 1)
-        per_sm = 1;
+    if (lanes == 1) {
+        if (mcpd::set_batch_smem(b->smem) != MCPD_OK) return set_err(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
+        if (mcpd::batch_occupancy(b->bp.coupled, b->bp.scan, b->block, b->smem, &per_sm) != MCPD_OK || per_sm < 1)
+            per_sm = 1;
+    } else {
+        if (mcpd::set_group_smem(lanes, b->smem) != MCPD_OK) return set_err(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
+        if (mcpd::group_occupancy(lanes, b->block, b->smem, &per_sm) != MCPD_OK || per_sm < 1) per_sm = 1;
+    }
     b->grid = ctx->sm_count * per_sm;
-    b->pairs = static_cast<long long>(b->grid) * b->block;
+    b->pairs = static_cast<long long>(b->grid) * b->block / lanes;
     if (b->pairs > b->scratch_pairs) {
         free_list(b->scratch);
         const size_t pn = static_cast<size_t>(b->pairs) * b->bp.max_na, pw = static_cast<size_t>(b->pairs) * b->bp.max_W;
@@ -467,7 +479,8 @@ int batch_enqueue(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev,
         CU(cudaMemsetAsync(b->bp.touched_slot, 0, pw * 4, s));
         CU(cudaMemsetAsync(b->bp.y_state, 0, static_cast<size_t>(b->pairs) * b->bp.max_wpp * 4, s));
     }
-    if (mcpd::launch_batch(b->bp, b->grid, b->block, b->smem, s) != MCPD_OK)
+    if ((b->bp.lanes == 1 ? mcpd::launch_batch(b->bp, b->grid, b->block, b->smem, s)
+                          : mcpd::launch_group(b->bp, b->grid, b->block, b->smem, s)) != MCPD_OK)
         return set_err(ctx, MCPD_ECUDA, std::string("batch kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
     if (mcpd::launch_finalize_batch(b->d_insts, b->bp.n_inst, b->d_clone_inst, b->d_clone_local,
                                     b->total_active, est_dev, se_dev, s) != MCPD_OK)
@@ -523,7 +536,7 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     if (cudaSetDevice(ctx->device) != cudaSuccess) { mcpd_batch_destroy(b); return set_err(ctx, MCPD_ECUDA, "cudaSetDevice"); }
     // Sizes.
     size_t table_bytes = 0;
-    int32_t max_na = 0, max_W = 0, max_wpp = 0;
+    int32_t max_na = 0, max_W = 0, max_wpp = 0, max_m = 0;
     b->out_offset.assign(n_inst + 1, 0);
     b->bucket_offset.assign(n_inst, 0);
     b->count_offset.assign(n_inst, 0);
@@ -531,8 +544,9 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     for (int32_t i = 0; i < n_inst; ++i) {
         const mcpd::Tables &t = b->t[i];
         table_bytes += up16(t.alias.size() * 8) + up16(t.rows.size() * 2) + up16(t.T.size() * 8) + up16(t.Tnu.size() * 8) +
-                       up16(t.init_pairs.size() * 4);
+                       up16(t.init_pairs.size() * 4) + up16(t.rows_pool.size() * 2);
         max_na = std::max(max_na, t.na); max_W = std::max(max_W, t.W); max_wpp = std::max(max_wpp, t.wpp);
+        max_m = std::max(max_m, t.m);
         b->out_offset[i + 1] = b->out_offset[i] + t.na;
         b->bucket_offset[i] = static_cast<int64_t>(b->total_bucket_words);
         b->total_bucket_words += static_cast<size_t>(t.nb) * t.na;
@@ -575,6 +589,7 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         d.Tnu = static_cast<const uint64_t *>(put(t.Tnu.data(), t.Tnu.size() * 8));
         d.init_pairs = static_cast<const uint32_t *>(put(t.init_pairs.data(), t.init_pairs.size() * 4));
         d.n_init_pairs = static_cast<int32_t>(t.init_pairs.size());
+        d.rows_pool = static_cast<const uint16_t *>(put(t.rows_pool.data(), t.rows_pool.size() * 2));
         d.S1 = b->d_buckets + b->bucket_offset[i];
         d.S2lo = b->d_buckets + b->total_bucket_words + b->bucket_offset[i];
         d.S2hi = b->d_buckets + 2 * b->total_bucket_words + b->bucket_offset[i];
@@ -600,7 +615,8 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     b->bp.n_inst = n_inst;
     b->bp.coupled = b->t[0].coupled ? 1 : 0;
     b->bp.scan = b->t[0].scan;
-    b->bp.max_wpp = max_wpp; b->bp.max_na = max_na; b->bp.max_W = max_W;
+    b->bp.max_wpp = max_wpp; b->bp.max_na = max_na; b->bp.max_W = max_W; b->bp.max_m = max_m;
+    b->bp.lanes = 1;
     b->bp.total_work = work;
     if ((rc = batch_shape(ctx, b, 0)) != MCPD_OK) { mcpd_batch_destroy(b); return rc; }
     CU(cudaEventCreate(&b->ev0));
@@ -615,7 +631,7 @@ int mcpd_batch_info(const mcpd_batch *b, int64_t info[16]) {
     std::memset(info, 0, 16 * sizeof(int64_t));
     info[0] = b->total_active; info[1] = b->bp.n_inst; info[2] = b->total_slots; info[3] = b->bp.max_na;
     info[4] = b->warps; info[5] = b->grid; info[6] = b->pairs; info[7] = static_cast<int64_t>(b->smem);
-    info[8] = 1;   // lanes per pair
+    info[8] = b->bp.lanes;
     return MCPD_OK;
 }
 
@@ -625,10 +641,10 @@ int mcpd_batch_offsets(const mcpd_batch *b, int64_t *offsets) {
     return MCPD_OK;
 }
 
-int mcpd_batch_set_shape(mcpd_ctx *ctx, mcpd_batch *b, int32_t warps_per_block) {
+int mcpd_batch_set_shape(mcpd_ctx *ctx, mcpd_batch *b, int32_t lanes_per_pair, int32_t warps_per_block) {
     if (!ctx || !b) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
-    return batch_shape(ctx, b, warps_per_block);
+    return batch_shape(ctx, b, warps_per_block, lanes_per_pair);
 }
 
 int mcpd_batch_run_async(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev) {
@@ -723,23 +739,19 @@ int mcpd_batch_fetch(mcpd_ctx *ctx, const mcpd_batch *b, int32_t inst, int what,
     return MCPD_OK;
 }
 
-// Time each candidate launch shape on the batch itself (reps runs each after one warm-up run)
-// and keep the fastest.  times[c] receives the mean milliseconds of candidate c.
-int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *b, const int32_t *cand_warps, int32_t n_cand,
-                        int32_t reps, double *est_dev, double *se_dev, int32_t *best_warps,
-                        double *times) {
-    if (!ctx || !b || !cand_warps || n_cand < 1 || reps < 1 || !est_dev || !se_dev) return MCPD_EINVAL;
+// Time each candidate launch shape (lanes per pair, warps per block) on the batch itself (reps
+// timed decodes after one warm-up each) and keep the fastest; times[c] receives the mean
+// milliseconds of candidate c (-1 if it does not fit).
+int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *b, const int32_t *cand_lanes,
+                        const int32_t *cand_warps, int32_t n_cand, int32_t reps, double *est_dev,
+                        double *se_dev, int32_t *best_index, double *times) {
+    if (!ctx || !b || !cand_lanes || !cand_warps || n_cand < 1 || reps < 1 || !est_dev || !se_dev) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
-    const size_t per_warp = static_cast<size_t>(b->bp.max_wpp) * (128 + 4 * mcpd::kYSlots) + 4;
-    const int cap = mcpd::pairs_max_threads(b->bp.coupled, b->bp.scan, 0, true) / 32;
-    const int fit = static_cast<int>(std::min<size_t>(cap, ctx->smem_optin / per_warp));
     double best = 1e300;
-    int32_t best_w = 0;
+    int32_t best_c = -1;
     for (int32_t c = 0; c < n_cand; ++c) {
-        const int w = cand_warps[c];
-        if (w < 1 || w > fit) { if (times) times[c] = -1.0; continue; }
-        int rc = batch_shape(ctx, b, w);
-        if (rc != MCPD_OK) return rc;
+        int rc = batch_shape(ctx, b, cand_warps[c], cand_lanes[c]);
+        if (rc != MCPD_OK) { if (times) times[c] = -1.0; ctx->err.clear(); continue; }
         double total = 0.0;
         for (int32_t r = 0; r <= reps; ++r) {
             if ((rc = mcpd_batch_run_async(ctx, b, est_dev, se_dev)) != MCPD_OK) return rc;
@@ -749,11 +761,11 @@ int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *b, const int32_t *cand_warps,
         }
         const double mean = total / reps;
         if (times) times[c] = mean;
-        if (mean < best) { best = mean; best_w = w; }
+        if (mean < best) { best = mean; best_c = c; }
     }
-    if (best_w == 0) return set_err(ctx, MCPD_EINVAL, "no candidate shape fits");
-    if (best_warps) *best_warps = best_w;
-    return batch_shape(ctx, b, best_w);
+    if (best_c < 0) return set_err(ctx, MCPD_EINVAL, "no candidate shape fits");
+    if (best_index) *best_index = best_c;
+    return batch_shape(ctx, b, cand_warps[best_c], cand_lanes[best_c]);
 }
 
 }  // extern "C"

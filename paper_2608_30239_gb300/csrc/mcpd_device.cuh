@@ -1,0 +1,33 @@
+// Device helpers shared by the sampling kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mcpd {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32 S-box with the Weyl
+// key schedule.
+static __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Add G and G^2 (128-bit, carried into the high word) of one slot to bucket N*_p - 1.
+static __device__ __forceinline__ void bucket_add(unsigned long long *S1, unsigned long long *S2lo,
+                                           unsigned long long *S2hi, int na, int bkt, int j, long long g) {
+    const size_t idx = static_cast<size_t>(bkt) * na + j;
+    atomicAdd(&S1[idx], static_cast<unsigned long long>(g));
+    const unsigned long long a = static_cast<unsigned long long>(g < 0 ? -g : g);
+    const unsigned long long lo = a * a, hi = __umul64hi(a, a);
+    const unsigned long long old = atomicAdd(&S2lo[idx], lo);
+    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry) atomicAdd(&S2hi[idx], hi + carry);
+}
+
+}  // namespace mcpd

@@ -43,6 +43,7 @@ struct Tables {
     std::vector<int32_t> active;      // [na] original index of active clone a, ascending
     std::vector<uint64_t> alias;      // [na] prob (low 32) | alias index (high 32)
     std::vector<uint16_t> rows;       // [na * kRow] byte offset of the pool's count | y << 15
+    std::vector<uint16_t> rows_pool;  // [na * kRow] pool id | y << 15, 0xFFFF past the clone's pools
     std::vector<uint64_t> T;          // [kTSide * kTSide]
     std::vector<uint64_t> Tnu;        // [na] or empty
     std::vector<uint32_t> init_pairs; // even clone ids a with Tnu[a] or Tnu[a+1] nonzero
@@ -107,6 +108,7 @@ struct InstDesc {
     const uint64_t *T;                // [kTSide * kTSide]
     const uint64_t *Tnu;              // [na] or null
     const uint32_t *init_pairs;       // [n_init_pairs] even clone ids with a nonzero threshold
+    const uint16_t *rows_pool;        // [na * kRow] pool id | y << 15 (lane-group kernels)
     unsigned long long *S1, *S2lo, *S2hi, *bcount;   // this instance's N*_p buckets
     int32_t n_init_pairs, pad0;
     int32_t na, W, wpp, deg, nb, dummy_word_index;
@@ -122,6 +124,7 @@ struct InstDesc {
 struct BParams {
     const InstDesc *insts;
     int32_t n_inst, coupled, scan, max_wpp;
+    int32_t lanes, max_m;             // lanes per pair (1, 8, 16, 32); largest pool count
     long long total_work;
     long long *rep_acc;               // [pairs][max_na]
     long long *slot_acc;              // [pairs][max_na]
@@ -135,6 +138,10 @@ struct BParams {
 
 // Launchers (mcpd_kernels.cu).
 int launch_batch(const BParams &bp, int grid, int block, size_t smem, void *stream);
+int launch_group(const BParams &bp, int grid, int block, size_t smem, void *stream);
+int set_group_smem(int lanes, size_t bytes);
+int group_max_threads(int lanes);
+int group_occupancy(int lanes, int block, size_t smem, int *blocks_per_sm);
 int set_batch_smem(size_t bytes);
 int pairs_max_threads(int coupled, int scan, int udeg, bool batch);
 int batch_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm);

@@ -15,23 +15,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "mcpd_device.cuh"
 #include "mcpd_internal.h"
 
 namespace mcpd {
 namespace {
-
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the 4x32 S-box with the Weyl
-// key schedule.
-__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        if (round) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    }
-    return c;
-}
 
 // The estimator's integer bookkeeping.  Swapping the sums in
 // L H_{k:l} = sum_{r=k}^{l} [X_r + sum_{s>=1} (X_{r+s} - Y_{r+s-1})] gives
@@ -40,18 +28,6 @@ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 // W(u) = sum_{v<=u} w(v) (quadratic, then linear).  Uncoupled chains (Algorithms 1/2) use
 // w(t) = 1{b <= t <= b + T - 1}.  The kernel adds -+W at every flip and closes the open intervals
 // at the end of a replication.
-
-// Add G and G^2 (128-bit, carried into the high word) of one slot to bucket N*_p - 1.
-__device__ __forceinline__ void bucket_add(unsigned long long *S1, unsigned long long *S2lo,
-                                           unsigned long long *S2hi, int na, int bkt, int j, long long g) {
-    const size_t idx = static_cast<size_t>(bkt) * na + j;
-    atomicAdd(&S1[idx], static_cast<unsigned long long>(g));
-    const unsigned long long a = static_cast<unsigned long long>(g < 0 ? -g : g);
-    const unsigned long long lo = a * a, hi = __umul64hi(a, a);
-    const unsigned long long old = atomicAdd(&S2lo[idx], lo);
-    const unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
-    if (hi + carry) atomicAdd(&S2hi[idx], hi + carry);
-}
 
 // One persistent kernel for a single instance (BATCH = false: tables staged in shared memory,
 // parameters from KParams) or for many instances in one launch (BATCH = true: tables read through

@@ -217,12 +217,14 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
     t.dummy_word_index = t.W + (m >> 2);
     t.dummy_word = 2u << (8 * (m & 3));
     t.rows.assign(static_cast<size_t>(na) * kRow, t.dummy_entry);
+    t.rows_pool.assign(static_cast<size_t>(na) * kRow, 0xFFFFu);
     for (int32_t a = 0; a < na; ++a) {
         int32_t i = t.active[a];
         int32_t l = 0;
         for (int32_t e = d->clone_ptr[i]; e < d->clone_ptr[i + 1]; ++e, ++l) {
             int32_t j = d->clone_pools[e];
             t.rows[static_cast<size_t>(a) * kRow + l] = static_cast<uint16_t>(count_offset(j) | (y[j] ? 0x8000u : 0u));
+            t.rows_pool[static_cast<size_t>(a) * kRow + l] = static_cast<uint16_t>(j | (y[j] ? 0x8000u : 0u));
         }
     }
 

@@ -101,13 +101,13 @@ def lib(build_if_missing: bool = False):
             "mcpd_batch_destroy": (None, [P]),
             "mcpd_batch_info": (C.c_int, [P, P]),
             "mcpd_batch_offsets": (C.c_int, [P, P]),
-            "mcpd_batch_set_shape": (C.c_int, [P, P, C.c_int32]),
+            "mcpd_batch_set_shape": (C.c_int, [P, P, C.c_int32, C.c_int32]),
             "mcpd_batch_run_async": (C.c_int, [P, P, P, P]),
             "mcpd_batch_capture_graph": (C.c_int, [P, P, P, P]),
             "mcpd_batch_launch_graph": (C.c_int, [P, P]),
             "mcpd_batch_collect": (C.c_int, [P, P, C.POINTER(mcpd_stats)]),
             "mcpd_batch_fetch": (C.c_int, [P, P, C.c_int32, C.c_int, P, C.c_size_t]),
-            "mcpd_batch_autotune": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, P, P, P]),
+            "mcpd_batch_autotune": (C.c_int, [P, P, P, P, C.c_int32, C.c_int32, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -364,9 +364,9 @@ class Batch:
         lib().mcpd_batch_info(self.h, _ptr(info))
         return info
 
-    def set_shape(self, warps_per_block):
-        self.ctx.check(lib().mcpd_batch_set_shape(self.ctx.h, self.h, int(warps_per_block)),
-                       "mcpd_batch_set_shape")
+    def set_shape(self, warps_per_block=0, lanes_per_pair=1):
+        self.ctx.check(lib().mcpd_batch_set_shape(self.ctx.h, self.h, int(lanes_per_pair),
+                                                  int(warps_per_block)), "mcpd_batch_set_shape")
         self.info = self._info()
 
     def run_async(self, est_dev, se_dev):
@@ -396,15 +396,19 @@ class Batch:
             out[key] = a if what == MCPD_FETCH_COUNT else a.reshape(self.nb[i], self.na[i])
         return out
 
-    def autotune(self, est_dev, se_dev, candidates=(4, 6, 8, 12, 16), reps=1):
-        cand = np.asarray(candidates, np.int32)
+    def autotune(self, est_dev, se_dev, candidates=((1, 0), (8, 0), (16, 0), (32, 0)), reps=1):
+        """candidates: (lanes per pair, warps per block) pairs (0 warps: as many as fit).  Returns
+        the chosen pair and {pair: mean ms} (-1 where a candidate does not fit)."""
+        cand = [(int(a), int(b)) for a, b in candidates]
+        lanes = np.asarray([c[0] for c in cand], np.int32)
+        warps = np.asarray([c[1] for c in cand], np.int32)
         times = np.zeros(len(cand))
         best = C.c_int32()
-        self.ctx.check(lib().mcpd_batch_autotune(self.ctx.h, self.h, _ptr(cand), len(cand), int(reps),
-                                                 _ptr(est_dev), _ptr(se_dev), C.byref(best), _ptr(times)),
-                       "mcpd_batch_autotune")
+        self.ctx.check(lib().mcpd_batch_autotune(self.ctx.h, self.h, _ptr(lanes), _ptr(warps), len(cand),
+                                                 int(reps), _ptr(est_dev), _ptr(se_dev), C.byref(best),
+                                                 _ptr(times)), "mcpd_batch_autotune")
         self.info = self._info()
-        return int(best.value), dict(zip((int(c) for c in cand), (float(t) for t in times)))
+        return cand[int(best.value)], dict(zip(cand, (float(t) for t in times)))
 
     def close(self):
         if getattr(self, "h", None):
