@@ -142,6 +142,82 @@ def cpu_oracle_sample(seconds: float, steps_label: str = ""):
             "seconds": dt, "site_updates": site_updates}
 
 
+def batched_leg(ctx, device, slots_per_instance=1024, count=512, sweeps=20, seed=11, limit_sweeps=100):
+    """The uneven batch: `count` instances with n ~ U[200, 5000], m = round(n / 13), k ~ U{4..8},
+    1-6 positives, fp ~ U[.005, .1], fn ~ U[.02, .25], q = positives / n; each with its own slots
+    and a horizon of `sweeps` sweeps; one persistent launch, launch shape (lanes per pair, warps per
+    block) chosen by the autotuner (cached per GPU and shape).  A pair that has not met after
+    `limit_sweeps` sweeps is stopped (its slot is left out and counted): some low-noise instances
+    have meeting times far beyond what a timed step can wait for."""
+    import torch
+
+    import synth
+    from paper_2608_30239_gb300 import autotune, mcpd
+    stream = torch.cuda.Stream(device)         # graph capture needs a non-default stream
+    ctx = mcpd.Context(device, stream=stream)
+    t0 = time.perf_counter()
+    insts = synth.batched_configs(count, seed=seed)
+    params = [dict(slots=slots_per_instance, horizon=sweeps * inst.n, seed=5000 + i, instance_id=i,
+                   step_limit=limit_sweeps * inst.n) for i, inst in enumerate(insts)]
+    batch = mcpd.Batch(ctx, insts, params, order_mode=1)
+    t_setup = time.perf_counter() - t0
+    est = torch.empty(batch.total_active, dtype=torch.float64, device=f"cuda:{device}")
+    se = torch.empty_like(est)
+    name = torch.cuda.get_device_name(device)
+    shape, times, cached = autotune.tuned_shape(batch, est, se, name)
+    batch.run_async(est, se)                     # warm-up with the chosen shape
+    batch.collect(allow_step_limit=True)
+    batch.capture_graph(est, se)
+    ms = []
+    for _ in range(2):
+        batch.launch_graph()
+        st = batch.collect(allow_step_limit=True)
+        ms.append(st["kernel_ms"])
+    out = {"instances": count, "slots_per_instance": slots_per_instance, "horizon_sweeps": sweeps,
+           "clones_total": int(sum(inst.n for inst in insts)), "setup_s": t_setup,
+           "graph_ms": statistics.mean(ms), "site_updates_per_step": st["site_updates"],
+           "site_updates_per_s": st["site_updates"] / (statistics.mean(ms) / 1000.0),
+           "replications_per_s": st["reps_retained"] / (statistics.mean(ms) / 1000.0),
+           "step_limit_sweeps": limit_sweeps, "step_limit_hits": st["step_limit_hits"],
+           "slots_total": count * slots_per_instance,
+           "shape_lanes_warps": list(shape), "autotune_ms": {str(k): v for k, v in times.items()},
+           "autotune_cached": cached}
+    batch.close()
+    stream.synchronize()
+    ctx.close()
+    return out
+
+
+def learned_leg(ctx, device, train=512, slots=1 << 21):
+    """Time to a largest per-clone SE of 0.005 on the bench instance: paper score weights with the
+    all-negative start versus paper weights with initial marginals from the MLP trained (on the GPU)
+    on `train` generated high-noise instances.  Each variant is decoded once at P = `slots`; the
+    slot means are i.i.d., so the time to SE <= 0.005 is projected as ms * (max SE / 0.005)^2."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2608_30239_gb300 import learned, learned_ab
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    tr = [learned_ab.high_noise_like(int(i), 100000) for i in rng.permutation(train)]
+    p_hat, _, _ = learned.plain_marginals(ctx, tr, slots=1024, sweeps=10)
+    seg = learned.segments(tr)
+    X = learned.features(ctx, tr)
+    model = learned.MLP(ctx, seed=0)
+    model.fit(X, seg, torch.tensor(learned.weight_target(p_hat, seg, mode="positive"), dtype=torch.float32, device=X.device),
+              torch.tensor(np.clip(p_hat, 0, 1), dtype=torch.float32, device=X.device), epochs=30, batch_segments=64)
+    t_train = time.perf_counter() - t0
+    inst = synth.high_noise_config()
+    _, nu = learned.learned_inputs(model, learned.features(ctx, [inst]), learned.segments([inst]), nu_floor=0.02)
+    out = {"train_instances": train, "train_s": t_train, "slots": slots}
+    for name, kw in (("paper_weights_allneg", {}), ("paper_weights_learned_nu", dict(init=nu))):
+        mse, ms, _ = learned.decode_max_se(ctx, [inst], slots, 29.4, 7, **kw)
+        out[name] = {"max_se": mse, "kernel_ms": ms, "projected_s_to_se_0.005": ms / 1000.0 * (mse / 0.005) ** 2}
+    out["speedup"] = out["paper_weights_allneg"]["projected_s_to_se_0.005"] / out["paper_weights_learned_nu"]["projected_s_to_se_0.005"]
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -176,6 +252,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batch leg")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned time-to-SE leg")
     ap.add_argument("--slots", type=int, default=SLOTS,
                     help="slots per GPU; the budget scales with it so the horizon B stays 38146 "
                          "(smaller cases are for profiling captures)")
@@ -296,6 +374,10 @@ def main():
                     "d2h_bytes_per_step": d2h, "seconds_per_step": statistics.mean(e2e_times)},
             "gpu_launches": 2 * args.steps,
             "clocks": clk}
+    if rank == 0 and not args.no_batched:
+        line["batched"] = batched_leg(ctx, device)
+    if rank == 0 and not args.no_learned:
+        line["time_to_se"] = learned_leg(ctx, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample(args.cpu_seconds)
     if rank == 0:

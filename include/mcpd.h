@@ -206,7 +206,8 @@ int mcpd_batch_fetch(mcpd_ctx *ctx, const mcpd_batch *batch, int32_t inst, int w
                      void *host_dst, size_t bytes);
 /* Autotuner: time each candidate shape (cand_lanes[c] lanes per pair, cand_warps[c] warps per
  * block; reps timed decodes after one warm-up each) and keep the fastest; best_index receives its
- * index, times[c] candidate c's mean milliseconds (-1 if it does not fit). */
+ * index, times[c] candidate c's mean milliseconds (-1 if it does not fit).  Runs that stop a
+ * pair at its step limit still count as timings. */
 int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *batch, const int32_t *cand_lanes,
                         const int32_t *cand_warps, int32_t n_cand, int32_t reps, double *est_dev,
                         double *se_dev, int32_t *best_index, double *times);

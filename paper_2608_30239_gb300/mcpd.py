@@ -380,10 +380,14 @@ class Batch:
     def launch_graph(self):
         self.ctx.check(lib().mcpd_batch_launch_graph(self.ctx.h, self.h), "mcpd_batch_launch_graph")
 
-    def collect(self):
+    def collect(self, allow_step_limit=False):
         st = mcpd_stats()
-        self.ctx.check(lib().mcpd_batch_collect(self.ctx.h, self.h, C.byref(st)), "mcpd_batch_collect")
-        return st.as_dict()
+        rc = lib().mcpd_batch_collect(self.ctx.h, self.h, C.byref(st))
+        if rc != MCPD_OK and not (allow_step_limit and rc == MCPD_ESTEP_LIMIT):
+            self.ctx.check(rc, "mcpd_batch_collect")
+        out = st.as_dict()
+        out["status"] = rc
+        return out
 
     def buckets(self, i):
         out = {}
