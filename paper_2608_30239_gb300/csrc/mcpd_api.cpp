@@ -10,10 +10,6 @@
 
 #include "mcpd_internal.h"
 
-namespace mcpd {
-int pairs_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm);
-}
-
 struct mcpd_plan {
     mcpd_ctx *ctx = nullptr;
     mcpd::Tables t;
@@ -102,31 +98,21 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     const mcpd::Tables &t = pl->t;
     if (cudaSetDevice(ctx->device) != cudaSuccess) { delete pl; return set_err(ctx, MCPD_ECUDA, "cudaSetDevice"); }
 
-    // Launch shape: tables first in shared memory, then one 32-lane region per warp.
+    // Launch shape: tables first in shared memory, then one 32-column region per warp and the
+    // Y regions.
     const size_t tables = ((static_cast<size_t>(t.na) * 24 + mcpd::kTSide * mcpd::kTSide * 8) + 15) / 16 * 16;
-    const size_t per_warp = static_cast<size_t>(t.wpp) * (128 + 4 * mcpd::kYSlots) + 4;
-    if (tables + per_warp > ctx->smem_optin) {
+    mcpd::PairsShape shape;
+    rc = mcpd::pairs_shape(t.coupled, t.scan, t.udeg, false, tables, t.wpp, ctx->smem_optin, t.P,
+                           ctx->sm_count, 0, &shape);
+    if (rc != MCPD_OK) {
         delete pl;
-        return set_err(ctx, MCPD_ETOO_LARGE, "instance too large for the one-thread-per-pair layout");
+        return set_err(ctx, rc, rc == MCPD_ETOO_LARGE ? "instance too large for the one-thread-per-pair layout"
+                                                      : "launch shape (cudaFuncSetAttribute / occupancy)");
     }
-    const int max_warps = mcpd::pairs_max_threads(t.coupled, t.scan, t.udeg, false) / 32;
-    int warps = static_cast<int>(std::min<size_t>(max_warps, (ctx->smem_optin - tables) / per_warp));
-    // Two blocks per SM (each with its own copy of the tables) when that holds more warps in
-    // total than one block does.
-    const size_t half = ctx->smem_optin / 2;
-    if (half > tables) {
-        const int w2 = static_cast<int>(std::min<size_t>(max_warps, (half - tables) / per_warp));
-        if (2 * w2 > warps) warps = w2;
-    }
+    const int warps = shape.warps;
     pl->block = warps * 32;
-    pl->smem = tables + per_warp * warps;
-    if (mcpd::set_pairs_smem(pl->smem, t.coupled) != MCPD_OK) {
-        delete pl;
-        return set_err(ctx, MCPD_ECUDA, "cudaFuncSetAttribute(max dynamic shared memory)");
-    }
-    int per_sm = 1;
-    if (mcpd::pairs_occupancy(t.coupled, t.scan, pl->block, pl->smem, &per_sm) != MCPD_OK || per_sm < 1) per_sm = 1;
-    pl->grid = ctx->sm_count * per_sm;
+    pl->smem = shape.smem;
+    pl->grid = ctx->sm_count * shape.per_sm;
     pl->pairs = static_cast<long long>(pl->grid) * pl->block;
 
     mcpd::KParams &kp = pl->kp;
@@ -184,6 +170,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     kp.slot_offset = t.slot_offset; kp.trace_stride = t.trace_stride;
     kp.seed = t.seed; kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
+    kp.y_regions = shape.y_regions;
     CU(cudaEventCreate(&pl->ev0));
     CU(cudaEventCreate(&pl->ev1));
     CU(cudaStreamSynchronize(ctx->stream));
@@ -425,27 +412,33 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
     if (lanes != 1 && lanes != 8 && lanes != 16 && lanes != 32)
         return set_err(ctx, MCPD_EINVAL, "lanes per pair must be 1, 8, 16 or 32");
     if (lanes > 1 && !b->bp.coupled) return set_err(ctx, MCPD_EINVAL, "lane groups run coupled batches only");
-    const size_t per_warp = lanes == 1 ? static_cast<size_t>(b->bp.max_wpp) * (128 + 4 * mcpd::kYSlots) + 4
-                                       : static_cast<size_t>(32 / lanes) * 2 * b->bp.max_wpp * 4;
-    const int cap = (lanes == 1 ? mcpd::pairs_max_threads(b->bp.coupled, b->bp.scan, 0, true)
-                                : mcpd::group_max_threads(lanes)) / 32;
-    const int fit = static_cast<int>(std::min<size_t>(cap, ctx->smem_optin / per_warp));
-    if (fit < 1) return set_err(ctx, MCPD_ETOO_LARGE, "largest instance does not fit one warp of pair state");
-    if (warps <= 0) warps = fit;
-    if (warps > fit) return set_err(ctx, MCPD_EINVAL, "warps per block above what the kernel allows");
-    b->warps = warps;
-    b->block = warps * 32;
-    b->smem = per_warp * warps;
-    b->bp.lanes = lanes;
     int per_sm = 1;
     if (lanes == 1) {
-        if (mcpd::set_batch_smem(b->smem) != MCPD_OK) return set_err(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
-        if (mcpd::batch_occupancy(b->bp.coupled, b->bp.scan, b->block, b->smem, &per_sm) != MCPD_OK || per_sm < 1)
-            per_sm = 1;
+        mcpd::PairsShape shape;
+        const int rc = mcpd::pairs_shape(b->bp.coupled, b->bp.scan, 0, true, 0, b->bp.max_wpp, ctx->smem_optin, 0,
+                                         ctx->sm_count, warps, &shape);
+        if (rc == MCPD_ETOO_LARGE) return set_err(ctx, rc, "largest instance does not fit one warp of pair state");
+        if (rc == MCPD_EINVAL) return set_err(ctx, rc, "warps per block above what the kernel allows");
+        if (rc != MCPD_OK) return set_err(ctx, rc, "cudaFuncSetAttribute / occupancy");
+        warps = shape.warps;
+        b->smem = shape.smem;
+        b->bp.y_regions = shape.y_regions;
+        per_sm = shape.per_sm;
     } else {
+        const size_t per_warp = static_cast<size_t>(32 / lanes) * 2 * b->bp.max_wpp * 4;
+        const int cap = mcpd::group_max_threads(lanes) / 32;
+        const int fit = static_cast<int>(std::min<size_t>(cap, ctx->smem_optin / per_warp));
+        if (fit < 1) return set_err(ctx, MCPD_ETOO_LARGE, "largest instance does not fit one warp of pair state");
+        if (warps <= 0) warps = fit;
+        if (warps > fit) return set_err(ctx, MCPD_EINVAL, "warps per block above what the kernel allows");
+        b->smem = per_warp * warps;
+        b->bp.y_regions = 0;
         if (mcpd::set_group_smem(lanes, b->smem) != MCPD_OK) return set_err(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
-        if (mcpd::group_occupancy(lanes, b->block, b->smem, &per_sm) != MCPD_OK || per_sm < 1) per_sm = 1;
+        if (mcpd::group_occupancy(lanes, warps * 32, b->smem, &per_sm) != MCPD_OK || per_sm < 1) per_sm = 1;
     }
+    b->warps = warps;
+    b->block = warps * 32;
+    b->bp.lanes = lanes;
     b->grid = ctx->sm_count * per_sm;
     b->pairs = static_cast<long long>(b->grid) * b->block / lanes;
     if (b->pairs > b->scratch_pairs) {

@@ -23,7 +23,7 @@ namespace mcpd {
 
 constexpr int kRow = 8;              // pool entries per clone row (one 16-byte shared load)
 constexpr int kTSide = kRow + 1;     // acceptance table is kTSide x kTSide, indexed 9 n+ + n-
-constexpr int kYSlots = 4;           // shared-memory Y-chain slots per warp (pairs not yet met)
+constexpr int kWarpsPerYRegion = 8; // one 32-column Y region per 8 warps (pairs not yet met)
 constexpr int kMaxClones = 65535;
 constexpr int kMaxPools = 1022;      // pool byte offsets must fit 16 bits
 constexpr int kMaxPoolSize = 255;    // per-pool counts are bytes
@@ -52,7 +52,7 @@ struct Tables {
     int32_t udeg = 0;                 // d if every active clone sits in exactly d pools, else 0
     int32_t W = 0;                    // bit-set words per chain
     int32_t Mp = 0;                   // count words (four pools per word, the padding pool included)
-    int32_t wpp = 0;                  // words per pair = W + Mp (X chain; Y lives in global memory)
+    int32_t wpp = 0;                  // words per column = W + Mp (one chain)
     uint16_t dummy_entry = 0;         // row entry of the padding pool
     uint32_t dummy_word = 0;          // initial value of the word holding the padding pool
     int32_t dummy_word_index = 0;
@@ -79,7 +79,7 @@ struct KParams {
     long long *slot_acc;              // [pairs][na]
     uint32_t *touched_rep;            // [pairs][W]
     uint32_t *touched_slot;           // [pairs][W]
-    uint32_t *y_state;                // [pairs][wpp] Y chain of pairs that have not met
+    uint32_t *y_state;                // [pairs / 32][wpp][32] fallback Y columns (pairs not yet met)
     unsigned long long *S1;           // [nb][na]
     unsigned long long *S2lo;         // [nb][na]
     unsigned long long *S2hi;         // [nb][na]
@@ -99,6 +99,7 @@ struct KParams {
     uint32_t instance;
     int32_t warps;
     uint32_t smem_tables;             // bytes of staged tables at the start of shared memory
+    int32_t y_regions;                // 32-column Y regions in shared memory
 };
 
 // One instance of a batched launch (plain types; read by the kernels from global memory).
@@ -130,11 +131,26 @@ struct BParams {
     long long *slot_acc;              // [pairs][max_na]
     uint32_t *touched_rep;            // [pairs][max_W]
     uint32_t *touched_slot;           // [pairs][max_W]
-    uint32_t *y_state;                // [pairs][max_wpp]
+    uint32_t *y_state;                // [pairs / 32][max_wpp][32] fallback Y columns
     unsigned long long *counters;
     int *error;
     int32_t max_na, max_W;
+    int32_t y_regions, pad2;          // 32-column Y regions in shared memory
 };
+
+// Launch shape of the one-thread-per-pair kernel (mcpd_kernels.cu).
+struct PairsShape {
+    int warps = 0;                    // warps per block
+    int y_regions = 0;                // 32-column Y regions per block
+    int per_sm = 1;                   // resident blocks per SM
+    size_t smem = 0;                  // dynamic shared memory per block
+};
+int pairs_y_regions(int coupled, int warps);
+size_t pairs_smem_bytes(size_t tables, int wpp, int warps, int y_regions);
+// tables: bytes staged at the start of shared memory (0 for batches); wpp: words per column;
+// P: slots of a single instance (0 = do not shape by rounds); warps: requested warps (0 = auto).
+int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int wpp, size_t smem_optin,
+                long long P, int sm_count, int warps, PairsShape *out);
 
 // Launchers (mcpd_kernels.cu).
 int launch_batch(const BParams &bp, int grid, int block, size_t smem, void *stream);
@@ -142,9 +158,7 @@ int launch_group(const BParams &bp, int grid, int block, size_t smem, void *stre
 int set_group_smem(int lanes, size_t bytes);
 int group_max_threads(int lanes);
 int group_occupancy(int lanes, int block, size_t smem, int *blocks_per_sm);
-int set_batch_smem(size_t bytes);
 int pairs_max_threads(int coupled, int scan, int udeg, bool batch);
-int batch_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm);
 int launch_finalize_batch(const InstDesc *insts, int n_inst, const int32_t *clone_inst,
                           const int32_t *clone_local, long long total_clones, double *est,
                           double *se, void *stream);
@@ -155,6 +169,5 @@ int launch_finalize(const unsigned long long *S1, const unsigned long long *S2lo
 int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, long long n,
                   void *stream);
 int pairs_max_smem(int device, size_t *bytes);
-int set_pairs_smem(size_t bytes, int coupled);
 
 }  // namespace mcpd

@@ -27,7 +27,10 @@ namespace {
 // so a chain whose bit j is 1 on the time interval [s, e] contributes +-(W(e) - W(s-1)) with
 // W(u) = sum_{v<=u} w(v) (quadratic, then linear).  Uncoupled chains (Algorithms 1/2) use
 // w(t) = 1{b <= t <= b + T - 1}.  The kernel adds -+W at every flip and closes the open intervals
-// at the end of a replication.
+// at the end of a replication.  Once a pair has met (X_t = Y_{t-1}), Y_t = X_{t+1}: a flip of X at
+// step t is also the flip of Y at step t, and the two events add to -+(W(t) - W(t-1)) = -+w(t).
+// The uncoupled flip event W(t) has the same clamp form, so both modes use
+// wstep(u) = clamp(u - s + 1, 0, cap) with (s, cap) = (k, L) or (b, T).
 
 // One persistent kernel for a single instance (BATCH = false: tables staged in shared memory,
 // parameters from KParams) or for many instances in one launch (BATCH = true: tables read through
@@ -35,14 +38,23 @@ namespace {
 // instance-major from one counter).
 // DEG > 0: every clone of the (single) instance sits in exactly DEG pools, so the pool loops have
 // a compile-time trip count and rows hold no padding entries; DEG = 0 handles any degree <= 8.
+//
+// Shared memory: [tables (single instance)] [one region per warp] [y_regions Y regions] [one
+// free mask per Y region].  A region is 32 columns of wpp words, word w of column c at word
+// 32 w + c, so the same byte offset (a row entry) addresses a pool's count in any column and the
+// 32 lanes of a warp touch 32 different banks.  Lane l's X chain is column l of its warp's
+// region.  A pair that has not met keeps its Y chain in a column of the Y regions (column l of
+// some region first, so that it shares no bank with its warp's other lanes), else in its own
+// column of the global fallback (same layout, one region per warp).  A free Y column is all zero
+// except, for DEG = 0, the padding pool's count.
 template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG>
 __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs_kernel(const KParams p, const BParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     uint4 *sRows = reinterpret_cast<uint4 *>(smem);
     unsigned long long *sAlias = nullptr, *sT = nullptr;
-    uint32_t *st;
-    int wpp;
+    int wpp, nyr;
+    uint32_t *regions;
     if constexpr (!BATCH) {
         sAlias = reinterpret_cast<unsigned long long *>(smem + static_cast<size_t>(p.na) * 16);
         sT = sAlias + p.na;
@@ -52,21 +64,21 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         }
         for (int i = threadIdx.x; i < kTSide * kTSide; i += blockDim.x) sT[i] = p.T[i];
         wpp = p.wpp;
-        st = reinterpret_cast<uint32_t *>(smem + p.smem_tables) + static_cast<size_t>(warp) * 32 * wpp + lane;
+        nyr = p.y_regions;
+        regions = reinterpret_cast<uint32_t *>(smem + p.smem_tables);
     } else {
         wpp = bp.max_wpp;
-        st = reinterpret_cast<uint32_t *>(smem) + static_cast<size_t>(warp) * 32 * wpp + lane;
+        nyr = bp.y_regions;
+        regions = reinterpret_cast<uint32_t *>(smem);
     }
-    unsigned char *cbase = reinterpret_cast<unsigned char *>(st);   // word w of this pair: st[w * 32]
-    for (int w = 0; w < wpp; ++w) st[w * 32] = 0u;                  // the pair's state starts empty
-    // kYSlots Y-chain slots per warp follow the warps' regions, then one free-slot mask per warp.
-    const int nwarps = blockDim.x >> 5;
-    uint32_t *ySlots = reinterpret_cast<uint32_t *>(smem + (BATCH ? 0 : p.smem_tables)) +
-                       static_cast<size_t>(nwarps) * 32 * wpp + static_cast<size_t>(warp) * kYSlots * wpp;
-    uint32_t *ymask = reinterpret_cast<uint32_t *>(smem + (BATCH ? 0 : p.smem_tables)) +
-                      static_cast<size_t>(nwarps) * (32 + kYSlots) * wpp + warp;
-    for (int w = lane; w < kYSlots * wpp; w += 32) ySlots[w] = 0u;
-    if (lane == 0) *ymask = (1u << kYSlots) - 1u;
+    const uint32_t region_words = 32u * static_cast<uint32_t>(wpp);
+    uint32_t *const st = regions + warp * region_words + lane;        // word w of X: st[w * 32]
+    unsigned char *const cbase = reinterpret_cast<unsigned char *>(st);
+    uint32_t *const yreg = regions + nwarps * region_words;
+    uint32_t *const ymask = yreg + nyr * region_words;
+    for (int w = 0; w < wpp; ++w) st[w * 32] = 0u;
+    for (uint32_t i = threadIdx.x; i < nyr * region_words; i += blockDim.x) yreg[i] = 0u;
+    if (static_cast<int>(threadIdx.x) < nyr) ymask[threadIdx.x] = 0xFFFFFFFFu;
     if constexpr (!BATCH) st[p.dummy_word_index * 32] = p.dummy_word;
     __syncthreads();
 
@@ -77,9 +89,9 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     uint32_t *trep = (BATCH ? bp.touched_rep : p.touched_rep) + gpair * stride_W;
     uint32_t *tslot = (BATCH ? bp.touched_slot : p.touched_slot) + gpair * stride_W;
     unsigned long long *counters = BATCH ? bp.counters : p.counters;
-    uint32_t *const yglob = (BATCH ? bp.y_state : p.y_state) + gpair * wpp;
-    uint32_t *ybase = yglob;          // the Y state in use: a shared-memory slot or the global fallback
-    int yslot = -1;
+    uint32_t *const yglob = (BATCH ? bp.y_state : p.y_state) + static_cast<size_t>(gpair >> 5) * region_words + lane;
+    uint32_t *ycol = yglob;           // the Y column in use (shared or global), while D != 0
+    int yslot = -1;                   // its index in the Y regions, -1 for the global column
 
     // Per-instance values (fixed for a single instance, reloaded when a batched slot changes
     // instance).
@@ -90,9 +102,16 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     unsigned long long *bS1 = nullptr, *bS2lo = nullptr, *bS2hi = nullptr, *bCount = nullptr;
     int na = 0, deg = 0, dummy_word_index = 0;
     uint32_t W = 0, B = 0, unit = 0, ell = 0, step_limit = 0, instance = 0, k0 = 0, k1 = 0;
-    uint32_t dummy_entry = 0, dummy_word = 0, gshift = 0;
+    uint32_t dummy_entry = 0, dummy_word = 0, gshift = 0, ws0 = 0, wcap = 0;
     long long kk = 0, LL = 0, burn = 0, length = 0, P = 0, slot_offset = 0, work_begin = 0, work_end = 0;
     int cur = -1;
+    auto clamp32 = [](long long v) -> uint32_t { return v < 0 ? 0u : (v > 0xFFFFFFFFll ? 0xFFFFFFFFu : static_cast<uint32_t>(v)); };
+    auto derive = [&]() {
+        gshift = 0;
+        while (((W + (1u << gshift) - 1) >> gshift) > 32) ++gshift;
+        ws0 = clamp32(COUPLED ? kk : burn);
+        wcap = clamp32(COUPLED ? LL : length);
+    };
     auto load_instance = [&](const InstDesc &d) {
         gRows = reinterpret_cast<const uint4 *>(d.rows); gAlias = reinterpret_cast<const unsigned long long *>(d.alias);
         gT = reinterpret_cast<const unsigned long long *>(d.T); Tnu = reinterpret_cast<const unsigned long long *>(d.Tnu);
@@ -105,8 +124,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         k0 = static_cast<uint32_t>(d.seed); k1 = static_cast<uint32_t>(d.seed >> 32);
         kk = d.k; LL = d.L; burn = d.burn; length = d.length; P = d.P; slot_offset = d.slot_offset;
         work_begin = d.work_begin; work_end = d.work_begin + d.P;
-        gshift = 0;
-        while (((W + (1u << gshift) - 1) >> gshift) > 64) ++gshift;
+        derive();
     };
     if constexpr (!BATCH) {
         Tnu = reinterpret_cast<const unsigned long long *>(p.Tnu);
@@ -118,8 +136,9 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         step_limit = static_cast<uint32_t>(p.step_limit); instance = p.instance;
         k0 = static_cast<uint32_t>(p.seed); k1 = static_cast<uint32_t>(p.seed >> 32);
         kk = p.k; LL = p.L; burn = p.burn; length = p.length; P = p.P; slot_offset = p.slot_offset;
-        while (((W + (1u << gshift) - 1) >> gshift) > 64) ++gshift;
+        derive();
     }
+    constexpr int NE = DEG > 0 ? DEG : kRow;       // row entries visited per clone
     auto rowAt = [&](uint32_t c) -> uint4 {
         if constexpr (BATCH) return __ldg(gRows + c); else return sRows[c];
     };
@@ -128,6 +147,14 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     };
     auto tAt = [&](uint32_t i) -> unsigned long long {
         if constexpr (BATCH) return __ldg(gT + i); else return sT[i];
+    };
+    auto entries = [&](const uint4 &row, uint32_t *ent) {
+        ent[0] = row.x & 0xFFFFu; ent[1] = row.x >> 16; ent[2] = row.y & 0xFFFFu; ent[3] = row.y >> 16;
+        ent[4] = row.z & 0xFFFFu; ent[5] = row.z >> 16; ent[6] = row.w & 0xFFFFu; ent[7] = row.w >> 16;
+    };
+    // Entry l of a row is a real pool (not past the clone's degree, not the padding pool).
+    auto real = [&](int l, const uint32_t *ent) -> bool {
+        return l < NE && (DEG > 0 || (l < deg && ent[l] != dummy_entry));
     };
     // Prefix sums of the estimator's per-time weights (see the comment on wprefix).
     auto wpre = [&](long long u) -> long long {
@@ -140,87 +167,90 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             return v < 0 ? 0 : (v > length ? length : v);
         }
     };
+    auto wstep = [&](uint32_t u) -> uint32_t { return u < ws0 ? 0u : min(u - ws0 + 1u, wcap); };
 
     bool alive = true;
     uint32_t slot_local = 0, slot_g = 0, r = 0, t = 0, S = 0, N = 0, tau = 0, D = 0;
-    uint32_t abort_t = 0xFFFFFFFFu, sysI = 0, reps_in_slot = 0;
-    unsigned long long rep_words = 0, slot_words = 0;
+    uint32_t abort_t = 0xFFFFFFFFu, t_end = 0, stop_unmet = 0, sysI = 0, reps_in_slot = 0;
+    uint32_t rep_words = 0, slot_words = 0;   // groups of 2^gshift bit words touched
     unsigned long long c_prog = 0, c_started = 0, c_retained = 0, c_aborted = 0, c_zero = 0,
                        c_limit = 0, c_sumtau = 0;
     uint32_t c_maxtau = 0;
 
-    // X counts are bytes in the interleaved pair region; a row entry holds the byte offset of the
-    // pool's count (bits 0-14) and the pool's outcome y (bit 15).  The Y chain's state lives in
-    // global memory (ybase: W bit words, then one count byte per pool) and is touched only while
-    // the pair has not met; it is all zero whenever the pair has met.
-    auto ycnt = [&](uint32_t e) -> uint8_t * {
-        const uint32_t off = e & 0x7FFFu;
-        return reinterpret_cast<uint8_t *>(ybase + W) + (((off >> 7) - W) * 4 + (off & 3u));
-    };
-    // Add delta (mod 256) to the X count (or, with Y, the global Y count) of every pool of c.
-    auto bump_counts = [&](uint32_t c, uint32_t delta, bool y) {
+    // Add delta (mod 256) to the counts of every pool of clone c in the column at `base`.
+    auto bump_counts = [&](uint32_t c, uint32_t delta, unsigned char *base) {
         const uint4 row = rowAt(c);
-        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
-                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
+        uint32_t ent[8];
+        entries(row, ent);
 #pragma unroll
         for (int l = 0; l < kRow; ++l) {
-            if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
-            uint8_t *cnt = y ? ycnt(ent[l]) : cbase + (ent[l] & 0x7FFFu);
-            *cnt = static_cast<uint8_t>(*cnt + delta);
+            if (!real(l, ent)) continue;
+            unsigned char *cnt = base + (ent[l] & 0x7FFFu);
+            *cnt = static_cast<unsigned char>(*cnt + delta);
         }
     };
-    // A pair that stops being met takes a free Y slot of its warp (bounded retries; the global
-    // region is the fallback) and returns it, emptied, when it meets again.
+    // A pair that stops being met takes a free Y column (column `lane` of a Y region first,
+    // then any free one; bounded tries), else its global column.
     auto acquire_y = [&]() {
-        for (int tries = 0; tries <= kYSlots; ++tries) {
-            const uint32_t fm = *reinterpret_cast<volatile uint32_t *>(ymask);
-            if (!fm) break;
-            const int sl = __ffs(fm) - 1;
-            if (atomicAnd(ymask, ~(1u << sl)) & (1u << sl)) { yslot = sl; ybase = ySlots + sl * wpp; return; }
+        yslot = -1;
+        for (int g = 0; g < nyr && yslot < 0; ++g)
+            if (atomicAnd(&ymask[g], ~(1u << lane)) & (1u << lane)) yslot = g * 32 + lane;
+        for (int g = 0; g < nyr && yslot < 0; ++g) {
+            for (int tries = 0; tries < 32; ++tries) {
+                const uint32_t fm = *reinterpret_cast<volatile uint32_t *>(&ymask[g]);
+                if (!fm) break;
+                const int c = __ffs(fm) - 1;
+                if (atomicAnd(&ymask[g], ~(1u << c)) & (1u << c)) { yslot = g * 32 + c; break; }
+            }
         }
-        yslot = -1;
-        ybase = yglob;
+        __threadfence_block();
+        ycol = yslot >= 0 ? yreg + (yslot >> 5) * region_words + (yslot & 31) : yglob;
+        if (DEG == 0) ycol[dummy_word_index * 32] = dummy_word;
     };
+    // Empty the Y column in use (every Y bit lies in a group marked in rep_words) and return it.
     auto release_y = [&]() {
-        if (yslot >= 0) atomicOr(ymask, 1u << yslot);
-        yslot = -1;
-        ybase = yglob;
-    };
-    // Empty the Y state in use (every Y bit lies in a word marked in rep_words).
-    auto clear_y = [&]() {
-        unsigned long long groups = rep_words;
+        unsigned char *yb = reinterpret_cast<unsigned char *>(ycol);
+        uint32_t groups = rep_words;
         while (groups) {
-            const int g = __ffsll(static_cast<long long>(groups)) - 1;
+            const int g = __ffs(groups) - 1;
             groups &= groups - 1;
             const uint32_t q0 = static_cast<uint32_t>(g) << gshift, q1 = min(W, q0 + (1u << gshift));
             for (uint32_t q = q0; q < q1; ++q) {
-                uint32_t yw = ybase[q];
+                uint32_t yw = ycol[q * 32];
                 if (!yw) continue;
-                ybase[q] = 0u;
-                while (yw) { const int b = __ffs(yw) - 1; yw &= yw - 1; bump_counts(q * 32 + b, 0xFFu, true); }
+                ycol[q * 32] = 0u;
+                while (yw) { const int b = __ffs(yw) - 1; yw &= yw - 1; bump_counts(q * 32 + b, 0xFFu, yb); }
             }
         }
+        if (DEG == 0) ycol[dummy_word_index * 32] = 0u;
+        __threadfence_block();
+        if (yslot >= 0) atomicOr(&ymask[yslot >> 5], 1u << (yslot & 31));
+        yslot = -1;
+        ycol = yglob;
     };
-    // The pre-lag update just flipped site I of X_0 and the start was random: Y_0 = X_0 goes to the
-    // global Y state (X_1 with bit I restored).
+    // The pre-lag update flipped site I of X_0 and the start was random: Y_0 = X_0 (X_1 with bit
+    // I restored) goes to the Y column.
     auto copy_y0 = [&](uint32_t qI, uint32_t bitI) {
-        unsigned long long groups = rep_words;
+        unsigned char *yb = reinterpret_cast<unsigned char *>(ycol);
+        uint32_t groups = rep_words;
         while (groups) {
-            const int g = __ffsll(static_cast<long long>(groups)) - 1;
+            const int g = __ffs(groups) - 1;
             groups &= groups - 1;
             const uint32_t q0 = static_cast<uint32_t>(g) << gshift, q1 = min(W, q0 + (1u << gshift));
             for (uint32_t q = q0; q < q1; ++q) {
                 uint32_t yw = st[q * 32] ^ (q == qI ? bitI : 0u);
                 if (!yw) continue;
-                ybase[q] = yw;
-                while (yw) { const int b = __ffs(yw) - 1; yw &= yw - 1; bump_counts(q * 32 + b, 1u, true); }
+                ycol[q * 32] = yw;
+                while (yw) { const int b = __ffs(yw) - 1; yw &= yw - 1; bump_counts(q * 32 + b, 1u, yb); }
             }
         }
     };
 
     auto start_rep = [&]() {
-        t = 0; D = 0; tau = 0; sysI = 0;
+        t = 0; D = 0; tau = 1; sysI = 0;      // tau = 1 unless the pre-lag update moves X
         abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
+        stop_unmet = min(abort_t, step_limit);
+        t_end = COUPLED ? min(max(ell, 1u), stop_unmet) : min(unit, step_limit);
         ++c_started;
         ++reps_in_slot;
         if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0 (clones with nu_i = 0 stay 0)
@@ -237,8 +267,8 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
                     if (u < Tnu[c]) {
                         const uint32_t q = c >> 5;
                         st[q * 32] |= 1u << (c & 31);
-                        bump_counts(c, 1u, false);
-                        rep_words |= 1ull << (q >> gshift);
+                        bump_counts(c, 1u, cbase);
+                        rep_words |= 1u << (q >> gshift);
                     }
                 }
             }
@@ -273,14 +303,14 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
 
     // End of a replication: empty the pair's state and the replication's accumulators; when `move`
     // (completed, so X_C = Y_{C-1}), first close the open intervals at C, which for a bit set in
-    // X_C adds W(C) - W(C-1) (coupled) or W(C) (uncoupled), and add the replication's G into the
-    // slot's sums.
+    // X_C adds W(C) - W(C-1) (coupled) or W(C) (uncoupled), both wstep(C), and add the
+    // replication's G into the slot's sums.
     auto finish_rep = [&](bool move, uint32_t C) {
-        const long long wX = move ? (COUPLED ? wpre(C) - wpre(static_cast<long long>(C) - 1) : wpre(C)) : 0;
-        if (COUPLED && D != 0) { clear_y(); release_y(); }
-        unsigned long long groups = rep_words;
+        const long long wX = move ? static_cast<long long>(wstep(C)) : 0;
+        if (COUPLED && D != 0) release_y();
+        uint32_t groups = rep_words;
         while (groups) {
-            const int g = __ffsll(static_cast<long long>(groups)) - 1;
+            const int g = __ffs(groups) - 1;
             groups &= groups - 1;
             const uint32_t q0 = static_cast<uint32_t>(g) << gshift;
             const uint32_t q1 = min(W, q0 + (1u << gshift));
@@ -303,11 +333,11 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
                             moved |= bit;
                         }
                     }
-                    if (xw & bit) bump_counts(j, 0xFFu, false);
+                    if (xw & bit) bump_counts(j, 0xFFu, cbase);
                 }
                 if (tw) trep[q] = 0u;
                 if (xw) st[q * 32] = 0u;
-                if (moved) { atomicOr(&tslot[q], moved); slot_words |= 1ull << g; }
+                if (moved) { atomicOr(&tslot[q], moved); slot_words |= 1u << g; }
             }
         }
         rep_words = 0;
@@ -320,9 +350,9 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             if (valid && p.trace_stride > 0 && (slot_local % p.trace_stride) == 0)
                 tr = p.trace_G + (static_cast<long long>(slot_local) / p.trace_stride) * na;
         }
-        unsigned long long groups = slot_words;
+        uint32_t groups = slot_words;
         while (groups) {
-            const int g = __ffsll(static_cast<long long>(groups)) - 1;
+            const int g = __ffs(groups) - 1;
             groups &= groups - 1;
             const uint32_t q0 = static_cast<uint32_t>(g) << gshift;
             const uint32_t q1 = min(W, q0 + (1u << gshift));
@@ -385,121 +415,127 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         end_slot(false);
     };
 
-    // Advance the clock after a step; 0 = continue, 1 = completed, 2 = doomed, 3 = step limit.
-    auto after_step = [&]() -> int {
-        ++t;
-        if (SYSTEMATIC) { ++sysI; if (sysI == static_cast<uint32_t>(na)) sysI = 0; }
+    // The clock reached t_end: 1 = completed, 2 = doomed, 3 = step limit.
+    auto classify = [&]() -> int {
         if (COUPLED) {
-            if (D == 0) {
-                if (tau == 0) tau = t;               // tau_1 = first t >= 1 with X_t = Y_{t-1}
-                if (t >= ell) return 1;
-            }
-            if (t >= abort_t) return 2;
-        } else if (t >= unit) {
-            return 1;
+            if (D == 0 && t >= ell) return 1;
+            return t >= abort_t ? 2 : 3;
         }
-        return t >= step_limit ? 3 : 0;
+        return t >= unit ? 1 : 3;
     };
 
-    auto draw_site = [&](uint32_t ws) -> uint32_t {
-        if (SYSTEMATIC) return sysI;
-        const unsigned long long prod = static_cast<unsigned long long>(ws) * static_cast<uint32_t>(na);
-        const uint32_t col = static_cast<uint32_t>(prod >> 32), coin = static_cast<uint32_t>(prod);
-        const unsigned long long e = aliasAt(col);
-        return coin < static_cast<uint32_t>(e) ? col : static_cast<uint32_t>(e >> 32);
-    };
-
-    // X's update; on a flip, its counts, the accumulator event of the pair and D.  `met` means the
-    // pair has met (t >= 1, X_t = Y_{t-1}): Y_t = X_{t+1} flips with it and the two events add to
-    // W(t) - W(t-1); at t = 0 (pre-lag) X alone moves.
-    auto apply_x_flip = [&](uint32_t I, uint32_t q, uint32_t bit, uint32_t xw, uint32_t nX,
-                            const uint32_t *ent, bool met) {
+    // X moved at site I on a step where Y_t = X_{t+1} (met, or the pre-lag update t = 0, where
+    // Y stays at Y_0): the counts of I's pools (from the values loaded this step), the event
+    // -+w(t) and, at t = 0, the start of an unmet stretch.
+    auto met_flip = [&](uint32_t I, uint32_t q, uint32_t bit, uint32_t xw, uint32_t nX,
+                        const uint32_t *ent, const uint32_t *cx) {
         st[q * 32] = xw ^ bit;
         const uint32_t delta = nX ? 1u : 0xFFu;
 #pragma unroll
-        for (int l = 0; l < kRow; ++l) {
-            if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
-            uint8_t *cnt = cbase + (ent[l] & 0x7FFFu);
-            *cnt = static_cast<uint8_t>(*cnt + delta);
-        }
-        long long w;
-        if (COUPLED) {
-            if (met) {
-                const long long a = static_cast<long long>(t) - kk + 1;
-                w = a < 0 ? 0 : (a > LL ? LL : a);
-            } else {
-                w = wpre(0);                                     // X_1 only
-                D = 1;
-                acquire_y();
-                if (Tnu) copy_y0(q, bit);
-            }
-        } else {
-            w = wpre(t);
-        }
-        if (w != 0) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]), static_cast<unsigned long long>(nX ? -w : w));
+        for (int l = 0; l < kRow; ++l)
+            if (real(l, ent)) cbase[ent[l] & 0x7FFFu] = static_cast<unsigned char>(cx[l] + delta);
+        const uint32_t w = wstep(t);
+        if (w) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]),
+                      static_cast<unsigned long long>(nX ? -static_cast<long long>(w) : static_cast<long long>(w)));
             atomicOr(&trep[q], bit);
+        }
+        rep_words |= 1u << (q >> gshift);
+        if (COUPLED && t == 0) {            // X_1 differs from Y_0 in bit I
+            D = 1; tau = 0; t_end = stop_unmet;
+            acquire_y();
+            if (Tnu) copy_y0(q, bit);
         }
     };
 
-    // One step for a pair whose Y chain equals its X chain where it matters: the pre-lag update
-    // (t = 0, X only) or a pair that has met.  Uncoupled chains always take this path.
-    auto step_fast = [&](uint32_t ws, uint32_t wu) -> int {
-        const uint32_t I = draw_site(ws);
+    // A pair that has not met: X and Y move separately (events -+W(t) and +-W(t-1)); D follows
+    // the Hamming distance, and at D = 0 the pair has met at tau = t + 1.
+    auto unmet_flip = [&](uint32_t I, uint32_t q, uint32_t bit, uint32_t xw, uint32_t yw,
+                          uint32_t xI, uint32_t yI, uint32_t nX, uint32_t nY, const uint32_t *ent,
+                          const uint32_t *cx, const uint32_t *cy) {
+        long long ev = 0;
+        if (nX != xI) {
+            st[q * 32] = xw ^ bit;
+            const uint32_t delta = nX ? 1u : 0xFFu;
+#pragma unroll
+            for (int l = 0; l < kRow; ++l)
+                if (real(l, ent)) cbase[ent[l] & 0x7FFFu] = static_cast<unsigned char>(cx[l] + delta);
+            const long long w = wpre(t);
+            ev += nX ? -w : w;
+        }
+        if (nY != yI) {
+            ycol[q * 32] = yw ^ bit;
+            unsigned char *yb = reinterpret_cast<unsigned char *>(ycol);
+            const uint32_t delta = nY ? 1u : 0xFFu;
+#pragma unroll
+            for (int l = 0; l < kRow; ++l)
+                if (real(l, ent)) yb[ent[l] & 0x7FFFu] = static_cast<unsigned char>(cy[l] + delta);
+            const long long w = wpre(static_cast<long long>(t) - 1);
+            ev += nY ? w : -w;
+        }
+        if (ev != 0) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]), static_cast<unsigned long long>(ev));
+            atomicOr(&trep[q], bit);
+        }
+        rep_words |= 1u << (q >> gshift);
+        D = D + (nX ^ nY) - (xI ^ yI);
+        if (D == 0) {
+            release_y();
+            tau = t + 1;
+            t_end = min(max(ell, tau), stop_unmet);
+        }
+    };
+
+    // One step of the pair.  X's full conditional from its counts; when some lane of the warp
+    // has not met, Y's from its own column (a met lane reads its X column there, so Y = X).
+    // The uniform U = wu 2^32 + lo needs lo only when wu equals a threshold's high word.
+    auto step = [&](uint32_t ws, uint32_t wu) -> int {
+        uint32_t I;
+        if (SYSTEMATIC) {
+            I = sysI;
+        } else {
+            const unsigned long long prod = static_cast<unsigned long long>(ws) * static_cast<uint32_t>(na);
+            const uint32_t col = static_cast<uint32_t>(prod >> 32), coin = static_cast<uint32_t>(prod);
+            const unsigned long long e = aliasAt(col);
+            I = coin < static_cast<uint32_t>(e) ? col : static_cast<uint32_t>(e >> 32);
+        }
         const uint4 row = rowAt(I);
         const uint32_t q = I >> 5, bit = 1u << (I & 31);
         const uint32_t xw = st[q * 32];
         const uint32_t xI = (xw & bit) ? 1u : 0u;
-        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
-                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
+        uint32_t ent[8];
+        entries(row, ent);
+        uint32_t cx[kRow], cy[kRow];
         uint32_t ix = 0;
 #pragma unroll
         for (int l = 0; l < kRow; ++l) {
-            if (l < (DEG > 0 ? DEG : deg)) {
-                const uint32_t e = ent[l];
-                const uint32_t c = cbase[e & 0x7FFFu];             // X count of the pool
-                if (c == xI) ix += (e >> 15) ? 9u : 1u;           // c_j - x_I = 0: pool j decides
+            cx[l] = 0u;
+            cy[l] = 0u;
+            if (l < NE && (DEG > 0 || l < deg)) {
+                cx[l] = cbase[ent[l] & 0x7FFFu];
+                if (cx[l] == xI) ix += (ent[l] >> 15) ? 9u : 1u;   // c_j - x_I = 0: pool j decides
             }
         }
         const unsigned long long TX = tAt(ix);
-        const uint32_t thx = static_cast<uint32_t>(TX >> 32);
-        uint32_t nX = wu < thx ? 1u : 0u;
-        if (wu == thx) {                                        // the low half of U decides
-            const uint32_t lo = philox10(make_uint4(t, r, slot_g, instance | (2u << 24)), k0, k1).x;
-            nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
-        }
-        if (nX != xI) {
-            apply_x_flip(I, q, bit, xw, nX, ent, COUPLED && t > 0);
-            rep_words |= 1ull << (q >> gshift);
-        }
-        return after_step();
-    };
-
-    // One coupled step for a warp holding a pair that has not met: such a pair reads its Y chain
-    // from the global Y state; pairs that have met (or are at t = 0) use X for Y.
-    auto step_full = [&](uint32_t ws, uint32_t wu) -> int {
-        const uint32_t I = draw_site(ws);
-        const uint4 row = rowAt(I);
-        const uint32_t q = I >> 5, bit = 1u << (I & 31);
-        const uint32_t xw = st[q * 32];
-        const bool own_y = t > 0 && D != 0;
-        const uint32_t yw = own_y ? ybase[q] : xw;
-        const uint32_t xI = (xw & bit) ? 1u : 0u, yI = (yw & bit) ? 1u : 0u;
-        const uint32_t ent[8] = {row.x & 0xFFFFu, row.x >> 16, row.y & 0xFFFFu, row.y >> 16,
-                                 row.z & 0xFFFFu, row.z >> 16, row.w & 0xFFFFu, row.w >> 16};
-        uint32_t ix = 0, iy = 0;
+        unsigned long long TY = TX;
+        uint32_t yw = xw, yI = xI;
+        bool own = false;
+        if (COUPLED && __any_sync(__activemask(), D != 0)) {
+            own = D != 0;
+            const uint32_t *yp = own ? ycol : st;
+            const unsigned char *yb = reinterpret_cast<const unsigned char *>(yp);
+            yw = yp[q * 32];
+            yI = (yw & bit) ? 1u : 0u;
+            uint32_t iy = 0;
 #pragma unroll
-        for (int l = 0; l < kRow; ++l) {
-            if (l < (DEG > 0 ? DEG : deg)) {
-                const uint32_t e = ent[l];
-                const uint32_t code = (e >> 15) ? 9u : 1u;
-                const uint32_t cx = cbase[e & 0x7FFFu];
-                const uint32_t cy = own_y ? static_cast<uint32_t>(*ycnt(e)) : cx;
-                if (cx == xI) ix += code;
-                if (cy == yI) iy += code;
+            for (int l = 0; l < kRow; ++l) {
+                if (l < NE && (DEG > 0 || l < deg)) {
+                    cy[l] = yb[ent[l] & 0x7FFFu];
+                    if (cy[l] == yI) iy += (ent[l] >> 15) ? 9u : 1u;
+                }
             }
+            TY = tAt(iy);
         }
-        const unsigned long long TX = tAt(ix), TY = tAt(iy);
         const uint32_t thx = static_cast<uint32_t>(TX >> 32), thy = static_cast<uint32_t>(TY >> 32);
         uint32_t nX = wu < thx ? 1u : 0u, nY = wu < thy ? 1u : 0u;
         if (wu == thx || wu == thy) {
@@ -507,49 +543,14 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             if (wu == thx) nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
             if (wu == thy) nY = lo < static_cast<uint32_t>(TY) ? 1u : 0u;
         }
-        if (!own_y) {                                           // pre-lag, or met: as the fast path
-            if (nX != xI) {
-                apply_x_flip(I, q, bit, xw, nX, ent, t > 0);
-                rep_words |= 1ull << (q >> gshift);
-            }
-            return after_step();
+        if (COUPLED && own) {
+            if ((nX ^ xI) | (nY ^ yI)) unmet_flip(I, q, bit, xw, yw, xI, yI, nX, nY, ent, cx, cy);
+        } else if (nX != xI) {
+            met_flip(I, q, bit, xw, nX, ent, cx);
         }
-        const uint32_t fx = nX ^ xI, fy = nY ^ yI;
-        if (fx | fy) {
-            long long ev = 0;
-            if (fx) {
-                st[q * 32] = xw ^ bit;
-                const uint32_t delta = nX ? 1u : 0xFFu;
-#pragma unroll
-                for (int l = 0; l < kRow; ++l) {
-                    if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
-                    uint8_t *cnt = cbase + (ent[l] & 0x7FFFu);
-                    *cnt = static_cast<uint8_t>(*cnt + delta);
-                }
-                const long long w = wpre(t);                     // X_{t+1}
-                ev += nX ? -w : w;
-            }
-            if (fy) {
-                ybase[q] = yw ^ bit;
-                const uint32_t delta = nY ? 1u : 0xFFu;
-#pragma unroll
-                for (int l = 0; l < kRow; ++l) {
-                    if (l >= (DEG > 0 ? DEG : deg) || (DEG == 0 && ent[l] == dummy_entry)) continue;
-                    uint8_t *cnt = ycnt(ent[l]);
-                    *cnt = static_cast<uint8_t>(*cnt + delta);
-                }
-                const long long w = wpre(static_cast<long long>(t) - 1);   // Y_t
-                ev += nY ? w : -w;
-            }
-            if (ev != 0) {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]), static_cast<unsigned long long>(ev));
-                atomicOr(&trep[q], bit);
-            }
-            rep_words |= 1ull << (q >> gshift);
-            D = D + (nX ^ nY) - (xI ^ yI);
-            if (D == 0) { clear_y(); release_y(); }             // met: Y is X from now on
-        }
-        return after_step();
+        ++t;
+        if (SYSTEMATIC) { ++sysI; if (sysI == static_cast<uint32_t>(na)) sysI = 0; }
+        return t < t_end ? 0 : classify();
     };
 
     start_slot();
@@ -560,11 +561,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         const uint4 nxt = philox10(make_uint4((t >> 1) + 1, r, slot_g, instance), k0, k1);
         int ended = 0;
 #pragma unroll 1
-        for (int h = 0; h < 2 && !ended; ++h) {
-            const uint32_t ws = h ? blk.z : blk.x, wu = h ? blk.w : blk.y;
-            if (COUPLED && !__all_sync(__activemask(), t == 0 || D == 0)) ended = step_full(ws, wu);
-            else ended = step_fast(ws, wu);
-        }
+        for (int h = 0; h < 2 && !ended; ++h) ended = step(h ? blk.z : blk.x, h ? blk.w : blk.y);
         if (ended) {
             if (ended == 1) complete();
             else if (ended == 2) abort_rep();
@@ -673,13 +670,6 @@ int set_smem(size_t bytes, bool batch) {
 
 }  // namespace
 
-int set_pairs_smem(size_t bytes, int coupled) {
-    (void)coupled;
-    return set_smem(bytes, false);
-}
-
-int set_batch_smem(size_t bytes) { return set_smem(bytes, true); }
-
 int pairs_max_smem(int device, size_t *bytes) {
     int v = 0;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess)
@@ -723,9 +713,62 @@ int launch_philox(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, 
     return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
 }
 
-int pairs_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(coupled, scan, false, 0), block, smem) == cudaSuccess
-               ? MCPD_OK : MCPD_ECUDA;
+int pairs_y_regions(int coupled, int warps) {
+    return coupled ? (warps + kWarpsPerYRegion - 1) / kWarpsPerYRegion : 0;
+}
+
+size_t pairs_smem_bytes(size_t tables, int wpp, int warps, int y_regions) {
+    const size_t b = tables + static_cast<size_t>(warps + y_regions) * static_cast<size_t>(wpp) * 128 +
+                     static_cast<size_t>(y_regions) * 4;
+    return (b + 15) / 16 * 16;
+}
+
+int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int wpp, size_t smem_optin,
+                long long P, int sm_count, int warps, PairsShape *out) {
+    const int cap = pairs_max_threads(coupled, scan, udeg, batch) / 32;
+    auto bytes = [&](int w) { return pairs_smem_bytes(tables, wpp, w, pairs_y_regions(coupled, w)); };
+    auto most = [&](size_t budget) {
+        int best = 0;
+        for (int w = 1; w <= cap && bytes(w) <= budget; ++w) best = w;
+        return best;
+    };
+    auto resident = [&](int w, int *per_sm) {
+        *per_sm = 1;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pick(coupled, scan, batch, batch ? 0 : udeg),
+                                                             w * 32, bytes(w)) == cudaSuccess;
+    };
+    const int w1 = most(smem_optin);
+    if (w1 < 1) return MCPD_ETOO_LARGE;
+    if (set_smem(bytes(w1), batch) != MCPD_OK) return MCPD_ECUDA;
+    PairsShape s;
+    if (warps > 0) {
+        if (warps > w1) return MCPD_EINVAL;
+        s.warps = warps;
+        if (!resident(warps, &s.per_sm)) return MCPD_ECUDA;
+    } else {
+        s.warps = w1;
+        if (!resident(w1, &s.per_sm)) return MCPD_ECUDA;
+        if (!batch) {
+            // Two blocks per SM (each with its own copy of the tables) when that holds more warps.
+            const int w2 = most(smem_optin / 2);
+            int per2 = 1;
+            if (w2 >= 1 && resident(w2, &per2) && per2 * w2 > s.per_sm * s.warps) { s.warps = w2; s.per_sm = per2; }
+            // Whole rounds of slots: slots run for about the same time, so the fewest warps that
+            // need no more rounds per thread than the widest shape finish at the same time with
+            // no partly filled last round.
+            if (P > 0) {
+                const long long blocks = static_cast<long long>(sm_count) * s.per_sm;
+                const long long rounds = (P + blocks * s.warps * 32 - 1) / (blocks * s.warps * 32);
+                const long long w = (P + rounds * blocks * 32 - 1) / (rounds * blocks * 32);
+                if (w >= 1 && w < s.warps) s.warps = static_cast<int>(w);
+            }
+        }
+    }
+    s.y_regions = pairs_y_regions(coupled, s.warps);
+    s.smem = bytes(s.warps);
+    if (s.per_sm < 1) s.per_sm = 1;
+    *out = s;
+    return MCPD_OK;
 }
 
 int pairs_max_threads(int coupled, int scan, int udeg, bool batch) {
@@ -734,9 +777,5 @@ int pairs_max_threads(int coupled, int scan, int udeg, bool batch) {
     return a.maxThreadsPerBlock;
 }
 
-int batch_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, pick(coupled, scan, true), block, smem) == cudaSuccess
-               ? MCPD_OK : MCPD_ECUDA;
-}
 
 }  // namespace mcpd

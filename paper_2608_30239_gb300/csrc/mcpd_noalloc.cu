@@ -29,7 +29,6 @@
 #include "mcpd_internal.h"
 
 namespace mcpd {
-int pairs_occupancy(int coupled, int scan, int block, size_t smem, int *blocks_per_sm);
 
 namespace {
 
@@ -104,29 +103,21 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
 
     // Launch shape as the allocating path would choose it, then as many whole warps as fit.
     const size_t tables = ((na * 24 + kTSide * kTSide * 8) + 15) / 16 * 16;
-    const size_t per_warp_smem = static_cast<size_t>(t.wpp) * (128 + 4 * kYSlots) + 4;
-    if (tables + per_warp_smem > ctx->smem_optin)
-        return fail(ctx, MCPD_ETOO_LARGE, "instance too large for the one-thread-per-pair layout");
-    const int max_warps = pairs_max_threads(t.coupled, t.scan, t.udeg, false) / 32;
-    int warps = static_cast<int>(std::min<size_t>(max_warps, (ctx->smem_optin - tables) / per_warp_smem));
-    const size_t half = ctx->smem_optin / 2;
-    if (half > tables) {
-        const int w2 = static_cast<int>(std::min<size_t>(max_warps, (half - tables) / per_warp_smem));
-        if (2 * w2 > warps) warps = w2;
-    }
+    PairsShape shape;
+    const int src = pairs_shape(t.coupled, t.scan, t.udeg, false, tables, t.wpp, ctx->smem_optin, t.P,
+                                ctx->sm_count, 0, &shape);
+    if (src == MCPD_ETOO_LARGE) return fail(ctx, src, "instance too large for the one-thread-per-pair layout");
+    if (src != MCPD_OK) return fail(ctx, MCPD_ECUDA, "launch shape (cudaFuncSetAttribute / occupancy)");
     const size_t per_pair = na * 16 + static_cast<size_t>(t.W) * 8 + static_cast<size_t>(t.wpp) * 4;   // sums, touched sets, Y state
     if (fixed >= kNoAllocScratchBytes)
         return fail(ctx, MCPD_ETOO_LARGE, "tables and N*_p buckets exceed the 64 MiB no-alloc scratch");
     const size_t fit_warps = (kNoAllocScratchBytes - fixed - 5 * 256) / (32 * per_pair);
     if (fit_warps < 1)
         return fail(ctx, MCPD_ETOO_LARGE, "not even one warp of pair accumulators fits the 64 MiB no-alloc scratch");
-    int per_sm = 1;
-    size_t smem = tables + per_warp_smem * warps;
-    if (set_pairs_smem(smem, t.coupled) != MCPD_OK) return fail(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
-    if (pairs_occupancy(t.coupled, t.scan, warps * 32, smem, &per_sm) != MCPD_OK || per_sm < 1) per_sm = 1;
-    warps = static_cast<int>(std::min<size_t>(warps, fit_warps));
-    smem = tables + per_warp_smem * warps;
-    const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(ctx->sm_count) * per_sm, fit_warps / warps));
+    const int warps = static_cast<int>(std::min<size_t>(shape.warps, fit_warps));
+    const int y_regions = pairs_y_regions(t.coupled, warps);
+    const size_t smem = pairs_smem_bytes(tables, t.wpp, warps, y_regions);
+    const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(ctx->sm_count) * shape.per_sm, fit_warps / warps));
     const size_t pairs = static_cast<size_t>(grid) * warps * 32;
     const size_t o_racc = take(pairs * na * 8), o_sacc = take(pairs * na * 8);
     const size_t o_trep = take(pairs * t.W * 4), o_tslot = take(pairs * t.W * 4);
@@ -170,6 +161,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     kp.slot_offset = t.slot_offset; kp.trace_stride = 0;
     kp.seed = t.seed; kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
+    kp.y_regions = y_regions;
     if (launch_pairs(kp, grid, warps * 32, smem, s) != MCPD_OK)
         return fail(ctx, MCPD_ECUDA, std::string("pairs kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
     if (launch_finalize(kp.S1, kp.S2lo, kp.S2hi, t.na, static_cast<int>(t.nb), t.P, t.L, est_dev, se_dev, s) != MCPD_OK)

@@ -132,6 +132,20 @@ def tapestry_like_design(n: int, m: int, deg: int, seed: int):
     return clone_ptr, np.asarray(rows, dtype=np.int32).reshape(-1)
 
 
+def mixed_degree_design(n: int, m: int, deg_lo: int, deg_hi: int, seed: int):
+    """Each clone draws its own number of pools uniformly from [deg_lo, deg_hi], then that many
+    distinct pools uniformly (rows of different lengths)."""
+    if deg_hi > m or deg_lo < 1 or deg_lo > deg_hi:
+        raise ValueError("need 1 <= deg_lo <= deg_hi <= m")
+    rng = SplitMix64(seed)
+    degs = deg_lo + rng.below(n, deg_hi - deg_lo + 1).astype(np.int64)
+    picks = _partial_shuffle(rng, n, m, deg_hi)
+    rows = [np.sort(picks[i, :degs[i]]) for i in range(n)]
+    clone_ptr = np.zeros(n + 1, dtype=np.int32)
+    clone_ptr[1:] = np.cumsum(degs)
+    return clone_ptr, np.concatenate(rows).astype(np.int32)
+
+
 def draw_outcomes(n: int, m: int, clone_ptr, clone_pools, n_pos: int, fp: float, fn: float,
                   seed: int):
     """Pick `n_pos` true positives uniformly, then y_j ~ Bern(1-fn) if pool j holds one, else
@@ -148,6 +162,14 @@ def draw_outcomes(n: int, m: int, clone_ptr, clone_pools, n_pos: int, fp: float,
 
 def make_instance(n, m, deg, n_pos, fp, fn, q, design_seed, outcome_seed, label=""):
     clone_ptr, clone_pools = kset_design(n, m, deg, design_seed)
+    positives, y = draw_outcomes(n, m, clone_ptr, clone_pools, n_pos, fp, fn, outcome_seed)
+    return Instance(n=n, m=m, clone_ptr=clone_ptr, clone_pools=clone_pools, y=y,
+                    positives=positives, fp=fp, fn=fn, q=q, seed=design_seed, label=label)
+
+
+def make_mixed_instance(n, m, deg_lo, deg_hi, n_pos, fp, fn, q, design_seed, outcome_seed, label=""):
+    """As `make_instance`, on a `mixed_degree_design`."""
+    clone_ptr, clone_pools = mixed_degree_design(n, m, deg_lo, deg_hi, design_seed)
     positives, y = draw_outcomes(n, m, clone_ptr, clone_pools, n_pos, fp, fn, outcome_seed)
     return Instance(n=n, m=m, clone_ptr=clone_ptr, clone_pools=clone_pools, y=y,
                     positives=positives, fp=fp, fn=fn, q=q, seed=design_seed, label=label)

@@ -188,3 +188,29 @@ def test_paper_sized_batch_runs(ctx):
         got = batch.buckets(i)
         assert np.array_equal(got["S1"], ref["S1"]) and np.array_equal(got["count"], ref["count"])
     batch.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 8, 32])
+def test_batch_mixed_degree_instances(ctx, lanes):
+    """Instances whose clones sit in different numbers of pools (padded rows), next to uniform
+    ones, with a random start on one: every launch shape equals the oracle per instance."""
+    from paper_2608_30239_gb300 import mcpd
+    insts = [synth.make_mixed_instance(180 + 40 * i, 17 + 2 * i, 2, 7, 4, 0.08, 0.18, 4 / (180 + 40 * i),
+                                       600 + i, 700 + i) for i in range(3)] + _uneven(2, seed=21)
+    ps = _params(insts)
+    ps[0] = dict(ps[0], init_marginals=np.random.default_rng(9).random(insts[0].n) * 0.25)
+    batch = mcpd.Batch(ctx, insts, ps)
+    if lanes != 1:
+        batch.set_shape(0, lanes)
+    est, se, st = _run(ctx, batch)
+    for i, (inst, kw) in enumerate(zip(insts, ps)):
+        M = oracle.Model(inst, init_marginals=kw.get("init_marginals"))
+        run = oracle.coupled_run(kw["k"], kw["ell"], kw["horizon"], kw["seed"], instance=kw["instance_id"])
+        ref = M.run_slots(run, 0, kw["slots"], THREADS)
+        ref["est"], ref["se"] = M.finalize(ref, kw["slots"], kw["ell"] - kw["k"] + 1)
+        got = batch.buckets(i)
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (lanes, i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"])
+    batch.close()

@@ -179,6 +179,60 @@ def test_step_limit_reports_error_and_context_survives(ctx):
     assert again["stats"]["status"] == mcpd.MCPD_OK
 
 
+def _mixed():
+    """260 clones x 23 pools, each clone in 2 to 8 pools: rows padded to the longest."""
+    return synth.make_mixed_instance(260, 23, 2, 8, 6, 0.1, 0.2, 6 / 260, 31, 32)
+
+
+@pytest.mark.parametrize("start", ["all_negative", "bernoulli"])
+def test_mixed_degree_design(ctx, start):
+    """Clones in different numbers of pools (the padding entries must never count as deciding
+    pools, in either chain), coupled with refill; the random start copies Y_0 after a pre-lag
+    flip."""
+    inst = _mixed()
+    nu = None
+    if start == "bernoulli":
+        nu = np.random.default_rng(5).random(inst.n) * 0.2
+    k, ell = oracle.window_defaults(inst.n, 1)
+    P, B = 3000, 3 * ell + 5
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=808, init_marginals=nu,
+                 record_slots=True, trace_stride=11)
+    o = _oracle_run(inst, P, k, ell, B, 808, init=nu, slot_G=True)
+    _assert_same(g, o)
+    assert np.array_equal(g["trace_G"], o["slot_G"][::11])
+    assert g["stats"]["sum_tau"] > g["stats"]["reps_retained"]     # unmet stretches did occur
+
+
+def test_mixed_degree_uncoupled(ctx):
+    inst = _mixed()
+    P = 1200
+    g = _gpu_run(ctx, inst, slots=P, coupled=False, burn=20, length=240, horizon=900, seed=6,
+                 record_slots=True)
+    o = _oracle_run(inst, P, 0, 0, 900, 6, coupled=False, burn=20, length=240)
+    _assert_same(g, o)
+
+
+def test_unmet_pairs_overflow_shared_y(ctx):
+    """An instance whose pairs stay unmet about half of the time (200 x 20, k = 3, 8 positives,
+    fp .2, fn .3): far more pairs are unmet at once than the shared Y regions hold, so many use
+    their global Y column.  Sampled slots equal the oracle's, and every slot is accounted for."""
+    inst = synth.make_instance(200, 20, 3, 8, 0.2, 0.3, 8 / 200, 11, 12)
+    k, ell = oracle.window_defaults(inst.n, 1)
+    P, B, stride = 120_000, 2 * ell, 1499
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=99, record_slots=True,
+                 trace_stride=stride)
+    st = g["stats"]
+    assert st["status"] == 0 and int(g["count"].sum()) == P
+    assert st["sum_tau"] > 0.3 * st["progress_units"]
+    M = oracle.Model(inst)
+    for idx, p in enumerate(range(0, P, stride)):
+        run = oracle.coupled_run(k, ell, B, 99, slot_offset=p)
+        r = M.run_slots(run, 0, 1, 1, per_slot=True, slot_G=True)
+        assert g["slot_nstar"][p] == r["slot_nstar"][0]
+        assert g["slot_S"][p] == r["slot_S"][0]
+        assert np.array_equal(g["trace_G"][idx], r["slot_G"][0]), p
+
+
 # -------------------------------------------------------------------------------------------
 # Full size: the 1298 x 97 high-noise configuration with 524288 slots and a 4e10 site-update
 # budget, in the launch configuration the bench times.  Sampled slots are recomputed one by one.
