@@ -134,6 +134,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     ALLOC(kp.touched_rep, static_cast<size_t>(pl->pairs) * t.W);
     ALLOC(kp.touched_slot, static_cast<size_t>(pl->pairs) * t.W);
     ALLOC(kp.y_state, static_cast<size_t>(pl->pairs) * t.wpp);
+    ALLOC(kp.pair_stats, static_cast<size_t>(pl->pairs) * mcpd::kPairStats);
     ALLOC(kp.S1, static_cast<size_t>(t.nb) * t.na);
     ALLOC(kp.S2lo, static_cast<size_t>(t.nb) * t.na);
     ALLOC(kp.S2hi, static_cast<size_t>(t.nb) * t.na);
@@ -168,7 +169,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     kp.P = t.P; kp.B = t.B; kp.k = t.k; kp.ell = t.ell; kp.L = t.L; kp.burn = t.burn;
     kp.length = t.length; kp.unit = t.unit; kp.step_limit = t.step_limit;
     kp.slot_offset = t.slot_offset; kp.trace_stride = t.trace_stride;
-    kp.seed = t.seed; kp.instance = t.instance; kp.warps = warps;
+    kp.seed = t.seed; mcpd::philox_round_keys(t.seed, kp.rk); kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
     kp.y_regions = shape.y_regions;
     CU(cudaEventCreate(&pl->ev0));
@@ -450,6 +451,7 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
         if ((rc = balloc(ctx, b->scratch, &b->bp.touched_rep, pw)) != MCPD_OK) return rc;
         if ((rc = balloc(ctx, b->scratch, &b->bp.touched_slot, pw)) != MCPD_OK) return rc;
         if ((rc = balloc(ctx, b->scratch, &b->bp.y_state, static_cast<size_t>(b->pairs) * b->bp.max_wpp)) != MCPD_OK) return rc;
+        if ((rc = balloc(ctx, b->scratch, &b->bp.pair_stats, static_cast<size_t>(b->pairs) * mcpd::kPairStats)) != MCPD_OK) return rc;
         b->scratch_pairs = b->pairs;
         b->dirty = true;
     }

@@ -18,6 +18,30 @@ static __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t 
     return c;
 }
 
+// The same with the round keys (k0 + i W0, k1 + i W1), i = 0..9, given as rk[2 i], rk[2 i + 1].
+static __device__ __forceinline__ uint4 philox10_rk(uint4 c, const uint32_t (&rk)[20]) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk[2 * round], lo1, hi0 ^ c.w ^ rk[2 * round + 1], lo0);
+    }
+    return c;
+}
+
+// Word 0 of a block, out of line (the rare draw of a uniform's low half).
+static __device__ __noinline__ uint32_t philox_low_word(uint4 c, uint32_t k0, uint32_t k1) {
+    return philox10(c, k0, k1).x;
+}
+
+// Fire-and-forget global reductions (no value returned, no wait).
+static __device__ __forceinline__ void red_add(long long *a, long long v) {
+    asm volatile("red.global.add.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
+static __device__ __forceinline__ void red_or(uint32_t *a, uint32_t v) {
+    asm volatile("red.global.or.b32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
 // Add G and G^2 (128-bit, carried into the high word) of one slot to bucket N*_p - 1.
 static __device__ __forceinline__ void bucket_add(unsigned long long *S1, unsigned long long *S2lo,
                                            unsigned long long *S2hi, int na, int bkt, int j, long long g) {

@@ -35,6 +35,12 @@ enum Counter {
     kZeroCompletion, kStepLimitHits, kMaxTau, kSumTau, kNumCounters = 16
 };
 
+// Per-pair statistics record of the one-thread-per-pair kernel, summed into the counters at exit.
+enum PairStat {
+    kPsProgress = 0, kPsStarted, kPsRetained, kPsAborted, kPsZero, kPsLimit, kPsSumTau, kPsMaxTau,
+    kPairStats = 8
+};
+
 // Everything the sampler needs, built on the host from (design, y, params).
 struct Tables {
     int32_t n = 0, m = 0, na = 0, deg_max = 0;
@@ -80,6 +86,7 @@ struct KParams {
     uint32_t *touched_rep;            // [pairs][W]
     uint32_t *touched_slot;           // [pairs][W]
     uint32_t *y_state;                // [pairs / 32][wpp][32] fallback Y columns (pairs not yet met)
+    unsigned long long *pair_stats;   // [pairs][kPairStats]
     unsigned long long *S1;           // [nb][na]
     unsigned long long *S2lo;         // [nb][na]
     unsigned long long *S2hi;         // [nb][na]
@@ -100,7 +107,19 @@ struct KParams {
     int32_t warps;
     uint32_t smem_tables;             // bytes of staged tables at the start of shared memory
     int32_t y_regions;                // 32-column Y regions in shared memory
+    uint32_t rk[20];                  // Philox round keys of the seed
 };
+
+// Philox4x32-10 round keys of a 64-bit seed: (lo + i 0x9E3779B9, hi + i 0xBB67AE85), i = 0..9.
+inline void philox_round_keys(uint64_t seed, uint32_t rk[20]) {
+    uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        rk[2 * i] = k0;
+        rk[2 * i + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
 
 // One instance of a batched launch (plain types; read by the kernels from global memory).
 struct InstDesc {
@@ -132,6 +151,7 @@ struct BParams {
     uint32_t *touched_rep;            // [pairs][max_W]
     uint32_t *touched_slot;           // [pairs][max_W]
     uint32_t *y_state;                // [pairs / 32][max_wpp][32] fallback Y columns
+    unsigned long long *pair_stats;   // [pairs][kPairStats]
     unsigned long long *counters;
     int *error;
     int32_t max_na, max_W;

@@ -92,6 +92,10 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     uint32_t *const yglob = (BATCH ? bp.y_state : p.y_state) + static_cast<size_t>(gpair >> 5) * region_words + lane;
     uint32_t *ycol = yglob;           // the Y column in use (shared or global), while D != 0
     int yslot = -1;                   // its index in the Y regions, -1 for the global column
+    // This pair's statistics (rare updates, plain global read-modify-write), summed at the end.
+    unsigned long long *const pst = (BATCH ? bp.pair_stats : p.pair_stats) + gpair * kPairStats;
+#pragma unroll
+    for (int i = 0; i < kPairStats; ++i) pst[i] = 0ull;
 
     // Per-instance values (fixed for a single instance, reloaded when a batched slot changes
     // instance).
@@ -173,9 +177,6 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     uint32_t slot_local = 0, slot_g = 0, r = 0, t = 0, S = 0, N = 0, tau = 0, D = 0;
     uint32_t abort_t = 0xFFFFFFFFu, t_end = 0, stop_unmet = 0, sysI = 0, reps_in_slot = 0;
     uint32_t rep_words = 0, slot_words = 0;   // groups of 2^gshift bit words touched
-    unsigned long long c_prog = 0, c_started = 0, c_retained = 0, c_aborted = 0, c_zero = 0,
-                       c_limit = 0, c_sumtau = 0;
-    uint32_t c_maxtau = 0;
 
     // Add delta (mod 256) to the counts of every pool of clone c in the column at `base`.
     auto bump_counts = [&](uint32_t c, uint32_t delta, unsigned char *base) {
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
         stop_unmet = min(abort_t, step_limit);
         t_end = COUPLED ? min(max(ell, 1u), stop_unmet) : min(unit, step_limit);
-        ++c_started;
+        ++pst[kPsStarted];
         ++reps_in_slot;
         if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0 (clones with nu_i = 0 stay 0)
             for (int e = 0; e < n_init_pairs; ++e) {
@@ -389,27 +390,30 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     // finish within B is aborted before it completes); then refill or end the slot.
     auto complete = [&]() {
         const uint32_t C = t;
-        c_prog += C;
-        if (COUPLED) { c_sumtau += tau; c_maxtau = max(c_maxtau, tau); }
+        pst[kPsProgress] += C;
+        if (COUPLED) {
+            pst[kPsSumTau] += tau;
+            if (tau > pst[kPsMaxTau]) pst[kPsMaxTau] = tau;
+        }
         finish_rep(true, C);
         S += C;
         N += 1;
-        ++c_retained;
-        if (S > B) ++c_zero;                 // only a slot's first replication can end beyond B
+        ++pst[kPsRetained];
+        if (S > B) ++pst[kPsZero];           // only a slot's first replication can end beyond B
         if (S < B && B - S >= unit) { ++r; start_rep(); }
         else end_slot(true);
     };
 
     auto abort_rep = [&]() {                  // doomed: S_p(r) would exceed B; discard it
-        c_prog += t;
-        ++c_aborted;
+        pst[kPsProgress] += t;
+        ++pst[kPsAborted];
         finish_rep(false, 0);
         end_slot(true);
     };
 
     auto limit_hit = [&]() {
-        c_prog += t;
-        ++c_limit;
+        pst[kPsProgress] += t;
+        ++pst[kPsLimit];
         atomicExch(BATCH ? bp.error : p.error, 1);
         finish_rep(false, 0);
         end_slot(false);
@@ -436,9 +440,8 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             if (real(l, ent)) cbase[ent[l] & 0x7FFFu] = static_cast<unsigned char>(cx[l] + delta);
         const uint32_t w = wstep(t);
         if (w) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]),
-                      static_cast<unsigned long long>(nX ? -static_cast<long long>(w) : static_cast<long long>(w)));
-            atomicOr(&trep[q], bit);
+            red_add(&racc[I], nX ? -static_cast<long long>(w) : static_cast<long long>(w));
+            red_or(&trep[q], bit);
         }
         rep_words |= 1u << (q >> gshift);
         if (COUPLED && t == 0) {            // X_1 differs from Y_0 in bit I
@@ -474,8 +477,8 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             ev += nY ? w : -w;
         }
         if (ev != 0) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]), static_cast<unsigned long long>(ev));
-            atomicOr(&trep[q], bit);
+            red_add(&racc[I], ev);
+            red_or(&trep[q], bit);
         }
         rep_words |= 1u << (q >> gshift);
         D = D + (nX ^ nY) - (xI ^ yI);
@@ -520,26 +523,32 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         unsigned long long TY = TX;
         uint32_t yw = xw, yI = xI;
         bool own = false;
-        if (COUPLED && __any_sync(__activemask(), D != 0)) {
-            own = D != 0;
-            const uint32_t *yp = own ? ycol : st;
+        // Y's side, for the lanes that have not met (a met lane keeps Y = X).
+        auto ypart = [&](const uint32_t *yp) {
             const unsigned char *yb = reinterpret_cast<const unsigned char *>(yp);
-            yw = yp[q * 32];
+            yw = own ? yp[q * 32] : xw;
             yI = (yw & bit) ? 1u : 0u;
             uint32_t iy = 0;
 #pragma unroll
             for (int l = 0; l < kRow; ++l) {
                 if (l < NE && (DEG > 0 || l < deg)) {
-                    cy[l] = yb[ent[l] & 0x7FFFu];
+                    cy[l] = own ? static_cast<uint32_t>(yb[ent[l] & 0x7FFFu]) : cx[l];
                     if (cy[l] == yI) iy += (ent[l] >> 15) ? 9u : 1u;
                 }
             }
             TY = tAt(iy);
+        };
+        if (COUPLED) {
+            const bool ymode = __any_sync(__activemask(), D != 0);
+            if (ymode) {
+                own = D != 0;
+                ypart(ycol);
+            }
         }
         const uint32_t thx = static_cast<uint32_t>(TX >> 32), thy = static_cast<uint32_t>(TY >> 32);
         uint32_t nX = wu < thx ? 1u : 0u, nY = wu < thy ? 1u : 0u;
         if (wu == thx || wu == thy) {
-            const uint32_t lo = philox10(make_uint4(t, r, slot_g, instance | (2u << 24)), k0, k1).x;
+            const uint32_t lo = philox_low_word(make_uint4(t, r, slot_g, instance | (2u << 24)), k0, k1);
             if (wu == thx) nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
             if (wu == thy) nY = lo < static_cast<uint32_t>(TY) ? 1u : 0u;
         }
@@ -553,12 +562,18 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         return t < t_end ? 0 : classify();
     };
 
+    // Step draws: one Philox block per pair of steps (for a single instance with the round keys
+    // precomputed in the kernel parameters).
+    auto draw = [&](uint32_t c0) -> uint4 {
+        if constexpr (BATCH) return philox10(make_uint4(c0, r, slot_g, instance), k0, k1);
+        else return philox10_rk(make_uint4(c0, r, slot_g, instance), p.rk);
+    };
     start_slot();
-    uint4 blk = philox10(make_uint4(t >> 1, r, slot_g, instance), k0, k1);
+    uint4 blk = draw(t >> 1);
     while (alive) {
-        // one Philox block per pair of steps, words (0,1) at even t and (2,3) at odd t; the next
-        // block is computed ahead and discarded if the replication ends
-        const uint4 nxt = philox10(make_uint4((t >> 1) + 1, r, slot_g, instance), k0, k1);
+        // words (0,1) at even t and (2,3) at odd t; the next block is computed ahead and
+        // discarded if the replication ends
+        const uint4 nxt = draw((t >> 1) + 1);
         int ended = 0;
 #pragma unroll 1
         for (int h = 0; h < 2 && !ended; ++h) ended = step(h ? blk.z : blk.x, h ? blk.w : blk.y);
@@ -566,20 +581,27 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             if (ended == 1) complete();
             else if (ended == 2) abort_rep();
             else limit_hit();
-            blk = philox10(make_uint4(t >> 1, r, slot_g, instance), k0, k1);
+            blk = draw(t >> 1);
         } else {
             blk = nxt;
         }
     }
 
-    if (c_prog) atomicAdd(&counters[kProgress], c_prog);
-    if (c_started) atomicAdd(&counters[kRepsStarted], c_started);
-    if (c_retained) atomicAdd(&counters[kRepsRetained], c_retained);
-    if (c_aborted) atomicAdd(&counters[kRepsAborted], c_aborted);
-    if (c_zero) atomicAdd(&counters[kZeroCompletion], c_zero);
-    if (c_limit) atomicAdd(&counters[kStepLimitHits], c_limit);
-    if (c_sumtau) atomicAdd(&counters[kSumTau], c_sumtau);
-    if (c_maxtau) atomicMax(&counters[kMaxTau], static_cast<unsigned long long>(c_maxtau));
+    // Every lane of the warp is here: sum (or max) the pairs' statistics over the warp.
+    const int dst[kPairStats] = {kProgress, kRepsStarted, kRepsRetained, kRepsAborted,
+                                 kZeroCompletion, kStepLimitHits, kSumTau, kMaxTau};
+#pragma unroll
+    for (int i = 0; i < kPairStats; ++i) {
+        unsigned long long v = pst[i];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long u = __shfl_down_sync(0xFFFFFFFFu, v, o);
+            v = i == kPsMaxTau ? max(v, u) : v + u;
+        }
+        if (lane == 0 && v) {
+            if (i == kPsMaxTau) atomicMax(&counters[dst[i]], v);
+            else atomicAdd(&counters[dst[i]], v);
+        }
+    }
 }
 
 // theta_j = (sum_{n ascending} S1[n][j] / n) / (P L);  Q_j = (sum_n S2[n][j] / n^2) / L^2;

@@ -108,10 +108,11 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
                                 ctx->sm_count, 0, &shape);
     if (src == MCPD_ETOO_LARGE) return fail(ctx, src, "instance too large for the one-thread-per-pair layout");
     if (src != MCPD_OK) return fail(ctx, MCPD_ECUDA, "launch shape (cudaFuncSetAttribute / occupancy)");
-    const size_t per_pair = na * 16 + static_cast<size_t>(t.W) * 8 + static_cast<size_t>(t.wpp) * 4;   // sums, touched sets, Y state
+    // sums, touched sets, Y column, statistics record
+    const size_t per_pair = na * 16 + static_cast<size_t>(t.W) * 8 + static_cast<size_t>(t.wpp) * 4 + kPairStats * 8;
     if (fixed >= kNoAllocScratchBytes)
         return fail(ctx, MCPD_ETOO_LARGE, "tables and N*_p buckets exceed the 64 MiB no-alloc scratch");
-    const size_t fit_warps = (kNoAllocScratchBytes - fixed - 5 * 256) / (32 * per_pair);
+    const size_t fit_warps = (kNoAllocScratchBytes - fixed - 6 * 256) / (32 * per_pair);
     if (fit_warps < 1)
         return fail(ctx, MCPD_ETOO_LARGE, "not even one warp of pair accumulators fits the 64 MiB no-alloc scratch");
     const int warps = static_cast<int>(std::min<size_t>(shape.warps, fit_warps));
@@ -122,6 +123,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     const size_t o_racc = take(pairs * na * 8), o_sacc = take(pairs * na * 8);
     const size_t o_trep = take(pairs * t.W * 4), o_tslot = take(pairs * t.W * 4);
     const size_t o_y = take(pairs * t.wpp * 4);
+    const size_t o_ps = take(pairs * kPairStats * 8);
     if (off > kNoAllocScratchBytes) return fail(ctx, MCPD_ETOO_LARGE, "no-alloc scratch layout overflow");
 
     unsigned char *b = static_cast<unsigned char *>(base);
@@ -146,6 +148,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     kp.touched_rep = reinterpret_cast<uint32_t *>(b + o_trep);
     kp.touched_slot = reinterpret_cast<uint32_t *>(b + o_tslot);
     kp.y_state = reinterpret_cast<uint32_t *>(b + o_y);
+    kp.pair_stats = reinterpret_cast<unsigned long long *>(b + o_ps);
     kp.S1 = reinterpret_cast<unsigned long long *>(b + o_S1);
     kp.S2lo = reinterpret_cast<unsigned long long *>(b + o_S2lo);
     kp.S2hi = reinterpret_cast<unsigned long long *>(b + o_S2hi);
@@ -159,7 +162,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     kp.P = t.P; kp.B = t.B; kp.k = t.k; kp.ell = t.ell; kp.L = t.L; kp.burn = t.burn;
     kp.length = t.length; kp.unit = t.unit; kp.step_limit = t.step_limit;
     kp.slot_offset = t.slot_offset; kp.trace_stride = 0;
-    kp.seed = t.seed; kp.instance = t.instance; kp.warps = warps;
+    kp.seed = t.seed; philox_round_keys(t.seed, kp.rk); kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
     kp.y_regions = y_regions;
     if (launch_pairs(kp, grid, warps * 32, smem, s) != MCPD_OK)
