@@ -129,12 +129,8 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     ALLOC(d_T, t.T.size());
     ALLOC(d_Tnu, t.Tnu.size());
     ALLOC(d_init, t.init_pairs.size());
-    ALLOC(kp.rep_acc, static_cast<size_t>(pl->pairs) * t.na);
-    ALLOC(kp.slot_acc, static_cast<size_t>(pl->pairs) * t.na);
-    ALLOC(kp.touched_rep, static_cast<size_t>(pl->pairs) * t.W);
-    ALLOC(kp.touched_slot, static_cast<size_t>(pl->pairs) * t.W);
+    ALLOC(kp.pair_scratch, static_cast<size_t>(pl->pairs) * mcpd::pair_words(t.na, t.W));
     ALLOC(kp.y_state, static_cast<size_t>(pl->pairs) * t.wpp);
-    ALLOC(kp.pair_stats, static_cast<size_t>(pl->pairs) * mcpd::kPairStats);
     ALLOC(kp.S1, static_cast<size_t>(t.nb) * t.na);
     ALLOC(kp.S2lo, static_cast<size_t>(t.nb) * t.na);
     ALLOC(kp.S2hi, static_cast<size_t>(t.nb) * t.na);
@@ -209,11 +205,7 @@ int mcpd_run_async(mcpd_ctx *ctx, mcpd_plan *pl, double *est_dev, double *se_dev
     CU(cudaMemsetAsync(kp.counters, 0, mcpd::kNumCounters * 8, ctx->stream));
     CU(cudaMemsetAsync(kp.error, 0, sizeof(int), ctx->stream));
     if (pl->dirty) {   // the kernel leaves these zeroed when it completes normally
-        const size_t pn = static_cast<size_t>(pl->pairs) * t.na;
-        CU(cudaMemsetAsync(kp.rep_acc, 0, pn * 8, ctx->stream));
-        CU(cudaMemsetAsync(kp.slot_acc, 0, pn * 8, ctx->stream));
-        CU(cudaMemsetAsync(kp.touched_rep, 0, static_cast<size_t>(pl->pairs) * t.W * 4, ctx->stream));
-        CU(cudaMemsetAsync(kp.touched_slot, 0, static_cast<size_t>(pl->pairs) * t.W * 4, ctx->stream));
+        CU(cudaMemsetAsync(kp.pair_scratch, 0, static_cast<size_t>(pl->pairs) * mcpd::pair_words(t.na, t.W) * 8, ctx->stream));
         CU(cudaMemsetAsync(kp.y_state, 0, static_cast<size_t>(pl->pairs) * t.wpp * 4, ctx->stream));
     }
     if (kp.trace_G) CU(cudaMemsetAsync(kp.trace_G, 0, static_cast<size_t>(pl->n_trace) * t.na * 8, ctx->stream));
@@ -444,14 +436,11 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
     b->pairs = static_cast<long long>(b->grid) * b->block / lanes;
     if (b->pairs > b->scratch_pairs) {
         free_list(b->scratch);
-        const size_t pn = static_cast<size_t>(b->pairs) * b->bp.max_na, pw = static_cast<size_t>(b->pairs) * b->bp.max_W;
         int rc;
-        if ((rc = balloc(ctx, b->scratch, &b->bp.rep_acc, pn)) != MCPD_OK) return rc;
-        if ((rc = balloc(ctx, b->scratch, &b->bp.slot_acc, pn)) != MCPD_OK) return rc;
-        if ((rc = balloc(ctx, b->scratch, &b->bp.touched_rep, pw)) != MCPD_OK) return rc;
-        if ((rc = balloc(ctx, b->scratch, &b->bp.touched_slot, pw)) != MCPD_OK) return rc;
+        if ((rc = balloc(ctx, b->scratch, &b->bp.pair_scratch,
+                         static_cast<size_t>(b->pairs) * mcpd::pair_words(b->bp.max_na, b->bp.max_W))) != MCPD_OK)
+            return rc;
         if ((rc = balloc(ctx, b->scratch, &b->bp.y_state, static_cast<size_t>(b->pairs) * b->bp.max_wpp)) != MCPD_OK) return rc;
-        if ((rc = balloc(ctx, b->scratch, &b->bp.pair_stats, static_cast<size_t>(b->pairs) * mcpd::kPairStats)) != MCPD_OK) return rc;
         b->scratch_pairs = b->pairs;
         b->dirty = true;
     }
@@ -467,11 +456,8 @@ int batch_enqueue(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev,
     CU(cudaMemsetAsync(b->bp.counters, 0, mcpd::kNumCounters * 8, s));
     CU(cudaMemsetAsync(b->bp.error, 0, sizeof(int), s));
     if (b->dirty || always_clear) {
-        const size_t pn = static_cast<size_t>(b->pairs) * b->bp.max_na, pw = static_cast<size_t>(b->pairs) * b->bp.max_W;
-        CU(cudaMemsetAsync(b->bp.rep_acc, 0, pn * 8, s));
-        CU(cudaMemsetAsync(b->bp.slot_acc, 0, pn * 8, s));
-        CU(cudaMemsetAsync(b->bp.touched_rep, 0, pw * 4, s));
-        CU(cudaMemsetAsync(b->bp.touched_slot, 0, pw * 4, s));
+        CU(cudaMemsetAsync(b->bp.pair_scratch, 0,
+                           static_cast<size_t>(b->pairs) * mcpd::pair_words(b->bp.max_na, b->bp.max_W) * 8, s));
         CU(cudaMemsetAsync(b->bp.y_state, 0, static_cast<size_t>(b->pairs) * b->bp.max_wpp * 4, s));
     }
     if ((b->bp.lanes == 1 ? mcpd::launch_batch(b->bp, b->grid, b->block, b->smem, s)

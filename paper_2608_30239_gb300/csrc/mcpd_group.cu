@@ -34,10 +34,11 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
     for (int w = gl; w < 2 * wpp; w += G) X[w] = 0u;
     __syncthreads();
 
-    long long *racc = bp.rep_acc + gid * bp.max_na;
-    long long *sacc = bp.slot_acc + gid * bp.max_na;
-    uint32_t *trep = bp.touched_rep + gid * bp.max_W;
-    uint32_t *tslot = bp.touched_slot + gid * bp.max_W;
+    long long *const pb = bp.pair_scratch + gid * pair_words(bp.max_na, bp.max_W);   // see pair_words
+    long long *racc = pb;
+    long long *sacc = pb + bp.max_na;
+    uint32_t *trep = reinterpret_cast<uint32_t *>(pb + 2 * bp.max_na + kPairStats);
+    uint32_t *tslot = trep + bp.max_W;
 
     // per-instance values (group-uniform)
     const unsigned long long *gAlias = nullptr, *gT = nullptr, *Tnu = nullptr;

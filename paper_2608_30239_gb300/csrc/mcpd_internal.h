@@ -41,6 +41,14 @@ enum PairStat {
     kPairStats = 8
 };
 
+// Per-pair scratch, one contiguous block of 8-byte words per pair: the replication's sums G
+// [0, na), the slot's sums [na, 2 na), the statistics record [2 na, 2 na + kPairStats), then the
+// touched-clone bit sets of the replication and of the slot (W 32-bit words each).
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline long long pair_words(long long na, long long W) { return 2 * na + kPairStats + W; }
+
 // Everything the sampler needs, built on the host from (design, y, params).
 struct Tables {
     int32_t n = 0, m = 0, na = 0, deg_max = 0;
@@ -81,12 +89,8 @@ struct KParams {
     const uint64_t *Tnu;
     const uint32_t *init_pairs;       // [n_init_pairs]
     int32_t n_init_pairs;
-    long long *rep_acc;               // [pairs][na]
-    long long *slot_acc;              // [pairs][na]
-    uint32_t *touched_rep;            // [pairs][W]
-    uint32_t *touched_slot;           // [pairs][W]
+    long long *pair_scratch;          // [pairs][pair_words(na, W)]
     uint32_t *y_state;                // [pairs / 32][wpp][32] fallback Y columns (pairs not yet met)
-    unsigned long long *pair_stats;   // [pairs][kPairStats]
     unsigned long long *S1;           // [nb][na]
     unsigned long long *S2lo;         // [nb][na]
     unsigned long long *S2hi;         // [nb][na]
@@ -146,12 +150,8 @@ struct BParams {
     int32_t n_inst, coupled, scan, max_wpp;
     int32_t lanes, max_m;             // lanes per pair (1, 8, 16, 32); largest pool count
     long long total_work;
-    long long *rep_acc;               // [pairs][max_na]
-    long long *slot_acc;              // [pairs][max_na]
-    uint32_t *touched_rep;            // [pairs][max_W]
-    uint32_t *touched_slot;           // [pairs][max_W]
+    long long *pair_scratch;          // [pairs][pair_words(max_na, max_W)]
     uint32_t *y_state;                // [pairs / 32][max_wpp][32] fallback Y columns
-    unsigned long long *pair_stats;   // [pairs][kPairStats]
     unsigned long long *counters;
     int *error;
     int32_t max_na, max_W;

@@ -82,20 +82,24 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     if constexpr (!BATCH) st[p.dummy_word_index * 32] = p.dummy_word;
     __syncthreads();
 
-    const long long gpair = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint32_t gpair = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride_na = BATCH ? bp.max_na : p.na, stride_W = BATCH ? bp.max_W : p.W;
-    long long *racc = (BATCH ? bp.rep_acc : p.rep_acc) + gpair * stride_na;
-    long long *sacc = (BATCH ? bp.slot_acc : p.slot_acc) + gpair * stride_na;
-    uint32_t *trep = (BATCH ? bp.touched_rep : p.touched_rep) + gpair * stride_W;
-    uint32_t *tslot = (BATCH ? bp.touched_slot : p.touched_slot) + gpair * stride_W;
+    // This pair's scratch block (see pair_words): one base pointer, the parts at fixed offsets.
+    long long *const pb = (BATCH ? bp.pair_scratch : p.pair_scratch) +
+                          static_cast<size_t>(gpair) * static_cast<size_t>(pair_words(stride_na, stride_W));
+    auto racc = [&]() { return pb; };
+    auto sacc = [&]() { return pb + stride_na; };
+    auto pst = [&]() { return reinterpret_cast<unsigned long long *>(pb + 2 * stride_na); };
+    auto trep = [&]() { return reinterpret_cast<uint32_t *>(pb + 2 * stride_na + kPairStats); };
+    auto tslot = [&]() { return reinterpret_cast<uint32_t *>(pb + 2 * stride_na + kPairStats) + stride_W; };
     unsigned long long *counters = BATCH ? bp.counters : p.counters;
-    uint32_t *const yglob = (BATCH ? bp.y_state : p.y_state) + static_cast<size_t>(gpair >> 5) * region_words + lane;
-    uint32_t *ycol = yglob;           // the Y column in use (shared or global), while D != 0
+    auto yglob = [&]() {
+        return (BATCH ? bp.y_state : p.y_state) + static_cast<size_t>(gpair >> 5) * region_words + lane;
+    };
+    uint32_t *ycol = nullptr;         // the Y column in use (shared or global), while D != 0
     int yslot = -1;                   // its index in the Y regions, -1 for the global column
-    // This pair's statistics (rare updates, plain global read-modify-write), summed at the end.
-    unsigned long long *const pst = (BATCH ? bp.pair_stats : p.pair_stats) + gpair * kPairStats;
 #pragma unroll
-    for (int i = 0; i < kPairStats; ++i) pst[i] = 0ull;
+    for (int i = 0; i < kPairStats; ++i) pst()[i] = 0ull;
 
     // Per-instance values (fixed for a single instance, reloaded when a batched slot changes
     // instance).
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             }
         }
         __threadfence_block();
-        ycol = yslot >= 0 ? yreg + (yslot >> 5) * region_words + (yslot & 31) : yglob;
+        ycol = yslot >= 0 ? yreg + (yslot >> 5) * region_words + (yslot & 31) : yglob();
         if (DEG == 0) ycol[dummy_word_index * 32] = dummy_word;
     };
     // Empty the Y column in use (every Y bit lies in a group marked in rep_words) and return it.
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         __threadfence_block();
         if (yslot >= 0) atomicOr(&ymask[yslot >> 5], 1u << (yslot & 31));
         yslot = -1;
-        ycol = yglob;
+        ycol = nullptr;
     };
     // The pre-lag update flipped site I of X_0 and the start was random: Y_0 = X_0 (X_1 with bit
     // I restored) goes to the Y column.
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
         stop_unmet = min(abort_t, step_limit);
         t_end = COUPLED ? min(max(ell, 1u), stop_unmet) : min(unit, step_limit);
-        ++pst[kPsStarted];
+        ++pst()[kPsStarted];
         ++reps_in_slot;
         if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0 (clones with nu_i = 0 stay 0)
             for (int e = 0; e < n_init_pairs; ++e) {
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             const uint32_t q1 = min(W, q0 + (1u << gshift));
             for (uint32_t q = q0; q < q1; ++q) {
                 const uint32_t xw = st[q * 32];
-                const uint32_t tw = trep[q];
+                const uint32_t tw = trep()[q];
                 uint32_t m = tw | xw, moved = 0;
                 if (!m) continue;
                 while (m) {
@@ -326,19 +330,19 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
                     m &= m - 1;
                     const uint32_t j = q * 32 + b;
                     long long v = 0;
-                    if (tw & bit) { v = racc[j]; racc[j] = 0; }
+                    if (tw & bit) { v = racc()[j]; racc()[j] = 0; }
                     if (move) {
                         if (xw & bit) v += wX;
                         if (v != 0) {
-                            atomicAdd(reinterpret_cast<unsigned long long *>(&sacc[j]), static_cast<unsigned long long>(v));
+                            atomicAdd(reinterpret_cast<unsigned long long *>(&sacc()[j]), static_cast<unsigned long long>(v));
                             moved |= bit;
                         }
                     }
                     if (xw & bit) bump_counts(j, 0xFFu, cbase);
                 }
-                if (tw) trep[q] = 0u;
+                if (tw) trep()[q] = 0u;
                 if (xw) st[q * 32] = 0u;
-                if (moved) { atomicOr(&tslot[q], moved); slot_words |= 1u << g; }
+                if (moved) { atomicOr(&tslot()[q], moved); slot_words |= 1u << g; }
             }
         }
         rep_words = 0;
@@ -358,20 +362,20 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             const uint32_t q0 = static_cast<uint32_t>(g) << gshift;
             const uint32_t q1 = min(W, q0 + (1u << gshift));
             for (uint32_t q = q0; q < q1; ++q) {
-                uint32_t tw = tslot[q];
+                uint32_t tw = tslot()[q];
                 if (!tw) continue;
                 while (tw) {
                     const int b = __ffs(tw) - 1;
                     tw &= tw - 1;
                     const uint32_t j = q * 32 + b;
-                    const long long gsum = sacc[j];
-                    sacc[j] = 0;
+                    const long long gsum = sacc()[j];
+                    sacc()[j] = 0;
                     if (valid && gsum != 0) {
                         bucket_add(bS1, bS2lo, bS2hi, na, bkt, static_cast<int>(j), gsum);
                         if (tr) tr[j] = gsum;
                     }
                 }
-                tslot[q] = 0u;
+                tslot()[q] = 0u;
             }
         }
         slot_words = 0;
@@ -390,30 +394,30 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     // finish within B is aborted before it completes); then refill or end the slot.
     auto complete = [&]() {
         const uint32_t C = t;
-        pst[kPsProgress] += C;
+        pst()[kPsProgress] += C;
         if (COUPLED) {
-            pst[kPsSumTau] += tau;
-            if (tau > pst[kPsMaxTau]) pst[kPsMaxTau] = tau;
+            pst()[kPsSumTau] += tau;
+            if (tau > pst()[kPsMaxTau]) pst()[kPsMaxTau] = tau;
         }
         finish_rep(true, C);
         S += C;
         N += 1;
-        ++pst[kPsRetained];
-        if (S > B) ++pst[kPsZero];           // only a slot's first replication can end beyond B
+        ++pst()[kPsRetained];
+        if (S > B) ++pst()[kPsZero];           // only a slot's first replication can end beyond B
         if (S < B && B - S >= unit) { ++r; start_rep(); }
         else end_slot(true);
     };
 
     auto abort_rep = [&]() {                  // doomed: S_p(r) would exceed B; discard it
-        pst[kPsProgress] += t;
-        ++pst[kPsAborted];
+        pst()[kPsProgress] += t;
+        ++pst()[kPsAborted];
         finish_rep(false, 0);
         end_slot(true);
     };
 
     auto limit_hit = [&]() {
-        pst[kPsProgress] += t;
-        ++pst[kPsLimit];
+        pst()[kPsProgress] += t;
+        ++pst()[kPsLimit];
         atomicExch(BATCH ? bp.error : p.error, 1);
         finish_rep(false, 0);
         end_slot(false);
@@ -440,8 +444,8 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             if (real(l, ent)) cbase[ent[l] & 0x7FFFu] = static_cast<unsigned char>(cx[l] + delta);
         const uint32_t w = wstep(t);
         if (w) {
-            red_add(&racc[I], nX ? -static_cast<long long>(w) : static_cast<long long>(w));
-            red_or(&trep[q], bit);
+            red_add(&racc()[I], nX ? -static_cast<long long>(w) : static_cast<long long>(w));
+            red_or(&trep()[q], bit);
         }
         rep_words |= 1u << (q >> gshift);
         if (COUPLED && t == 0) {            // X_1 differs from Y_0 in bit I
@@ -477,8 +481,8 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             ev += nY ? w : -w;
         }
         if (ev != 0) {
-            red_add(&racc[I], ev);
-            red_or(&trep[q], bit);
+            red_add(&racc()[I], ev);
+            red_or(&trep()[q], bit);
         }
         rep_words |= 1u << (q >> gshift);
         D = D + (nX ^ nY) - (xI ^ yI);
@@ -592,7 +596,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
                                  kZeroCompletion, kStepLimitHits, kSumTau, kMaxTau};
 #pragma unroll
     for (int i = 0; i < kPairStats; ++i) {
-        unsigned long long v = pst[i];
+        unsigned long long v = pst()[i];
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long u = __shfl_down_sync(0xFFFFFFFFu, v, o);
             v = i == kPsMaxTau ? max(v, u) : v + u;

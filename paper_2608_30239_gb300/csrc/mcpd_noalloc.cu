@@ -108,11 +108,11 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
                                 ctx->sm_count, 0, &shape);
     if (src == MCPD_ETOO_LARGE) return fail(ctx, src, "instance too large for the one-thread-per-pair layout");
     if (src != MCPD_OK) return fail(ctx, MCPD_ECUDA, "launch shape (cudaFuncSetAttribute / occupancy)");
-    // sums, touched sets, Y column, statistics record
-    const size_t per_pair = na * 16 + static_cast<size_t>(t.W) * 8 + static_cast<size_t>(t.wpp) * 4 + kPairStats * 8;
+    // scratch block (sums, statistics, touched sets) and Y column
+    const size_t per_pair = static_cast<size_t>(pair_words(t.na, t.W)) * 8 + static_cast<size_t>(t.wpp) * 4;
     if (fixed >= kNoAllocScratchBytes)
         return fail(ctx, MCPD_ETOO_LARGE, "tables and N*_p buckets exceed the 64 MiB no-alloc scratch");
-    const size_t fit_warps = (kNoAllocScratchBytes - fixed - 6 * 256) / (32 * per_pair);
+    const size_t fit_warps = (kNoAllocScratchBytes - fixed - 2 * 256) / (32 * per_pair);
     if (fit_warps < 1)
         return fail(ctx, MCPD_ETOO_LARGE, "not even one warp of pair accumulators fits the 64 MiB no-alloc scratch");
     const int warps = static_cast<int>(std::min<size_t>(shape.warps, fit_warps));
@@ -120,10 +120,8 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     const size_t smem = pairs_smem_bytes(tables, t.wpp, warps, y_regions);
     const int grid = static_cast<int>(std::min<size_t>(static_cast<size_t>(ctx->sm_count) * shape.per_sm, fit_warps / warps));
     const size_t pairs = static_cast<size_t>(grid) * warps * 32;
-    const size_t o_racc = take(pairs * na * 8), o_sacc = take(pairs * na * 8);
-    const size_t o_trep = take(pairs * t.W * 4), o_tslot = take(pairs * t.W * 4);
+    const size_t o_pair = take(pairs * static_cast<size_t>(pair_words(t.na, t.W)) * 8);
     const size_t o_y = take(pairs * t.wpp * 4);
-    const size_t o_ps = take(pairs * kPairStats * 8);
     if (off > kNoAllocScratchBytes) return fail(ctx, MCPD_ETOO_LARGE, "no-alloc scratch layout overflow");
 
     unsigned char *b = static_cast<unsigned char *>(base);
@@ -143,12 +141,8 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     kp.Tnu = t.Tnu.empty() ? nullptr : reinterpret_cast<const uint64_t *>(b + o_Tnu);
     kp.init_pairs = reinterpret_cast<const uint32_t *>(b + o_init);
     kp.n_init_pairs = static_cast<int32_t>(t.init_pairs.size());
-    kp.rep_acc = reinterpret_cast<long long *>(b + o_racc);
-    kp.slot_acc = reinterpret_cast<long long *>(b + o_sacc);
-    kp.touched_rep = reinterpret_cast<uint32_t *>(b + o_trep);
-    kp.touched_slot = reinterpret_cast<uint32_t *>(b + o_tslot);
+    kp.pair_scratch = reinterpret_cast<long long *>(b + o_pair);
     kp.y_state = reinterpret_cast<uint32_t *>(b + o_y);
-    kp.pair_stats = reinterpret_cast<unsigned long long *>(b + o_ps);
     kp.S1 = reinterpret_cast<unsigned long long *>(b + o_S1);
     kp.S2lo = reinterpret_cast<unsigned long long *>(b + o_S2lo);
     kp.S2hi = reinterpret_cast<unsigned long long *>(b + o_S2hi);
