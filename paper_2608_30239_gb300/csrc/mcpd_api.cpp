@@ -100,7 +100,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
 
     // Launch shape: tables first in shared memory, then one 32-column region per warp and the
     // Y regions.
-    const size_t tables = ((static_cast<size_t>(t.na) * 24 + mcpd::kTSide * mcpd::kTSide * 8) + 15) / 16 * 16;
+    const size_t tables = mcpd::kernel_table_bytes(t);
     mcpd::PairsShape shape;
     rc = mcpd::pairs_shape(t.coupled, t.scan, t.udeg, false, tables, t.wpp, ctx->smem_optin, t.P,
                            ctx->sm_count, 0, &shape);
@@ -125,8 +125,8 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
         if (r_ != MCPD_OK) { mcpd_plan_destroy(pl); return r_; }             \
     } while (0)
     ALLOC(d_alias, t.alias.size());
-    ALLOC(d_rows, t.rows.size());
-    ALLOC(d_T, t.T.size());
+    ALLOC(d_rows, mcpd::kernel_rows(t).size());
+    ALLOC(d_T, mcpd::kernel_T(t).size());
     ALLOC(d_Tnu, t.Tnu.size());
     ALLOC(d_init, t.init_pairs.size());
     ALLOC(kp.pair_scratch, static_cast<size_t>(pl->pairs) * mcpd::pair_words(t.na, t.W));
@@ -150,8 +150,8 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     }
 #undef ALLOC
     CU(cudaMemcpyAsync(d_alias, t.alias.data(), t.alias.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(d_rows, t.rows.data(), t.rows.size() * 2, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(d_T, t.T.data(), t.T.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(d_rows, mcpd::kernel_rows(t).data(), mcpd::kernel_rows(t).size() * 2, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaMemcpyAsync(d_T, mcpd::kernel_T(t).data(), mcpd::kernel_T(t).size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     if (!t.Tnu.empty())
         CU(cudaMemcpyAsync(d_Tnu, t.Tnu.data(), t.Tnu.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
     if (!t.init_pairs.empty())
@@ -167,6 +167,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     kp.slot_offset = t.slot_offset; kp.trace_stride = t.trace_stride;
     kp.seed = t.seed; mcpd::philox_round_keys(t.seed, kp.rk); kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
+    kp.nT = static_cast<int32_t>(mcpd::kernel_T(t).size());
     kp.y_regions = shape.y_regions;
     CU(cudaEventCreate(&pl->ev0));
     CU(cudaEventCreate(&pl->ev1));

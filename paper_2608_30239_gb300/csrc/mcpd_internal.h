@@ -23,6 +23,7 @@ namespace mcpd {
 
 constexpr int kRow = 8;              // pool entries per clone row (one 16-byte shared load)
 constexpr int kTSide = kRow + 1;     // acceptance table is kTSide x kTSide, indexed 9 n+ + n-
+constexpr int kMaskDeg = 6;          // uniform degrees up to this use mask-indexed thresholds
 constexpr int kWarpsPerYRegion = 8; // one 32-column Y region per 8 warps (pairs not yet met)
 constexpr int kMaxClones = 65535;
 constexpr int kMaxPools = 1022;      // pool byte offsets must fit 16 bits
@@ -62,6 +63,8 @@ struct Tables {
     std::vector<uint64_t> Tnu;        // [na] or empty
     std::vector<uint32_t> init_pairs; // even clone ids a with Tnu[a] or Tnu[a+1] nonzero
     std::vector<double> w;            // [na] scan weights
+    std::vector<uint16_t> rows_mask;  // [na * kRow] uniform degree <= kMaskDeg: see build_tables
+    std::vector<uint64_t> T_mask;     // [(kMaskDeg + 1) * 64] or empty
     // shared-memory layout of one pair (32-bit words, interleaved over the 32 lanes of a warp)
     int32_t udeg = 0;                 // d if every active clone sits in exactly d pools, else 0
     int32_t W = 0;                    // bit-set words per chain
@@ -80,6 +83,13 @@ struct Tables {
 
 int build_tables(const mcpd_design *design, const uint8_t *y, const mcpd_params *params,
                  Tables *out, std::string *err);
+
+// The rows and thresholds the single-instance kernel stages (mask-indexed when available).
+inline const std::vector<uint16_t> &kernel_rows(const Tables &t) { return t.rows_mask.empty() ? t.rows : t.rows_mask; }
+inline const std::vector<uint64_t> &kernel_T(const Tables &t) { return t.T_mask.empty() ? t.T : t.T_mask; }
+inline size_t kernel_table_bytes(const Tables &t) {
+    return (static_cast<size_t>(t.na) * 24 + kernel_T(t).size() * 8 + 15) / 16 * 16;
+}
 
 // Kernel arguments (plain types only: shared by host and device compilation units).
 struct KParams {
@@ -112,6 +122,7 @@ struct KParams {
     uint32_t smem_tables;             // bytes of staged tables at the start of shared memory
     int32_t y_regions;                // 32-column Y regions in shared memory
     uint32_t rk[20];                  // Philox round keys of the seed
+    int32_t nT;                       // threshold entries staged (kTSide^2, or mask-indexed)
 };
 
 // Philox4x32-10 round keys of a 64-bit seed: (lo + i 0x9E3779B9, hi + i 0xBB67AE85), i = 0..9.

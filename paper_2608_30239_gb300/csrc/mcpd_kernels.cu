@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             sRows[i] = reinterpret_cast<const uint4 *>(p.rows)[i];
             sAlias[i] = p.alias[i];
         }
-        for (int i = threadIdx.x; i < kTSide * kTSide; i += blockDim.x) sT[i] = p.T[i];
+        for (int i = threadIdx.x; i < p.nT; i += blockDim.x) sT[i] = p.T[i];
         wpp = p.wpp;
         nyr = p.y_regions;
         regions = reinterpret_cast<uint32_t *>(smem + p.smem_tables);
@@ -147,6 +147,10 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         derive();
     }
     constexpr int NE = DEG > 0 ? DEG : kRow;       // row entries visited per clone
+    // Uniform degree <= kMaskDeg, single instance: rows hold plain offsets with the clone's
+    // positive-outcome pools first and their number in the last entry; thresholds are indexed
+    // npos * 64 + (mask of deciding pools).
+    constexpr bool MASKT = COUPLED && !BATCH && DEG >= 3 && DEG <= kMaskDeg;
     auto rowAt = [&](uint32_t c) -> uint4 {
         if constexpr (BATCH) return __ldg(gRows + c); else return sRows[c];
     };
@@ -519,10 +523,16 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             cx[l] = 0u;
             cy[l] = 0u;
             if (l < NE && (DEG > 0 || l < deg)) {
-                cx[l] = cbase[ent[l] & 0x7FFFu];
-                if (cx[l] == xI) ix += (ent[l] >> 15) ? 9u : 1u;   // c_j - x_I = 0: pool j decides
+                if constexpr (MASKT) {     // plain offsets, positive-outcome pools first
+                    cx[l] = cbase[ent[l]];
+                    if (cx[l] == xI) ix |= 1u << l;                // c_j - x_I = 0: pool j decides
+                } else {
+                    cx[l] = cbase[ent[l] & 0x7FFFu];
+                    if (cx[l] == xI) ix += (ent[l] >> 15) ? 9u : 1u;
+                }
             }
         }
+        if constexpr (MASKT) ix += ent[kRow - 1] << 6;           // row of the positive-pool count
         const unsigned long long TX = tAt(ix);
         unsigned long long TY = TX;
         uint32_t yw = xw, yI = xI;
@@ -536,10 +546,16 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
 #pragma unroll
             for (int l = 0; l < kRow; ++l) {
                 if (l < NE && (DEG > 0 || l < deg)) {
-                    cy[l] = own ? static_cast<uint32_t>(yb[ent[l] & 0x7FFFu]) : cx[l];
-                    if (cy[l] == yI) iy += (ent[l] >> 15) ? 9u : 1u;
+                    if constexpr (MASKT) {
+                        cy[l] = own ? static_cast<uint32_t>(yb[ent[l]]) : cx[l];
+                        if (cy[l] == yI) iy |= 1u << l;
+                    } else {
+                        cy[l] = own ? static_cast<uint32_t>(yb[ent[l] & 0x7FFFu]) : cx[l];
+                        if (cy[l] == yI) iy += (ent[l] >> 15) ? 9u : 1u;
+                    }
                 }
             }
+            if constexpr (MASKT) iy += ent[kRow - 1] << 6;
             TY = tAt(iy);
         };
         if (COUPLED) {

@@ -95,14 +95,14 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     const size_t na = static_cast<size_t>(t.na), nb = static_cast<size_t>(t.nb);
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t at = off; off += up256(bytes); return at; };
-    const size_t o_alias = take(na * 8), o_rows = take(na * 16), o_T = take(t.T.size() * 8);
+    const size_t o_alias = take(na * 8), o_rows = take(na * 16), o_T = take(kernel_T(t).size() * 8);
     const size_t o_Tnu = take(t.Tnu.size() * 8), o_init = take(t.init_pairs.size() * 4);
     const size_t o_S1 = take(nb * na * 8), o_S2lo = take(nb * na * 8), o_S2hi = take(nb * na * 8);
     const size_t o_bc = take(nb * 8), o_cnt = take(kNumCounters * 8), o_err = take(sizeof(int));
     const size_t fixed = off;
 
     // Launch shape as the allocating path would choose it, then as many whole warps as fit.
-    const size_t tables = ((na * 24 + kTSide * kTSide * 8) + 15) / 16 * 16;
+    const size_t tables = kernel_table_bytes(t);
     PairsShape shape;
     const int src = pairs_shape(t.coupled, t.scan, t.udeg, false, tables, t.wpp, ctx->smem_optin, t.P,
                                 ctx->sm_count, 0, &shape);
@@ -128,8 +128,8 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     cudaStream_t s = ctx->stream;
     CUN(cudaMemsetAsync(b, 0, off, s));     // the array keeps the previous call's contents
     CUN(cudaMemcpyAsync(b + o_alias, t.alias.data(), na * 8, cudaMemcpyHostToDevice, s));
-    CUN(cudaMemcpyAsync(b + o_rows, t.rows.data(), t.rows.size() * 2, cudaMemcpyHostToDevice, s));
-    CUN(cudaMemcpyAsync(b + o_T, t.T.data(), t.T.size() * 8, cudaMemcpyHostToDevice, s));
+    CUN(cudaMemcpyAsync(b + o_rows, kernel_rows(t).data(), kernel_rows(t).size() * 2, cudaMemcpyHostToDevice, s));
+    CUN(cudaMemcpyAsync(b + o_T, kernel_T(t).data(), kernel_T(t).size() * 8, cudaMemcpyHostToDevice, s));
     if (!t.Tnu.empty()) CUN(cudaMemcpyAsync(b + o_Tnu, t.Tnu.data(), t.Tnu.size() * 8, cudaMemcpyHostToDevice, s));
     if (!t.init_pairs.empty())
         CUN(cudaMemcpyAsync(b + o_init, t.init_pairs.data(), t.init_pairs.size() * 4, cudaMemcpyHostToDevice, s));
@@ -158,6 +158,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     kp.slot_offset = t.slot_offset; kp.trace_stride = 0;
     kp.seed = t.seed; philox_round_keys(t.seed, kp.rk); kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
+    kp.nT = static_cast<int32_t>(kernel_T(t).size());
     kp.y_regions = y_regions;
     if (launch_pairs(kp, grid, warps * 32, smem, s) != MCPD_OK)
         return fail(ctx, MCPD_ECUDA, std::string("pairs kernel launch: ") + cudaGetErrorString(cudaGetLastError()));

@@ -227,6 +227,33 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
             t.rows_pool[static_cast<size_t>(a) * kRow + l] = static_cast<uint16_t>(j | (y[j] ? 0x8000u : 0u));
         }
     }
+    // Coupled runs with a uniform degree 3 <= d <= kMaskDeg (single-instance kernels compiled
+    // for d): each row lists the clone's positive-outcome pools first, as plain count offsets,
+    // with their number in entry kRow - 1; T_mask[npos][m] = T[9 n+ + n-] for the mask m of
+    // deciding pools (n+ of them among the first npos entries, n- among the rest).  The same
+    // thresholds, indexed without per-entry codes.
+    t.rows_mask.clear();
+    t.T_mask.clear();
+    if (t.coupled && t.udeg >= 3 && t.udeg <= kMaskDeg) {   // the kernels compiled for degree d
+        t.rows_mask.assign(static_cast<size_t>(na) * kRow, 0);
+        for (int32_t a = 0; a < na; ++a) {
+            const uint16_t *src = &t.rows[static_cast<size_t>(a) * kRow];
+            uint16_t *dst = &t.rows_mask[static_cast<size_t>(a) * kRow];
+            int32_t n = 0;
+            for (int32_t l = 0; l < t.udeg; ++l) if (src[l] & 0x8000u) dst[n++] = static_cast<uint16_t>(src[l] & 0x7FFFu);
+            const int32_t npos = n;
+            for (int32_t l = 0; l < t.udeg; ++l) if (!(src[l] & 0x8000u)) dst[n++] = src[l];
+            dst[kRow - 1] = static_cast<uint16_t>(npos);
+        }
+        t.T_mask.assign(static_cast<size_t>(kMaskDeg + 1) * 64, 0);
+        for (int32_t npos = 0; npos <= kMaskDeg; ++npos)
+            for (int32_t m = 0; m < 64; ++m) {
+                int32_t np = 0, nn = 0;
+                for (int32_t l = 0; l < 6; ++l)
+                    if (m >> l & 1) { if (l < npos) ++np; else ++nn; }
+                t.T_mask[static_cast<size_t>(npos) * 64 + m] = t.T[static_cast<size_t>(np) * kTSide + nn];
+            }
+    }
 
     // Window, horizon and bucket count.
     t.P = prm->slots;
