@@ -500,17 +500,29 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     // One step of the pair.  X's full conditional from its counts; when some lane of the warp
     // has not met, Y's from its own column (a met lane reads its X column there, so Y = X).
     // The uniform U = wu 2^32 + lo needs lo only when wu equals a threshold's high word.
-    auto step = [&](uint32_t ws, uint32_t wu) -> int {
+    // The site a step word selects (alias draw).
+    auto site_of = [&](uint32_t ws) -> uint32_t {
+        const unsigned long long prod = static_cast<unsigned long long>(ws) * static_cast<uint32_t>(na);
+        const uint32_t col = static_cast<uint32_t>(prod >> 32), coin = static_cast<uint32_t>(prod);
+        const unsigned long long e = aliasAt(col);
+        return coin < static_cast<uint32_t>(e) ? col : static_cast<uint32_t>(e >> 32);
+    };
+    // The site of the current step and its row, drawn ahead: they depend on the step words only,
+    // so the next step's alias and row loads overlap this step's work.
+    uint32_t I_cur = 0;
+    uint4 row_cur = make_uint4(0u, 0u, 0u, 0u);
+    auto step = [&](uint32_t ws_next, uint32_t wu) -> int {
         uint32_t I;
+        uint4 row;
         if (SYSTEMATIC) {
             I = sysI;
+            row = rowAt(I);
         } else {
-            const unsigned long long prod = static_cast<unsigned long long>(ws) * static_cast<uint32_t>(na);
-            const uint32_t col = static_cast<uint32_t>(prod >> 32), coin = static_cast<uint32_t>(prod);
-            const unsigned long long e = aliasAt(col);
-            I = coin < static_cast<uint32_t>(e) ? col : static_cast<uint32_t>(e >> 32);
+            I = I_cur;
+            row = row_cur;
+            I_cur = site_of(ws_next);
+            row_cur = rowAt(I_cur);
         }
-        const uint4 row = rowAt(I);
         const uint32_t q = I >> 5, bit = 1u << (I & 31);
         const uint32_t xw = st[q * 32];
         const uint32_t xI = (xw & bit) ? 1u : 0u;
@@ -590,18 +602,23 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     };
     start_slot();
     uint4 blk = draw(t >> 1);
+    auto first_site = [&]() {               // the first step of a block
+        if (!SYSTEMATIC) { I_cur = site_of(blk.x); row_cur = rowAt(I_cur); }
+    };
+    first_site();
     while (alive) {
         // words (0,1) at even t and (2,3) at odd t; the next block is computed ahead and
         // discarded if the replication ends
         const uint4 nxt = draw((t >> 1) + 1);
         int ended = 0;
 #pragma unroll 1
-        for (int h = 0; h < 2 && !ended; ++h) ended = step(h ? blk.z : blk.x, h ? blk.w : blk.y);
+        for (int h = 0; h < 2 && !ended; ++h) ended = step(h ? nxt.x : blk.z, h ? blk.w : blk.y);
         if (ended) {
             if (ended == 1) complete();
             else if (ended == 2) abort_rep();
             else limit_hit();
             blk = draw(t >> 1);
+            first_site();
         } else {
             blk = nxt;
         }
