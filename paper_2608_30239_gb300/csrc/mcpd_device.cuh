@@ -38,6 +38,9 @@ static __device__ __noinline__ uint32_t philox_low_word(uint4 c, uint32_t k0, ui
 static __device__ __forceinline__ void red_add(long long *a, long long v) {
     asm volatile("red.global.add.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
 }
+static __device__ __forceinline__ void red_max(unsigned long long *a, unsigned long long v) {
+    asm volatile("red.global.max.u64 [%0], %1;" ::"l"(a), "l"(v) : "memory");
+}
 static __device__ __forceinline__ void red_or(uint32_t *a, uint32_t v) {
     asm volatile("red.global.or.b32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
 }

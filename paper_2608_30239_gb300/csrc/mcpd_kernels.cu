@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
         stop_unmet = min(abort_t, step_limit);
         t_end = COUPLED ? min(max(ell, 1u), stop_unmet) : min(unit, step_limit);
-        ++pst()[kPsStarted];
+        red_add(reinterpret_cast<long long *>(&pst()[kPsStarted]), 1);
         ++reps_in_slot;
         if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0 (clones with nu_i = 0 stay 0)
             for (int e = 0; e < n_init_pairs; ++e) {
@@ -317,6 +317,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     auto finish_rep = [&](bool move, uint32_t C) {
         const long long wX = move ? static_cast<long long>(wstep(C)) : 0;
         if (COUPLED && D != 0) release_y();
+        long long *const ra = racc();
         uint32_t groups = rep_words;
         while (groups) {
             const int g = __ffs(groups) - 1;
@@ -325,28 +326,25 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             const uint32_t q1 = min(W, q0 + (1u << gshift));
             for (uint32_t q = q0; q < q1; ++q) {
                 const uint32_t xw = st[q * 32];
-                const uint32_t tw = trep()[q];
-                uint32_t m = tw | xw, moved = 0;
-                if (!m) continue;
+                const uint32_t tw = __ldcg(&trep()[q]);
+                uint32_t moved = 0;
+                uint32_t m = tw | xw;
                 while (m) {
                     const int b = __ffs(m) - 1;
                     const uint32_t bit = 1u << b;
                     m &= m - 1;
                     const uint32_t j = q * 32 + b;
                     long long v = 0;
-                    if (tw & bit) { v = racc()[j]; racc()[j] = 0; }
+                    if (tw & bit) { v = __ldcg(&ra[j]); ra[j] = 0; }
                     if (move) {
                         if (xw & bit) v += wX;
-                        if (v != 0) {
-                            atomicAdd(reinterpret_cast<unsigned long long *>(&sacc()[j]), static_cast<unsigned long long>(v));
-                            moved |= bit;
-                        }
+                        if (v != 0) { red_add(&sacc()[j], v); moved |= bit; }
                     }
                     if (xw & bit) bump_counts(j, 0xFFu, cbase);
                 }
                 if (tw) trep()[q] = 0u;
                 if (xw) st[q * 32] = 0u;
-                if (moved) { atomicOr(&tslot()[q], moved); slot_words |= 1u << g; }
+                if (moved) { red_or(&tslot()[q], moved); slot_words |= 1u << g; }
             }
         }
         rep_words = 0;
@@ -366,13 +364,13 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             const uint32_t q0 = static_cast<uint32_t>(g) << gshift;
             const uint32_t q1 = min(W, q0 + (1u << gshift));
             for (uint32_t q = q0; q < q1; ++q) {
-                uint32_t tw = tslot()[q];
+                uint32_t tw = __ldcg(&tslot()[q]);
                 if (!tw) continue;
                 while (tw) {
                     const int b = __ffs(tw) - 1;
                     tw &= tw - 1;
                     const uint32_t j = q * 32 + b;
-                    const long long gsum = sacc()[j];
+                    const long long gsum = __ldcg(&sacc()[j]);
                     sacc()[j] = 0;
                     if (valid && gsum != 0) {
                         bucket_add(bS1, bS2lo, bS2hi, na, bkt, static_cast<int>(j), gsum);
@@ -398,30 +396,30 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     // finish within B is aborted before it completes); then refill or end the slot.
     auto complete = [&]() {
         const uint32_t C = t;
-        pst()[kPsProgress] += C;
+        red_add(reinterpret_cast<long long *>(&pst()[kPsProgress]), C);
         if (COUPLED) {
-            pst()[kPsSumTau] += tau;
-            if (tau > pst()[kPsMaxTau]) pst()[kPsMaxTau] = tau;
+            red_add(reinterpret_cast<long long *>(&pst()[kPsSumTau]), tau);
+            red_max(&pst()[kPsMaxTau], tau);
         }
         finish_rep(true, C);
         S += C;
         N += 1;
-        ++pst()[kPsRetained];
-        if (S > B) ++pst()[kPsZero];           // only a slot's first replication can end beyond B
+        red_add(reinterpret_cast<long long *>(&pst()[kPsRetained]), 1);
+        if (S > B) red_add(reinterpret_cast<long long *>(&pst()[kPsZero]), 1);   // only a slot's first replication ends beyond B
         if (S < B && B - S >= unit) { ++r; start_rep(); }
         else end_slot(true);
     };
 
     auto abort_rep = [&]() {                  // doomed: S_p(r) would exceed B; discard it
-        pst()[kPsProgress] += t;
-        ++pst()[kPsAborted];
+        red_add(reinterpret_cast<long long *>(&pst()[kPsProgress]), t);
+        red_add(reinterpret_cast<long long *>(&pst()[kPsAborted]), 1);
         finish_rep(false, 0);
         end_slot(true);
     };
 
     auto limit_hit = [&]() {
-        pst()[kPsProgress] += t;
-        ++pst()[kPsLimit];
+        red_add(reinterpret_cast<long long *>(&pst()[kPsProgress]), t);
+        red_add(reinterpret_cast<long long *>(&pst()[kPsLimit]), 1);
         atomicExch(BATCH ? bp.error : p.error, 1);
         finish_rep(false, 0);
         end_slot(false);
@@ -629,7 +627,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
                                  kZeroCompletion, kStepLimitHits, kSumTau, kMaxTau};
 #pragma unroll
     for (int i = 0; i < kPairStats; ++i) {
-        unsigned long long v = pst()[i];
+        unsigned long long v = __ldcg(&pst()[i]);
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long u = __shfl_down_sync(0xFFFFFFFFu, v, o);
             v = i == kPsMaxTau ? max(v, u) : v + u;
