@@ -32,6 +32,11 @@ UNIT = "site-updates/s"
 SLOTS = 524288
 BUDGET = 4e10
 SEED = 20260
+# DRAM bytes (read + written) per coupled draw of the sampling kernel on this workload, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 87,552-slot case of this
+# configuration (3.294e9 draws, 8.866 GB), scaled to a launch by its draws.  Taken for the current
+# kernel revision; it is the accumulator events and flushes, not a per-step stream.
+DRAM_BYTES_PER_DRAW = 2.6915
 
 
 def workload_config(extra=None):
@@ -339,7 +344,10 @@ def main():
         e2e_times.append(time.perf_counter() - t0)
         assert out["status"] == 0
     na = plan.n_active
-    h2d = na * 8 + na * 16 + 81 * 8                  # alias words, clone rows, thresholds
+    degs = np.diff(inst.clone_ptr)
+    uniform_deg = int(degs[0]) if degs.min() == degs.max() else 0
+    n_thresholds = 7 * 64 if 3 <= uniform_deg <= 6 else 81   # mask-indexed for uniform degrees 3..6
+    h2d = na * 8 + na * 16 + n_thresholds * 8        # alias words, clone rows, thresholds
     d2h = 2 * na * 8 + 16 * 8 + 4                    # estimates, standard errors, counters, flag
     e2e_val = su_step * world / statistics.mean(e2e_times)
 
@@ -351,7 +359,8 @@ def main():
     ops = algorithmic_ops_per_progress_unit(6) * pu_step
     achieved = ops / (kernel_ms / 1000.0)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
-                "unit": "Tops/s", "frac": achieved / peak_ops, "traffic": None,
+                "unit": "Tops/s", "frac": achieved / peak_ops,
+                "traffic": DRAM_BYTES_PER_DRAW * pu_step, "traffic_unit": "bytes per launch",
                 "note": f"issue-slot peak = 128 lane-ops/clk/SM x {sm_count} SMs x {max_mhz:.0f} MHz "
                         f"({peak_kind} max clock); algorithmic ops = "
                         f"{algorithmic_ops_per_progress_unit(6):.0f} per coupled draw"}
