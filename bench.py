@@ -150,8 +150,9 @@ def cpu_oracle_sample(seconds: float, steps_label: str = ""):
 def batched_leg(ctx, device, slots_per_instance=1024, count=512, sweeps=20, seed=11, limit_sweeps=100):
     """The uneven batch: `count` instances with n ~ U[200, 5000], m = round(n / 13), k ~ U{4..8},
     1-6 positives, fp ~ U[.005, .1], fn ~ U[.02, .25], q = positives / n; each with its own slots
-    and a horizon of `sweeps` sweeps; one persistent launch, launch shape (lanes per pair, warps per
-    block) chosen by the autotuner (cached per GPU and shape).  A pair that has not met after
+    and a horizon of `sweeps` sweeps; one persistent launch per size class (automatic classes),
+    launch shape (lanes per pair, warps per block) chosen by the autotuner (cached per GPU and
+    shape).  A pair that has not met after
     `limit_sweeps` sweeps is stopped (its slot is left out and counted): some low-noise instances
     have meeting times far beyond what a timed step can wait for."""
     import torch

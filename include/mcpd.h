@@ -172,23 +172,28 @@ int mcpd_inspect(const mcpd_design *design, const uint8_t *y, const mcpd_params 
  * offsets[i] .. offsets[i+1]-1 of est / se (its retained clones, ascending original index). */
 typedef struct mcpd_batch mcpd_batch;
 
-/* Build the batch.  designs, ys, params: [n_inst] host arrays (borrowed).  order_mode 0 keeps the
- * instances in input order in the work list; 1 puts the instances with the longest slots (largest
- * horizon) first. */
+/* Build the batch.  designs, ys, params: [n_inst] host arrays (borrowed).  order_mode bits 0-7:
+ * 0 keeps the instances in input order in the work list, 1 puts the instances with the longest
+ * slots (largest horizon) first.  Bits 8-15: size classes, 0 for automatic, else 1..8.  The
+ * instances are sorted by pair state (largest first) and cut into classes of about equal work
+ * (slots x slot length); each class is its own launch of the sampling kernel, with a launch shape
+ * fitted to its largest pair state.  Automatic gives as many classes as the total slots fill
+ * whole launches (at most four).  Results do not depend on the order or the classes. */
 int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
                       const uint8_t *const *ys, const mcpd_params *params, int32_t order_mode,
                       mcpd_batch **out);
 void mcpd_batch_destroy(mcpd_batch *batch);
 /* info[0] total retained clones, [1] instances, [2] total slots, [3] largest n_active,
- * [4] warps per block, [5] blocks, [6] resident pairs, [7] shared-memory bytes per block,
- * [8] lanes per pair. */
+ * [4] warps per block, [5] blocks and [7] shared-memory bytes per block of the first class (the
+ * largest pair state), [6] resident pairs of the widest class, [8] lanes per pair, [9] size
+ * classes, [10] largest warps per block over the classes. */
 int mcpd_batch_info(const mcpd_batch *batch, int64_t info[16]);
 /* offsets: [n_inst + 1] host array receiving each instance's first output index. */
 int mcpd_batch_offsets(const mcpd_batch *batch, int64_t *offsets);
-/* Choose the launch shape: lanes per pair (1: one thread per pair; 8, 16 or 32: a lane group per
- * pair, coupled batches only; all give identical results) and warps per block (0: as many as the
- * kernel and the largest instance's pair state allow).  May reallocate the per-pair scratch;
- * invalidates a captured graph. */
+/* Choose the launch shape of every class: lanes per pair (1: one thread per pair; 8, 16 or 32: a
+ * lane group per pair, coupled batches only; all give identical results) and at most
+ * warps_per_block warps per block (0: as many as the kernel and the class's largest pair state
+ * allow).  May reallocate the per-pair scratch; invalidates a captured graph. */
 int mcpd_batch_set_shape(mcpd_ctx *ctx, mcpd_batch *batch, int32_t lanes_per_pair,
                          int32_t warps_per_block);
 /* Enqueue one decode of every instance; est_dev, se_dev: device arrays [info[0]]. */

@@ -2,7 +2,9 @@
 
 The tuner itself is native (mcpd_batch_autotune times candidate launch shapes on the batch);
 this module remembers its choice (lanes per pair, warps per block) in a JSON cache keyed by GPU name and a coarse shape bucket
-(instance count, largest n_active, total slots, coupled), so a batch of the same shape reuses it.
+(instance count, largest n_active, total slots, size classes), so a batch of the same shape reuses
+it.  Warps per block are an upper bound per size class: 0 lets every class take all that fit
+(the 20-warp kernel variant where more than 12 fit), 12 keeps every class on the 12-warp variant.
 """
 from __future__ import annotations
 
@@ -18,7 +20,7 @@ CACHE = os.path.join(BUILD, "autotune_cache.json")
 def shape_key(gpu_name: str, batch) -> str:
     info = batch.info
     b = lambda v: 2 ** int(math.ceil(math.log2(max(1, int(v)))))   # noqa: E731
-    return f"{gpu_name}|inst{b(info[1])}|na{b(info[3])}|slots{b(info[2])}"
+    return f"{gpu_name}|inst{b(info[1])}|na{b(info[3])}|slots{b(info[2])}|cls{int(info[9])}"
 
 
 def load():
@@ -29,7 +31,7 @@ def load():
         return {}
 
 
-DEFAULT_CANDIDATES = ((1, 0), (1, 6), (8, 0), (8, 12), (16, 0), (32, 0))
+DEFAULT_CANDIDATES = ((1, 0), (1, 12), (1, 6), (8, 0), (8, 12), (16, 0), (32, 0))
 
 
 def tuned_shape(batch, est_dev, se_dev, gpu_name: str, candidates=DEFAULT_CANDIDATES, reps=1,

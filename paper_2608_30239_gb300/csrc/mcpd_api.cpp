@@ -356,30 +356,41 @@ int mcpd_philox_device(mcpd_ctx *ctx, const uint32_t *ctr_dev, uint32_t key0, ui
 // ------------------------------------------------------------------------------------------
 // Batched decoding: many instances of uneven size in one persistent launch.
 
+// One size class of a batch: instances with similar pair state, launched together so that the
+// launch shape (warps per block) fits their columns rather than the largest instance's.
+struct BatchClass {
+    int32_t first = 0, count = 0;      // positions [first, first + count) of the launch order
+    mcpd::BParams bp{};                // this class's launch arguments (insts = d_insts + first)
+    int grid = 0, block = 0, warps = 0;
+    size_t smem = 0;
+    long long pairs = 0, scratch_pairs = 0;
+    std::vector<void *> scratch;       // per-pair scratch (resized by the tuner)
+};
+
 struct mcpd_batch {
     mcpd_ctx *ctx = nullptr;
     std::vector<mcpd::Tables> t;
-    std::vector<int32_t> order;            // launch order of instances (instance-major work list)
+    std::vector<int32_t> order;            // launch order of instances (class-major, then instance-major)
     std::vector<int64_t> out_offset;       // [n + 1] offsets of each instance's clones in est/se
     std::vector<int64_t> bucket_offset;    // [n] offsets of each instance's buckets (in nb*na units)
     std::vector<int64_t> count_offset;     // [n]
-    mcpd::BParams bp{};
+    std::vector<BatchClass> cls;
+    int32_t n_inst = 0, lanes = 1;
+    bool coupled = true;
     mcpd::InstDesc *d_insts = nullptr;
     std::vector<mcpd::InstDesc> insts;     // in launch order
     int32_t *d_clone_inst = nullptr, *d_clone_local = nullptr;
     unsigned long long *d_buckets = nullptr;   // S1 | S2lo | S2hi, each total_bucket_words
     unsigned long long *d_bcount = nullptr;
+    unsigned long long *d_counters = nullptr;  // [classes][kNumCounters]
+    int *d_error = nullptr;
     size_t total_bucket_words = 0, total_counts = 0;
     int64_t total_active = 0, total_slots = 0;
-    int grid = 0, block = 0, warps = 0;
-    size_t smem = 0;
-    long long pairs = 0, scratch_pairs = 0;
     bool dirty = true, ran = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<void *> allocs;            // tables, descriptors, buckets (fixed)
-    std::vector<void *> scratch;           // per-pair accumulators (resized by the tuner)
 };
 
 namespace {
@@ -400,51 +411,60 @@ void free_list(std::vector<void *> &list) {
     list.clear();
 }
 
-// Launch shape: `lanes` per pair (1: one thread per pair; 8, 16, 32: a lane group per pair) and
-// `warps` per block (0: as many as fit), and the per-pair scratch it needs.
+// Launch shape of every class: `lanes` per pair (1: one thread per pair; 8, 16, 32: a lane group
+// per pair) and at most `warps` per block (0: as many as fit the class's largest pair state),
+// and the per-pair scratch it needs.
 int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
     if (lanes != 1 && lanes != 8 && lanes != 16 && lanes != 32)
         return set_err(ctx, MCPD_EINVAL, "lanes per pair must be 1, 8, 16 or 32");
-    if (lanes > 1 && !b->bp.coupled) return set_err(ctx, MCPD_EINVAL, "lane groups run coupled batches only");
-    int per_sm = 1;
-    if (lanes == 1) {
-        mcpd::PairsShape shape;
-        const int rc = mcpd::pairs_shape(b->bp.coupled, b->bp.scan, 0, true, 0, b->bp.max_wpp, ctx->smem_optin, 0,
-                                         ctx->sm_count, warps, &shape);
-        if (rc == MCPD_ETOO_LARGE) return set_err(ctx, rc, "largest instance does not fit one warp of pair state");
-        if (rc == MCPD_EINVAL) return set_err(ctx, rc, "warps per block above what the kernel allows");
-        if (rc != MCPD_OK) return set_err(ctx, rc, "cudaFuncSetAttribute / occupancy");
-        warps = shape.warps;
-        b->smem = shape.smem;
-        b->bp.y_regions = shape.y_regions;
-        per_sm = shape.per_sm;
-    } else {
-        const size_t per_warp = static_cast<size_t>(32 / lanes) * 2 * b->bp.max_wpp * 4;
-        const int cap = mcpd::group_max_threads(lanes) / 32;
-        const int fit = static_cast<int>(std::min<size_t>(cap, ctx->smem_optin / per_warp));
-        if (fit < 1) return set_err(ctx, MCPD_ETOO_LARGE, "largest instance does not fit one warp of pair state");
-        if (warps <= 0) warps = fit;
-        if (warps > fit) return set_err(ctx, MCPD_EINVAL, "warps per block above what the kernel allows");
-        b->smem = per_warp * warps;
-        b->bp.y_regions = 0;
-        if (mcpd::set_group_smem(lanes, b->smem) != MCPD_OK) return set_err(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
-        if (mcpd::group_occupancy(lanes, warps * 32, b->smem, &per_sm) != MCPD_OK || per_sm < 1) per_sm = 1;
+    if (lanes > 1 && !b->coupled) return set_err(ctx, MCPD_EINVAL, "lane groups run coupled batches only");
+    for (BatchClass &c : b->cls) {
+        int per_sm = 1, w = 0;
+        if (lanes == 1) {
+            mcpd::PairsShape shape;
+            int rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, 0, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
+                                       ctx->sm_count, 0, &shape);
+            if (rc == MCPD_ETOO_LARGE) return set_err(ctx, rc, "largest instance does not fit one warp of pair state");
+            if (rc != MCPD_OK) return set_err(ctx, rc, "cudaFuncSetAttribute / occupancy");
+            if (warps > 0 && warps < shape.warps) {
+                rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, 0, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
+                                       ctx->sm_count, warps, &shape);
+                if (rc != MCPD_OK) return set_err(ctx, rc, "launch shape");
+            }
+            w = shape.warps;
+            c.smem = shape.smem;
+            c.bp.y_regions = shape.y_regions;
+            c.bp.wide = shape.wide ? 1 : 0;
+            per_sm = shape.per_sm;
+        } else {
+            const size_t per_warp = static_cast<size_t>(32 / lanes) * 2 * c.bp.max_wpp * 4;
+            const int cap = mcpd::group_max_threads(lanes) / 32;
+            const int fit = static_cast<int>(std::min<size_t>(cap, ctx->smem_optin / per_warp));
+            if (fit < 1) return set_err(ctx, MCPD_ETOO_LARGE, "largest instance does not fit one warp of pair state");
+            w = warps > 0 ? std::min(warps, fit) : fit;
+            c.smem = per_warp * w;
+            c.bp.y_regions = 0;
+            // a permission shared by the launches of all classes: the device's opt-in maximum
+            if (mcpd::set_group_smem(lanes, ctx->smem_optin) != MCPD_OK) return set_err(ctx, MCPD_ECUDA, "cudaFuncSetAttribute");
+            if (mcpd::group_occupancy(lanes, w * 32, c.smem, &per_sm) != MCPD_OK || per_sm < 1) per_sm = 1;
+        }
+        c.warps = w;
+        c.block = w * 32;
+        c.bp.lanes = lanes;
+        c.grid = ctx->sm_count * per_sm;
+        c.pairs = static_cast<long long>(c.grid) * c.block / lanes;
+        if (c.pairs > c.scratch_pairs) {
+            free_list(c.scratch);
+            int rc;
+            if ((rc = balloc(ctx, c.scratch, &c.bp.pair_scratch,
+                             static_cast<size_t>(c.pairs) * mcpd::pair_words(c.bp.max_na, c.bp.max_W))) != MCPD_OK)
+                return rc;
+            if ((rc = balloc(ctx, c.scratch, &c.bp.y_state, static_cast<size_t>(c.pairs) * c.bp.max_wpp)) != MCPD_OK) return rc;
+            c.scratch_pairs = c.pairs;
+            b->dirty = true;
+        }
     }
-    b->warps = warps;
-    b->block = warps * 32;
-    b->bp.lanes = lanes;
-    b->grid = ctx->sm_count * per_sm;
-    b->pairs = static_cast<long long>(b->grid) * b->block / lanes;
-    if (b->pairs > b->scratch_pairs) {
-        free_list(b->scratch);
-        int rc;
-        if ((rc = balloc(ctx, b->scratch, &b->bp.pair_scratch,
-                         static_cast<size_t>(b->pairs) * mcpd::pair_words(b->bp.max_na, b->bp.max_W))) != MCPD_OK)
-            return rc;
-        if ((rc = balloc(ctx, b->scratch, &b->bp.y_state, static_cast<size_t>(b->pairs) * b->bp.max_wpp)) != MCPD_OK) return rc;
-        b->scratch_pairs = b->pairs;
-        b->dirty = true;
-    }
+    b->lanes = lanes;
     if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     return MCPD_OK;
@@ -454,17 +474,19 @@ int batch_enqueue(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev,
     const cudaStream_t s = ctx->stream;
     CU(cudaMemsetAsync(b->d_buckets, 0, b->total_bucket_words * 3 * 8, s));
     CU(cudaMemsetAsync(b->d_bcount, 0, b->total_counts * 8, s));
-    CU(cudaMemsetAsync(b->bp.counters, 0, mcpd::kNumCounters * 8, s));
-    CU(cudaMemsetAsync(b->bp.error, 0, sizeof(int), s));
-    if (b->dirty || always_clear) {
-        CU(cudaMemsetAsync(b->bp.pair_scratch, 0,
-                           static_cast<size_t>(b->pairs) * mcpd::pair_words(b->bp.max_na, b->bp.max_W) * 8, s));
-        CU(cudaMemsetAsync(b->bp.y_state, 0, static_cast<size_t>(b->pairs) * b->bp.max_wpp * 4, s));
+    CU(cudaMemsetAsync(b->d_counters, 0, b->cls.size() * mcpd::kNumCounters * 8, s));
+    CU(cudaMemsetAsync(b->d_error, 0, sizeof(int), s));
+    for (BatchClass &c : b->cls) {
+        if (b->dirty || always_clear) {
+            CU(cudaMemsetAsync(c.bp.pair_scratch, 0,
+                               static_cast<size_t>(c.pairs) * mcpd::pair_words(c.bp.max_na, c.bp.max_W) * 8, s));
+            CU(cudaMemsetAsync(c.bp.y_state, 0, static_cast<size_t>(c.pairs) * c.bp.max_wpp * 4, s));
+        }
+        if ((c.bp.lanes == 1 ? mcpd::launch_batch(c.bp, c.grid, c.block, c.smem, s)
+                             : mcpd::launch_group(c.bp, c.grid, c.block, c.smem, s)) != MCPD_OK)
+            return set_err(ctx, MCPD_ECUDA, std::string("batch kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
     }
-    if ((b->bp.lanes == 1 ? mcpd::launch_batch(b->bp, b->grid, b->block, b->smem, s)
-                          : mcpd::launch_group(b->bp, b->grid, b->block, b->smem, s)) != MCPD_OK)
-        return set_err(ctx, MCPD_ECUDA, std::string("batch kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
-    if (mcpd::launch_finalize_batch(b->d_insts, b->bp.n_inst, b->d_clone_inst, b->d_clone_local,
+    if (mcpd::launch_finalize_batch(b->d_insts, b->n_inst, b->d_clone_inst, b->d_clone_local,
                                     b->total_active, est_dev, se_dev, s) != MCPD_OK)
         return set_err(ctx, MCPD_ECUDA, "batch finalize launch");
     return MCPD_OK;
@@ -480,7 +502,7 @@ void mcpd_batch_destroy(mcpd_batch *b) {
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     free_list(b->allocs);
-    free_list(b->scratch);
+    for (BatchClass &c : b->cls) free_list(c.scratch);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;
@@ -490,10 +512,13 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
                       const uint8_t *const *ys, const mcpd_params *params, int32_t order_mode,
                       mcpd_batch **out) {
     if (!ctx || !out || n_inst < 1 || !designs || !ys || !params) return MCPD_EINVAL;
+    const int32_t mode = order_mode & 0xFF, want_classes = (order_mode >> 8) & 0xFF;
+    if (mode > 1 || want_classes > 8 || (order_mode >> 16) != 0) return set_err(ctx, MCPD_EINVAL, "order_mode: order 0 or 1, classes 0..8");
     *out = nullptr;
     mcpd_batch *b = new (std::nothrow) mcpd_batch();
     if (!b) return set_err(ctx, MCPD_ENOMEM, "host allocation");
     b->ctx = ctx;
+    b->n_inst = n_inst;
     b->t.resize(n_inst);
     for (int32_t i = 0; i < n_inst; ++i) {
         std::string err;
@@ -508,17 +533,58 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
             return set_err(ctx, MCPD_EINVAL, "batches keep no per-slot records or traces");
         }
     }
-    // Launch order: 0 = as given; 1 = costliest slots (horizon) first, so long slots start early.
+    b->coupled = b->t[0].coupled;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) { mcpd_batch_destroy(b); return set_err(ctx, MCPD_ECUDA, "cudaSetDevice"); }
+
+    // Size classes: instances by pair state (words per column), largest first, cut into classes
+    // of about equal work (slots x slot length), as many as whole rounds of a full launch allow
+    // (at most four) unless the caller fixed the number.
+    std::vector<int32_t> by_size(n_inst);
+    for (int32_t i = 0; i < n_inst; ++i) by_size[i] = i;
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t c) { return b->t[a].wpp > b->t[c].wpp; });
+    auto work_of = [&](int32_t i) { return static_cast<double>(b->t[i].P) * static_cast<double>(std::max(b->t[i].B, b->t[i].unit)); };
+    int64_t total_slots = 0;
+    double total_work = 0.0;
+    for (int32_t i = 0; i < n_inst; ++i) { total_slots += b->t[i].P; total_work += work_of(i); }
+    int n_cls = want_classes;
+    if (n_cls == 0) {
+        const int64_t round = static_cast<int64_t>(ctx->sm_count) * 32 * 20;
+        n_cls = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(4, total_slots / std::max<int64_t>(1, round))));
+    }
+    n_cls = std::min(n_cls, n_inst);
+    std::vector<int32_t> cls_of(n_inst, 0);
+    {
+        double acc = 0.0;
+        for (int32_t pos = 0; pos < n_inst; ++pos) {
+            const int32_t i = by_size[pos];
+            int c = static_cast<int>(acc / total_work * n_cls);
+            c = std::min(c, n_cls - 1);
+            // every class keeps at least one instance
+            c = std::max(c, n_cls - (n_inst - pos));
+            c = std::min(c, pos);
+            cls_of[i] = c;
+            acc += work_of(i);
+        }
+        // number the classes that received instances 0, 1, ... (a heavy instance may skip one)
+        int next = 0, last = -1;
+        for (int32_t pos = 0; pos < n_inst; ++pos) {
+            const int32_t i = by_size[pos];
+            if (cls_of[i] != last) { last = cls_of[i]; ++next; }
+            cls_of[i] = next - 1;
+        }
+    }
+    // Launch order: class by class; within a class, 0 = input order, 1 = longest slots first.
     b->order.resize(n_inst);
     for (int32_t i = 0; i < n_inst; ++i) b->order[i] = i;
-    if (order_mode == 1)
-        std::stable_sort(b->order.begin(), b->order.end(), [&](int32_t a, int32_t c) {
-            return std::max(b->t[a].B, b->t[a].unit) > std::max(b->t[c].B, b->t[c].unit);
-        });
-    if (cudaSetDevice(ctx->device) != cudaSuccess) { mcpd_batch_destroy(b); return set_err(ctx, MCPD_ECUDA, "cudaSetDevice"); }
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int32_t a, int32_t c) {
+        if (cls_of[a] != cls_of[c]) return cls_of[a] < cls_of[c];
+        if (mode == 1) return std::max(b->t[a].B, b->t[a].unit) > std::max(b->t[c].B, b->t[c].unit);
+        return false;
+    });
+    n_cls = cls_of[b->order[n_inst - 1]] + 1;
+
     // Sizes.
     size_t table_bytes = 0;
-    int32_t max_na = 0, max_W = 0, max_wpp = 0, max_m = 0;
     b->out_offset.assign(n_inst + 1, 0);
     b->bucket_offset.assign(n_inst, 0);
     b->count_offset.assign(n_inst, 0);
@@ -527,8 +593,6 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         const mcpd::Tables &t = b->t[i];
         table_bytes += up16(t.alias.size() * 8) + up16(t.rows.size() * 2) + up16(t.T.size() * 8) + up16(t.Tnu.size() * 8) +
                        up16(t.init_pairs.size() * 4) + up16(t.rows_pool.size() * 2);
-        max_na = std::max(max_na, t.na); max_W = std::max(max_W, t.W); max_wpp = std::max(max_wpp, t.wpp);
-        max_m = std::max(max_m, t.m);
         b->out_offset[i + 1] = b->out_offset[i] + t.na;
         b->bucket_offset[i] = static_cast<int64_t>(b->total_bucket_words);
         b->total_bucket_words += static_cast<size_t>(t.nb) * t.na;
@@ -545,17 +609,22 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     BALLOC(b->d_insts, static_cast<size_t>(n_inst));
     BALLOC(b->d_clone_inst, static_cast<size_t>(b->total_active));
     BALLOC(b->d_clone_local, static_cast<size_t>(b->total_active));
-    BALLOC(b->bp.counters, static_cast<size_t>(mcpd::kNumCounters));
-    BALLOC(b->bp.error, 1);
+    BALLOC(b->d_counters, static_cast<size_t>(n_cls) * mcpd::kNumCounters);
+    BALLOC(b->d_error, 1);
 #undef BALLOC
-    // Tables (host staging buffer, one copy) and descriptors in launch order.
+    // Tables (host staging buffer, one copy) and descriptors in launch order; each class's work
+    // items are numbered from 0.
     std::vector<unsigned char> host(table_bytes, 0);
     size_t off = 0;
     b->insts.resize(n_inst);
+    b->cls.assign(n_cls, BatchClass());
     long long work = 0;
     for (int32_t pos = 0; pos < n_inst; ++pos) {
         const int32_t i = b->order[pos];
         const mcpd::Tables &t = b->t[i];
+        BatchClass &c = b->cls[cls_of[i]];
+        if (c.count == 0) { c.first = pos; work = 0; }
+        ++c.count;
         mcpd::InstDesc &d = b->insts[pos];
         std::memset(&d, 0, sizeof(d));
         auto put = [&](const void *src, size_t bytes) -> const void * {
@@ -582,24 +651,31 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         d.unit = t.unit; d.step_limit = t.step_limit; d.slot_offset = t.slot_offset;
         d.work_begin = work; work += t.P;
         d.seed = t.seed; d.instance = t.instance;
+        mcpd::BParams &bp = c.bp;
+        bp.total_work = work;
+        bp.max_na = std::max(bp.max_na, t.na); bp.max_W = std::max(bp.max_W, t.W);
+        bp.max_wpp = std::max(bp.max_wpp, t.wpp); bp.max_m = std::max(bp.max_m, t.m);
     }
-    b->total_slots = work;
+    b->total_slots = total_slots;
+    for (int c = 0; c < n_cls; ++c) {
+        mcpd::BParams &bp = b->cls[c].bp;
+        bp.insts = b->d_insts + b->cls[c].first;
+        bp.n_inst = b->cls[c].count;
+        bp.coupled = b->coupled ? 1 : 0;
+        bp.scan = b->t[0].scan;
+        bp.lanes = 1;
+        bp.counters = b->d_counters + static_cast<size_t>(c) * mcpd::kNumCounters;
+        bp.error = b->d_error;
+    }
     std::vector<int32_t> ci(b->total_active), cl(b->total_active);
-    for (int32_t i = 0; i < n_inst; ++i) {
-        int32_t pos = static_cast<int32_t>(std::find(b->order.begin(), b->order.end(), i) - b->order.begin());
+    for (int32_t pos = 0; pos < n_inst; ++pos) {
+        const int32_t i = b->order[pos];
         for (int32_t a = 0; a < b->t[i].na; ++a) { ci[b->out_offset[i] + a] = pos; cl[b->out_offset[i] + a] = a; }
     }
     CU(cudaMemcpyAsync(d_tables, host.data(), table_bytes, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(b->d_insts, b->insts.data(), sizeof(mcpd::InstDesc) * n_inst, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(b->d_clone_inst, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaMemcpyAsync(b->d_clone_local, cl.data(), cl.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-    b->bp.insts = b->d_insts;
-    b->bp.n_inst = n_inst;
-    b->bp.coupled = b->t[0].coupled ? 1 : 0;
-    b->bp.scan = b->t[0].scan;
-    b->bp.max_wpp = max_wpp; b->bp.max_na = max_na; b->bp.max_W = max_W; b->bp.max_m = max_m;
-    b->bp.lanes = 1;
-    b->bp.total_work = work;
     if ((rc = batch_shape(ctx, b, 0)) != MCPD_OK) { mcpd_batch_destroy(b); return rc; }
     CU(cudaEventCreate(&b->ev0));
     CU(cudaEventCreate(&b->ev1));
@@ -611,9 +687,17 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
 int mcpd_batch_info(const mcpd_batch *b, int64_t info[16]) {
     if (!b || !info) return MCPD_EINVAL;
     std::memset(info, 0, 16 * sizeof(int64_t));
-    info[0] = b->total_active; info[1] = b->bp.n_inst; info[2] = b->total_slots; info[3] = b->bp.max_na;
-    info[4] = b->warps; info[5] = b->grid; info[6] = b->pairs; info[7] = static_cast<int64_t>(b->smem);
-    info[8] = b->bp.lanes;
+    int32_t max_na = 0;
+    int64_t pairs = 0, wmax = 0;
+    for (const BatchClass &c : b->cls) {
+        max_na = std::max(max_na, c.bp.max_na);
+        pairs = std::max<int64_t>(pairs, c.pairs);
+        wmax = std::max<int64_t>(wmax, c.warps);
+    }
+    const BatchClass &c0 = b->cls[0];
+    info[0] = b->total_active; info[1] = b->n_inst; info[2] = b->total_slots; info[3] = max_na;
+    info[4] = c0.warps; info[5] = c0.grid; info[6] = pairs; info[7] = static_cast<int64_t>(c0.smem);
+    info[8] = b->lanes; info[9] = static_cast<int64_t>(b->cls.size()); info[10] = wmax;
     return MCPD_OK;
 }
 
@@ -673,11 +757,17 @@ int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *b, mcpd_stats *stats) {
     if (!ctx || !b) return MCPD_EINVAL;
     if (!b->ran) return set_err(ctx, MCPD_EINVAL, "no run to collect");
     CU(cudaSetDevice(ctx->device));
-    unsigned long long c[mcpd::kNumCounters];
+    std::vector<unsigned long long> cc(b->cls.size() * mcpd::kNumCounters);
     int error = 0;
-    CU(cudaMemcpyAsync(c, b->bp.counters, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
-    CU(cudaMemcpyAsync(&error, b->bp.error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(cc.data(), b->d_counters, cc.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaMemcpyAsync(&error, b->d_error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    unsigned long long c[mcpd::kNumCounters] = {};
+    for (size_t k = 0; k < b->cls.size(); ++k)
+        for (int i = 0; i < mcpd::kNumCounters; ++i) {
+            const unsigned long long v = cc[k * mcpd::kNumCounters + i];
+            c[i] = i == mcpd::kMaxTau ? std::max(c[i], v) : c[i] + v;
+        }
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
     if (stats) {
@@ -690,7 +780,7 @@ int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *b, mcpd_stats *stats) {
         stats->step_limit_hits = static_cast<int64_t>(c[mcpd::kStepLimitHits]);
         stats->max_tau = static_cast<int64_t>(c[mcpd::kMaxTau]);
         stats->sum_tau = static_cast<int64_t>(c[mcpd::kSumTau]);
-        stats->site_updates = b->bp.coupled ? 2 * stats->progress_units - stats->reps_started : stats->progress_units;
+        stats->site_updates = b->coupled ? 2 * stats->progress_units - stats->reps_started : stats->progress_units;
         stats->n_buckets = static_cast<int64_t>(b->total_counts);
         stats->n_active = b->total_active;
         stats->kernel_ms = ms;
@@ -702,7 +792,7 @@ int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *b, mcpd_stats *stats) {
 
 int mcpd_batch_fetch(mcpd_ctx *ctx, const mcpd_batch *b, int32_t inst, int what, void *host_dst,
                      size_t bytes) {
-    if (!ctx || !b || !host_dst || inst < 0 || inst >= b->bp.n_inst) return MCPD_EINVAL;
+    if (!ctx || !b || !host_dst || inst < 0 || inst >= b->n_inst) return MCPD_EINVAL;
     const mcpd::Tables &t = b->t[inst];
     const size_t words = static_cast<size_t>(t.nb) * t.na;
     const unsigned long long *src = nullptr;

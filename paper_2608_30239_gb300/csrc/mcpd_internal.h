@@ -166,13 +166,15 @@ struct BParams {
     unsigned long long *counters;
     int *error;
     int32_t max_na, max_W;
-    int32_t y_regions, pad2;          // 32-column Y regions in shared memory
+    int32_t y_regions;                // 32-column Y regions in shared memory
+    int32_t wide;                     // launch the 20-warp variant of the batch kernel
 };
 
 // Launch shape of the one-thread-per-pair kernel (mcpd_kernels.cu).
 struct PairsShape {
     int warps = 0;                    // warps per block
     int y_regions = 0;                // 32-column Y regions per block
+    bool wide = false;                // (batches) the 20-warp variant of the kernel
     int per_sm = 1;                   // resident blocks per SM
     size_t smem = 0;                  // dynamic shared memory per block
 };
@@ -189,7 +191,7 @@ int launch_group(const BParams &bp, int grid, int block, size_t smem, void *stre
 int set_group_smem(int lanes, size_t bytes);
 int group_max_threads(int lanes);
 int group_occupancy(int lanes, int block, size_t smem, int *blocks_per_sm);
-int pairs_max_threads(int coupled, int scan, int udeg, bool batch);
+int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide = false);
 int launch_finalize_batch(const InstDesc *insts, int n_inst, const int32_t *clone_inst,
                           const int32_t *clone_local, long long total_clones, double *est,
                           double *se, void *stream);

@@ -47,8 +47,10 @@ namespace {
 // some region first, so that it shares no bank with its warp's other lanes), else in its own
 // column of the global fallback (same layout, one region per warp).  A free Y column is all zero
 // except, for DEG = 0, the padding pool's count.
-template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG>
-__global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs_kernel(const KParams p, const BParams bp) {
+// WIDE (batches only): compiled for 20 warps per block (96 registers) rather than 12 (up to 168),
+// for size classes whose pair state leaves room for more than 12 warps.
+template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG, bool WIDE = false>
+__global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 : 512), 1) pairs_kernel(const KParams p, const BParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     uint4 *sRows = reinterpret_cast<uint4 *>(smem);
@@ -103,47 +105,64 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
 
     // Per-instance values (fixed for a single instance, reloaded when a batched slot changes
     // instance).
+    // Values the step uses live in registers; the others are read where needed, from the kernel
+    // parameters (one instance) or from the instance's descriptor (batch, read-only, cached).
     const uint4 *gRows = nullptr;
-    const unsigned long long *gAlias = nullptr, *gT = nullptr, *Tnu = nullptr;
-    const uint32_t *init_pairs = nullptr;
-    int n_init_pairs = 0;
-    unsigned long long *bS1 = nullptr, *bS2lo = nullptr, *bS2hi = nullptr, *bCount = nullptr;
-    int na = 0, deg = 0, dummy_word_index = 0;
-    uint32_t W = 0, B = 0, unit = 0, ell = 0, step_limit = 0, instance = 0, k0 = 0, k1 = 0;
-    uint32_t dummy_entry = 0, dummy_word = 0, gshift = 0, ws0 = 0, wcap = 0;
-    long long kk = 0, LL = 0, burn = 0, length = 0, P = 0, slot_offset = 0, work_begin = 0, work_end = 0;
+    const unsigned long long *gAlias = nullptr, *gT = nullptr;
+    int na = 0, deg = 0;
+    uint32_t W = 0, ell = 0, instance = 0, k0 = 0, k1 = 0;
+    uint32_t dummy_entry = 0, gshift = 0, ws0 = 0, wcap = 0;
     int cur = -1;
+    auto desc = [&]() -> const InstDesc * { return bp.insts + cur; };
+#define MCPD_FIELD(name, batch_expr, single_expr) \
+    auto name = [&]() { if constexpr (BATCH) return batch_expr; else return single_expr; }
+    MCPD_FIELD(v_B, static_cast<uint32_t>(__ldg(&desc()->B)), static_cast<uint32_t>(p.B));
+    MCPD_FIELD(v_unit, static_cast<uint32_t>(__ldg(&desc()->unit)), static_cast<uint32_t>(p.unit));
+    MCPD_FIELD(v_step_limit, static_cast<uint32_t>(__ldg(&desc()->step_limit)), static_cast<uint32_t>(p.step_limit));
+    MCPD_FIELD(v_k, __ldg(&desc()->k), p.k);
+    MCPD_FIELD(v_L, __ldg(&desc()->L), p.L);
+    MCPD_FIELD(v_burn, __ldg(&desc()->burn), p.burn);
+    MCPD_FIELD(v_length, __ldg(&desc()->length), p.length);
+    MCPD_FIELD(v_P, __ldg(&desc()->P), p.P);
+    MCPD_FIELD(v_slot_offset, __ldg(&desc()->slot_offset), p.slot_offset);
+    MCPD_FIELD(v_work_begin, __ldg(&desc()->work_begin), 0ll);
+    MCPD_FIELD(v_dwi, __ldg(&desc()->dummy_word_index), p.dummy_word_index);
+    MCPD_FIELD(v_dw, __ldg(&desc()->dummy_word), p.dummy_word);
+    MCPD_FIELD(v_n_init, __ldg(&desc()->n_init_pairs), p.n_init_pairs);
+    MCPD_FIELD(v_Tnu, reinterpret_cast<const unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->Tnu))),
+               reinterpret_cast<const unsigned long long *>(p.Tnu));
+    MCPD_FIELD(v_init_pairs, reinterpret_cast<const uint32_t *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->init_pairs))),
+               p.init_pairs);
+    MCPD_FIELD(v_S1, reinterpret_cast<unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->S1))), p.S1);
+    MCPD_FIELD(v_S2lo, reinterpret_cast<unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->S2lo))), p.S2lo);
+    MCPD_FIELD(v_S2hi, reinterpret_cast<unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->S2hi))), p.S2hi);
+    MCPD_FIELD(v_bcount, reinterpret_cast<unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->bcount))), p.bcount);
+#undef MCPD_FIELD
     auto clamp32 = [](long long v) -> uint32_t { return v < 0 ? 0u : (v > 0xFFFFFFFFll ? 0xFFFFFFFFu : static_cast<uint32_t>(v)); };
     auto derive = [&]() {
         gshift = 0;
         while (((W + (1u << gshift) - 1) >> gshift) > 32) ++gshift;
-        ws0 = clamp32(COUPLED ? kk : burn);
-        wcap = clamp32(COUPLED ? LL : length);
+        ws0 = clamp32(COUPLED ? v_k() : v_burn());
+        wcap = clamp32(COUPLED ? v_L() : v_length());
     };
-    auto load_instance = [&](const InstDesc &d) {
+    auto load_instance = [&](int c) {
+        cur = c;
+        const InstDesc &d = bp.insts[c];
         gRows = reinterpret_cast<const uint4 *>(d.rows); gAlias = reinterpret_cast<const unsigned long long *>(d.alias);
-        gT = reinterpret_cast<const unsigned long long *>(d.T); Tnu = reinterpret_cast<const unsigned long long *>(d.Tnu);
-        init_pairs = d.init_pairs; n_init_pairs = d.n_init_pairs;
-        bS1 = d.S1; bS2lo = d.S2lo; bS2hi = d.S2hi; bCount = d.bcount;
-        na = d.na; deg = d.deg; W = d.W; dummy_word_index = d.dummy_word_index;
-        dummy_entry = d.dummy_entry; dummy_word = d.dummy_word;
-        B = static_cast<uint32_t>(d.B); unit = static_cast<uint32_t>(d.unit); ell = static_cast<uint32_t>(d.ell);
-        step_limit = static_cast<uint32_t>(d.step_limit); instance = d.instance;
+        gT = reinterpret_cast<const unsigned long long *>(d.T);
+        na = d.na; deg = d.deg; W = d.W;
+        dummy_entry = d.dummy_entry;
+        ell = static_cast<uint32_t>(d.ell);
+        instance = d.instance;
         k0 = static_cast<uint32_t>(d.seed); k1 = static_cast<uint32_t>(d.seed >> 32);
-        kk = d.k; LL = d.L; burn = d.burn; length = d.length; P = d.P; slot_offset = d.slot_offset;
-        work_begin = d.work_begin; work_end = d.work_begin + d.P;
         derive();
     };
     if constexpr (!BATCH) {
-        Tnu = reinterpret_cast<const unsigned long long *>(p.Tnu);
-        init_pairs = p.init_pairs; n_init_pairs = p.n_init_pairs;
-        bS1 = p.S1; bS2lo = p.S2lo; bS2hi = p.S2hi; bCount = p.bcount;
-        na = p.na; deg = p.deg; W = p.W; dummy_word_index = p.dummy_word_index;
-        dummy_entry = p.dummy_entry; dummy_word = p.dummy_word;
-        B = static_cast<uint32_t>(p.B); unit = static_cast<uint32_t>(p.unit); ell = static_cast<uint32_t>(p.ell);
-        step_limit = static_cast<uint32_t>(p.step_limit); instance = p.instance;
+        na = p.na; deg = p.deg; W = p.W;
+        dummy_entry = p.dummy_entry;
+        ell = static_cast<uint32_t>(p.ell);
+        instance = p.instance;
         k0 = static_cast<uint32_t>(p.seed); k1 = static_cast<uint32_t>(p.seed >> 32);
-        kk = p.k; LL = p.L; burn = p.burn; length = p.length; P = p.P; slot_offset = p.slot_offset;
         derive();
     }
     constexpr int NE = DEG > 0 ? DEG : kRow;       // row entries visited per clone
@@ -171,11 +190,12 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
     // Prefix sums of the estimator's per-time weights (see the comment on wprefix).
     auto wpre = [&](long long u) -> long long {
         if (COUPLED) {
+            const long long kk = v_k(), LL = v_L();
             if (u < kk) return 0;
             if (u <= static_cast<long long>(ell)) { const long long a = u - kk + 1; return a * (a + 1) / 2; }
             return LL * (LL + 1) / 2 + (u - static_cast<long long>(ell)) * LL;
         } else {
-            const long long v = u - burn + 1;
+            const long long v = u - v_burn() + 1, length = v_length();
             return v < 0 ? 0 : (v > length ? length : v);
         }
     };
@@ -214,7 +234,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         }
         __threadfence_block();
         ycol = yslot >= 0 ? yreg + (yslot >> 5) * region_words + (yslot & 31) : yglob();
-        if (DEG == 0) ycol[dummy_word_index * 32] = dummy_word;
+        if (DEG == 0) ycol[v_dwi() * 32] = v_dw();
     };
     // Empty the Y column in use (every Y bit lies in a group marked in rep_words) and return it.
     auto release_y = [&]() {
@@ -231,7 +251,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
                 while (yw) { const int b = __ffs(yw) - 1; yw &= yw - 1; bump_counts(q * 32 + b, 0xFFu, yb); }
             }
         }
-        if (DEG == 0) ycol[dummy_word_index * 32] = 0u;
+        if (DEG == 0) ycol[v_dwi() * 32] = 0u;
         __threadfence_block();
         if (yslot >= 0) atomicOr(&ymask[yslot >> 5], 1u << (yslot & 31));
         yslot = -1;
@@ -257,12 +277,16 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
 
     auto start_rep = [&]() {
         t = 0; D = 0; tau = 1; sysI = 0;      // tau = 1 unless the pre-lag update moves X
-        abort_t = (COUPLED && r > 0) ? (B - S) : 0xFFFFFFFFu;
+        const uint32_t step_limit = v_step_limit();
+        abort_t = (COUPLED && r > 0) ? (v_B() - S) : 0xFFFFFFFFu;
         stop_unmet = min(abort_t, step_limit);
-        t_end = COUPLED ? min(max(ell, 1u), stop_unmet) : min(unit, step_limit);
+        t_end = COUPLED ? min(max(ell, 1u), stop_unmet) : min(v_unit(), step_limit);
         red_add(reinterpret_cast<long long *>(&pst()[kPsStarted]), 1);
         ++reps_in_slot;
+        const unsigned long long *Tnu = v_Tnu();
         if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0 (clones with nu_i = 0 stay 0)
+            const uint32_t *init_pairs = v_init_pairs();
+            const int n_init_pairs = v_n_init();
             for (int e = 0; e < n_init_pairs; ++e) {
                 const int a = static_cast<int>(init_pairs[e]);
                 const uint4 b = philox10(make_uint4(static_cast<uint32_t>(a) >> 1, r, slot_g,
@@ -289,23 +313,22 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         if constexpr (BATCH) {
             if (s >= static_cast<unsigned long long>(bp.total_work)) { alive = false; return; }
             const long long w = static_cast<long long>(s);
-            if (cur < 0 || w < work_begin || w >= work_end) {
+            if (cur < 0 || w < v_work_begin() || w >= v_work_begin() + v_P()) {
                 int lo = 0, hi = bp.n_inst - 1;             // last instance with work_begin <= w
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
                     if (bp.insts[mid].work_begin <= w) lo = mid; else hi = mid - 1;
                 }
-                if (cur >= 0) st[dummy_word_index * 32] = 0u;   // the old layout's padding pool
-                cur = lo;
-                load_instance(bp.insts[cur]);
-                st[dummy_word_index * 32] = dummy_word;
+                if (cur >= 0) st[v_dwi() * 32] = 0u;    // the old layout's padding pool
+                load_instance(lo);
+                st[v_dwi() * 32] = v_dw();
             }
-            slot_local = static_cast<uint32_t>(w - work_begin);
+            slot_local = static_cast<uint32_t>(w - v_work_begin());
         } else {
-            if (s >= static_cast<unsigned long long>(P)) { alive = false; return; }
+            if (s >= static_cast<unsigned long long>(v_P())) { alive = false; return; }
             slot_local = static_cast<uint32_t>(s);
         }
-        slot_g = static_cast<uint32_t>(slot_offset + static_cast<long long>(slot_local));
+        slot_g = static_cast<uint32_t>(v_slot_offset() + static_cast<long long>(slot_local));
         S = 0; N = 0; r = 0; reps_in_slot = 0;
         start_rep();
     };
@@ -373,7 +396,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
                     const long long gsum = __ldcg(&sacc()[j]);
                     sacc()[j] = 0;
                     if (valid && gsum != 0) {
-                        bucket_add(bS1, bS2lo, bS2hi, na, bkt, static_cast<int>(j), gsum);
+                        bucket_add(v_S1(), v_S2lo(), v_S2hi(), na, bkt, static_cast<int>(j), gsum);
                         if (tr) tr[j] = gsum;
                     }
                 }
@@ -381,7 +404,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             }
         }
         slot_words = 0;
-        if (valid) atomicAdd(&bCount[bkt], 1ull);
+        if (valid) atomicAdd(&v_bcount()[bkt], 1ull);
         if constexpr (!BATCH) {
             if (p.slot_nstar) {
                 p.slot_nstar[slot_local] = valid ? static_cast<int32_t>(N) : 0;
@@ -405,8 +428,9 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         S += C;
         N += 1;
         red_add(reinterpret_cast<long long *>(&pst()[kPsRetained]), 1);
+        const uint32_t B = v_B();
         if (S > B) red_add(reinterpret_cast<long long *>(&pst()[kPsZero]), 1);   // only a slot's first replication ends beyond B
-        if (S < B && B - S >= unit) { ++r; start_rep(); }
+        if (S < B && B - S >= v_unit()) { ++r; start_rep(); }
         else end_slot(true);
     };
 
@@ -431,7 +455,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
             if (D == 0 && t >= ell) return 1;
             return t >= abort_t ? 2 : 3;
         }
-        return t >= unit ? 1 : 3;
+        return t >= v_unit() ? 1 : 3;
     };
 
     // X moved at site I on a step where Y_t = X_{t+1} (met, or the pre-lag update t = 0, where
@@ -453,7 +477,7 @@ __global__ void __launch_bounds__(BATCH ? 384 : (DEG >= 6 ? 640 : 512), 1) pairs
         if (COUPLED && t == 0) {            // X_1 differs from Y_0 in bit I
             D = 1; tau = 0; t_end = stop_unmet;
             acquire_y();
-            if (Tnu) copy_y0(q, bit);
+            if (v_Tnu()) copy_y0(q, bit);
         }
     };
 
@@ -692,10 +716,12 @@ __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uin
 
 using PairsFn = void (*)(const KParams, const BParams);
 
-PairsFn pick(int coupled, int scan, bool batch, int udeg = 0) {
+PairsFn pick(int coupled, int scan, bool batch, int udeg = 0, bool wide = false) {
     if (batch) {
-        if (coupled) return pairs_kernel<true, false, true, 0>;
-        return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true, true, 0> : pairs_kernel<false, false, true, 0>;
+        if (coupled) return wide ? pairs_kernel<true, false, true, 0, true> : pairs_kernel<true, false, true, 0, false>;
+        if (scan == MCPD_SCAN_SYSTEMATIC)
+            return wide ? pairs_kernel<false, true, true, 0, true> : pairs_kernel<false, true, true, 0, false>;
+        return wide ? pairs_kernel<false, false, true, 0, true> : pairs_kernel<false, false, true, 0, false>;
     }
     if (coupled) {
         switch (udeg) {
@@ -717,9 +743,10 @@ int set_smem(size_t bytes, bool batch) {
             if (c && sc == MCPD_SCAN_SYSTEMATIC) continue;
             for (int ud = 0; ud <= 8; ++ud) {
                 if (ud && (batch || !c || ud < 3)) continue;
-                if (cudaFuncSetAttribute(pick(c, sc, batch, ud), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(bytes)) != cudaSuccess)
-                    return MCPD_ECUDA;
+                for (int wide = 0; wide <= (batch ? 1 : 0); ++wide)
+                    if (cudaFuncSetAttribute(pick(c, sc, batch, ud, wide != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(bytes)) != cudaSuccess)
+                        return MCPD_ECUDA;
             }
         }
     return MCPD_OK;
@@ -743,7 +770,7 @@ int launch_pairs(const KParams &kp, int grid, int block, size_t smem, void *stre
 
 int launch_batch(const BParams &bp, int grid, int block, size_t smem, void *stream) {
     const KParams none{};
-    pick(bp.coupled, bp.scan, true)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(none, bp);
+    pick(bp.coupled, bp.scan, true, 0, bp.wide != 0)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(none, bp);
     return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
 }
 
@@ -782,7 +809,10 @@ size_t pairs_smem_bytes(size_t tables, int wpp, int warps, int y_regions) {
 
 int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int wpp, size_t smem_optin,
                 long long P, int sm_count, int warps, PairsShape *out) {
-    const int cap = pairs_max_threads(coupled, scan, udeg, batch) / 32;
+    // Batches: the wide variant when the pair state leaves room for more warps than the narrow one
+    // is compiled for.
+    bool wide = batch;
+    int cap = pairs_max_threads(coupled, scan, udeg, batch, wide) / 32;
     auto bytes = [&](int w) { return pairs_smem_bytes(tables, wpp, w, pairs_y_regions(coupled, w)); };
     auto most = [&](size_t budget) {
         int best = 0;
@@ -791,12 +821,19 @@ int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int 
     };
     auto resident = [&](int w, int *per_sm) {
         *per_sm = 1;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pick(coupled, scan, batch, batch ? 0 : udeg),
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pick(coupled, scan, batch, batch ? 0 : udeg, wide),
                                                              w * 32, bytes(w)) == cudaSuccess;
     };
-    const int w1 = most(smem_optin);
+    int w1 = most(smem_optin);
     if (w1 < 1) return MCPD_ETOO_LARGE;
-    if (set_smem(bytes(w1), batch) != MCPD_OK) return MCPD_ECUDA;
+    if (batch) {
+        const int narrow = pairs_max_threads(coupled, scan, 0, true, false) / 32;
+        const int target = warps > 0 ? std::min(warps, w1) : w1;
+        if (target <= narrow) { wide = false; cap = narrow; w1 = most(smem_optin); }
+    }
+    // The attribute is a permission shared by every launch of the kernel (the classes of a batch
+    // have different sizes): allow the device's opt-in maximum.
+    if (set_smem(smem_optin, batch) != MCPD_OK) return MCPD_ECUDA;
     PairsShape s;
     if (warps > 0) {
         if (warps > w1) return MCPD_EINVAL;
@@ -822,15 +859,16 @@ int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int 
         }
     }
     s.y_regions = pairs_y_regions(coupled, s.warps);
+    s.wide = wide;
     s.smem = bytes(s.warps);
     if (s.per_sm < 1) s.per_sm = 1;
     *out = s;
     return MCPD_OK;
 }
 
-int pairs_max_threads(int coupled, int scan, int udeg, bool batch) {
+int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide) {
     cudaFuncAttributes a{};
-    if (cudaFuncGetAttributes(&a, pick(coupled, scan, batch, batch ? 0 : udeg)) != cudaSuccess) return 512;
+    if (cudaFuncGetAttributes(&a, pick(coupled, scan, batch, batch ? 0 : udeg, wide)) != cudaSuccess) return 512;
     return a.maxThreadsPerBlock;
 }
 

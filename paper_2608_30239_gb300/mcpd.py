@@ -327,13 +327,15 @@ class Plan:
 
 
 class Batch:
-    """mcpd_batch: many instances (each with its own parameters) decoded in one persistent launch.
+    """mcpd_batch: many instances (each with its own parameters) decoded in one persistent launch
+    per size class.
 
     `instances` is a list of synth-like instances; `params` a list of keyword dicts (one per
-    instance) or one dict for all.  Outputs of run()/fetch are concatenated in input order;
-    `offsets[i]:offsets[i+1]` belong to instance i."""
+    instance) or one dict for all.  `order_mode` 0 (input order) or 1 (longest slots first);
+    `classes` 0 (automatic) or 1..8 size classes.  Outputs of run()/fetch are concatenated in
+    input order; `offsets[i]:offsets[i+1]` belong to instance i."""
 
-    def __init__(self, ctx: Context, instances, params, order_mode=0):
+    def __init__(self, ctx: Context, instances, params, order_mode=0, classes=0):
         self.ctx = ctx
         n = len(instances)
         if isinstance(params, dict):
@@ -348,11 +350,12 @@ class Batch:
             ys[i] = _ptr(y).value
             prms[i] = make_params(inst, self._keep, **kw)
         h = C.c_void_p()
-        ctx.check(lib().mcpd_batch_create(ctx.h, n, designs, ys, prms, int(order_mode), C.byref(h)),
-                  "mcpd_batch_create")
+        ctx.check(lib().mcpd_batch_create(ctx.h, n, designs, ys, prms, int(order_mode) | (int(classes) << 8),
+                                          C.byref(h)), "mcpd_batch_create")
         self.h = h
         self.n_inst = n
         self.info = self._info()
+        self.classes = int(self.info[9])
         self.total_active = int(self.info[0])
         self.offsets = np.zeros(n + 1, np.int64)
         lib().mcpd_batch_offsets(h, _ptr(self.offsets))

@@ -79,12 +79,15 @@ def _run(ctx, batch):
     return est.cpu().numpy(), se.cpu().numpy(), st
 
 
-@pytest.mark.parametrize("coupled", [True, False])
-def test_batch_matches_oracle_per_instance(ctx, coupled):
+@pytest.mark.parametrize("coupled,classes", [(True, 1), (True, 3), (False, 1), (False, 3)])
+def test_batch_matches_oracle_per_instance(ctx, coupled, classes):
+    """Every instance equals the oracle alone, with one launch or with three size classes (each a
+    launch fitted to its instances)."""
     from paper_2608_30239_gb300 import mcpd
     insts = _uneven()
     ps = _params(insts, coupled)
-    batch = mcpd.Batch(ctx, insts, ps)
+    batch = mcpd.Batch(ctx, insts, ps, classes=classes)
+    assert batch.classes == classes
     est, se, st = _run(ctx, batch)
     assert st["reps_retained"] > 0
     for i, (inst, kw) in enumerate(zip(insts, ps)):
@@ -122,8 +125,13 @@ def test_graph_shapes_and_order_do_not_change_results(ctx):
     other = mcpd.Batch(ctx, insts, ps, order_mode=1)
     e2, s2, _ = _run(ctx, other)
     assert np.array_equal(e2, e0) and np.array_equal(s2, s0)
+    split = mcpd.Batch(ctx, insts, ps, order_mode=1, classes=4)
+    assert split.classes == 4
+    e3, s3, _ = _run(ctx, split)
+    assert np.array_equal(e3, e0) and np.array_equal(s3, s0)
     batch.close()
     other.close()
+    split.close()
 
 
 @pytest.mark.parametrize("lanes", [8, 16, 32])
@@ -136,9 +144,9 @@ def test_lane_groups_match_oracle(ctx, lanes):
     ps = _params(insts)
     rng = np.random.default_rng(lanes)
     ps[1] = dict(ps[1], init_marginals=rng.random(insts[1].n) * 0.3)
-    batch = mcpd.Batch(ctx, insts, ps)
+    batch = mcpd.Batch(ctx, insts, ps, classes=2)
     batch.set_shape(0, lanes)
-    assert int(batch.info[8]) == lanes
+    assert int(batch.info[8]) == lanes and int(batch.info[9]) == 2
     est, se, st = _run(ctx, batch)
     for i, (inst, kw) in enumerate(zip(insts, ps)):
         M = oracle.Model(inst, init_marginals=kw.get("init_marginals"))
@@ -199,7 +207,7 @@ def test_batch_mixed_degree_instances(ctx, lanes):
                                        600 + i, 700 + i) for i in range(3)] + _uneven(2, seed=21)
     ps = _params(insts)
     ps[0] = dict(ps[0], init_marginals=np.random.default_rng(9).random(insts[0].n) * 0.25)
-    batch = mcpd.Batch(ctx, insts, ps)
+    batch = mcpd.Batch(ctx, insts, ps, classes=2)
     if lanes != 1:
         batch.set_shape(0, lanes)
     est, se, st = _run(ctx, batch)
