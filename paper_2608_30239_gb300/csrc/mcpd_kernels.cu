@@ -337,10 +337,15 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     // (completed, so X_C = Y_{C-1}), first close the open intervals at C, which for a bit set in
     // X_C adds W(C) - W(C-1) (coupled) or W(C) (uncoupled), both wstep(C), and add the
     // replication's G into the slot's sums.
+    // Flip events go to both the replication's sums and the slot's sums, so a completed
+    // replication only zeroes its own (stores) and adds its closing terms; the replication's sums
+    // are read back only when it is discarded (doomed or at the step limit), to take its events
+    // out of the slot's sums.
     auto finish_rep = [&](bool move, uint32_t C) {
         const long long wX = move ? static_cast<long long>(wstep(C)) : 0;
         if (COUPLED && D != 0) release_y();
         long long *const ra = racc();
+        long long *const sa = sacc();
         uint32_t groups = rep_words;
         while (groups) {
             const int g = __ffs(groups) - 1;
@@ -350,24 +355,32 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
             for (uint32_t q = q0; q < q1; ++q) {
                 const uint32_t xw = st[q * 32];
                 const uint32_t tw = __ldcg(&trep()[q]);
-                uint32_t moved = 0;
-                uint32_t m = tw | xw;
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    const uint32_t bit = 1u << b;
-                    m &= m - 1;
+                uint32_t tm = tw;
+                while (tm) {
+                    const int b = __ffs(tm) - 1;
+                    tm &= tm - 1;
                     const uint32_t j = q * 32 + b;
-                    long long v = 0;
-                    if (tw & bit) { v = __ldcg(&ra[j]); ra[j] = 0; }
-                    if (move) {
-                        if (xw & bit) v += wX;
-                        if (v != 0) { red_add(&sacc()[j], v); moved |= bit; }
-                    }
-                    if (xw & bit) bump_counts(j, 0xFFu, cbase);
+                    if (!move) red_add(&sa[j], -__ldcg(&ra[j]));   // discarded: its events leave the slot
+                    ra[j] = 0;
                 }
+                if (move && wX != 0) {          // closing terms of the sites set in X_C
+                    uint32_t om = xw;
+                    while (om) {
+                        const int b = __ffs(om) - 1;
+                        om &= om - 1;
+                        red_add(&sa[q * 32 + b], wX);
+                    }
+                }
+                uint32_t xm = xw;                 // X's counts back to zero
+                while (xm) {
+                    const int b = __ffs(xm) - 1;
+                    xm &= xm - 1;
+                    bump_counts(q * 32 + b, 0xFFu, cbase);
+                }
+                const uint32_t touched = tw | (move && wX != 0 ? xw : 0u);
                 if (tw) trep()[q] = 0u;
                 if (xw) st[q * 32] = 0u;
-                if (moved) { red_or(&tslot()[q], moved); slot_words |= 1u << g; }
+                if (touched) { red_or(&tslot()[q], touched); slot_words |= 1u << g; }
             }
         }
         rep_words = 0;
@@ -470,7 +483,9 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
             if (real(l, ent)) cbase[ent[l] & 0x7FFFu] = static_cast<unsigned char>(cx[l] + delta);
         const uint32_t w = wstep(t);
         if (w) {
-            red_add(&racc()[I], nX ? -static_cast<long long>(w) : static_cast<long long>(w));
+            const long long ev = nX ? -static_cast<long long>(w) : static_cast<long long>(w);
+            red_add(&racc()[I], ev);
+            red_add(&sacc()[I], ev);
             red_or(&trep()[q], bit);
         }
         rep_words |= 1u << (q >> gshift);
@@ -508,6 +523,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         }
         if (ev != 0) {
             red_add(&racc()[I], ev);
+            red_add(&sacc()[I], ev);
             red_or(&trep()[q], bit);
         }
         rep_words |= 1u << (q >> gshift);
