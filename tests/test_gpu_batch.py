@@ -222,3 +222,24 @@ def test_batch_mixed_degree_instances(ctx, lanes):
         a, b = batch.offsets[i], batch.offsets[i + 1]
         assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"])
     batch.close()
+
+
+def test_batch_systematic_uncoupled(ctx):
+    """Uncoupled systematic-scan chains (Algorithm 1) in a batch of uneven instances, two classes."""
+    from paper_2608_30239_gb300 import mcpd
+    insts = _uneven(4, seed=31)
+    ps = [dict(slots=150 + 40 * i, coupled=False, scan=mcpd.MCPD_SCAN_SYSTEMATIC, burn=inst.n // 10,
+               length=inst.n, horizon=3 * inst.n, seed=61 + i, instance_id=i) for i, inst in enumerate(insts)]
+    batch = mcpd.Batch(ctx, insts, ps, classes=2)
+    est, se, st = _run(ctx, batch)
+    for i, (inst, kw) in enumerate(zip(insts, ps)):
+        M = oracle.Model(inst, scan=oracle.SCAN_SYSTEMATIC)
+        run = oracle.uncoupled_run(kw["burn"], kw["length"], kw["horizon"], kw["seed"], instance=i)
+        ref = M.run_slots(run, 0, kw["slots"], THREADS)
+        ref["est"], ref["se"] = M.finalize(ref, kw["slots"], kw["length"])
+        got = batch.buckets(i)
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"])
+    batch.close()

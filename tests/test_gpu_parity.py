@@ -179,6 +179,18 @@ def test_step_limit_reports_error_and_context_survives(ctx):
     assert again["stats"]["status"] == mcpd.MCPD_OK
 
 
+@pytest.mark.parametrize("deg", [4, 7, 8])
+def test_uniform_degree_variants(ctx, deg):
+    """Kernels compiled for a uniform degree: 4 (mask-indexed thresholds), 7 and 8 (coded
+    thresholds); coupled with refill, against the oracle."""
+    inst = synth.make_instance(230, 21, deg, 4, 0.08, 0.15, 4 / 230, 70 + deg, 80 + deg)
+    k, ell = oracle.window_defaults(inst.n, 1)
+    P, B = 2500, 3 * ell + 11
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=313, record_slots=True)
+    o = _oracle_run(inst, P, k, ell, B, 313)
+    _assert_same(g, o)
+
+
 def _mixed():
     """260 clones x 23 pools, each clone in 2 to 8 pools: rows padded to the longest."""
     return synth.make_mixed_instance(260, 23, 2, 8, 6, 0.1, 0.2, 6 / 260, 31, 32)
