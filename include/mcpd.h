@@ -86,6 +86,9 @@ typedef struct mcpd_params {
     int32_t record_slots;      /* 1: keep per-slot N*_p, retained cost and replication counts     */
     int64_t slot_offset;       /* global id of slot 0 (partitioning slots across calls or GPUs)   */
     int64_t trace_stride;      /* > 0: keep the G vector of every slot p with p % stride == 0     */
+    int64_t tau_audit;         /* > 0 (coupled): count completed replications whose meeting time
+                                  tau exceeds this many progress units, the pairs a finite meeting
+                                  cap at that length would have stopped (the run stays uncapped)  */
 } mcpd_params;
 
 /* Counters of one run. */
@@ -100,6 +103,7 @@ typedef struct mcpd_stats {
     int64_t n_buckets;         /* number of N*_p values the integer sums are kept for             */
     int64_t n_active;
     double kernel_ms;          /* device time of the sampling kernel (CUDA events)                */
+    int64_t tau_over_audit;    /* completed replications with tau > params.tau_audit              */
 } mcpd_stats;
 
 typedef struct mcpd_ctx mcpd_ctx;

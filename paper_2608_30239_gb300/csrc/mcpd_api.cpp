@@ -163,7 +163,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     kp.dummy_entry = t.dummy_entry; kp.dummy_word = t.dummy_word;
     kp.dummy_word_index = t.dummy_word_index; kp.coupled = t.coupled ? 1 : 0;
     kp.P = t.P; kp.B = t.B; kp.k = t.k; kp.ell = t.ell; kp.L = t.L; kp.burn = t.burn;
-    kp.length = t.length; kp.unit = t.unit; kp.step_limit = t.step_limit;
+    kp.length = t.length; kp.unit = t.unit; kp.step_limit = t.step_limit; kp.tau_audit = t.tau_audit;
     kp.slot_offset = t.slot_offset; kp.trace_stride = t.trace_stride;
     kp.seed = t.seed; mcpd::philox_round_keys(t.seed, kp.rk); kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
@@ -248,6 +248,7 @@ int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *pl, mcpd_stats *stats) {
         stats->step_limit_hits = static_cast<int64_t>(c[mcpd::kStepLimitHits]);
         stats->max_tau = static_cast<int64_t>(c[mcpd::kMaxTau]);
         stats->sum_tau = static_cast<int64_t>(c[mcpd::kSumTau]);
+        stats->tau_over_audit = static_cast<int64_t>(c[mcpd::kTauOverAudit]);
         stats->site_updates = pl->t.coupled ? 2 * stats->progress_units - stats->reps_started
                                             : stats->progress_units;
         stats->n_buckets = pl->t.nb;
@@ -648,7 +649,7 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         d.na = t.na; d.W = t.W; d.wpp = t.wpp; d.deg = t.deg_max; d.nb = static_cast<int32_t>(t.nb);
         d.dummy_word_index = t.dummy_word_index; d.dummy_entry = t.dummy_entry; d.dummy_word = t.dummy_word;
         d.P = t.P; d.B = t.B; d.k = t.k; d.ell = t.ell; d.L = t.L; d.burn = t.burn; d.length = t.length;
-        d.unit = t.unit; d.step_limit = t.step_limit; d.slot_offset = t.slot_offset;
+        d.unit = t.unit; d.step_limit = t.step_limit; d.slot_offset = t.slot_offset; d.tau_audit = t.tau_audit;
         d.work_begin = work; work += t.P;
         d.seed = t.seed; d.instance = t.instance;
         mcpd::BParams &bp = c.bp;
@@ -780,6 +781,7 @@ int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *b, mcpd_stats *stats) {
         stats->step_limit_hits = static_cast<int64_t>(c[mcpd::kStepLimitHits]);
         stats->max_tau = static_cast<int64_t>(c[mcpd::kMaxTau]);
         stats->sum_tau = static_cast<int64_t>(c[mcpd::kSumTau]);
+        stats->tau_over_audit = static_cast<int64_t>(c[mcpd::kTauOverAudit]);
         stats->site_updates = b->coupled ? 2 * stats->progress_units - stats->reps_started : stats->progress_units;
         stats->n_buckets = static_cast<int64_t>(b->total_counts);
         stats->n_active = b->total_active;

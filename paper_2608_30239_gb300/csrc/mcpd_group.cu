@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
     unsigned long long *bS1 = nullptr, *bS2lo = nullptr, *bS2hi = nullptr, *bCount = nullptr;
     int na = 0, n_init = 0;
     uint32_t W = 0, B = 0, ell = 0, step_limit = 0, instance = 0, k0 = 0, k1 = 0, gshift = 0;
-    long long kk = 0, LL = 0, work_begin = 0, work_end = 0, slot_offset = 0;
+    long long kk = 0, LL = 0, work_begin = 0, work_end = 0, slot_offset = 0, tau_audit = 0;
     int cur = -1;
     auto load_instance = [&](const InstDesc &d) {
         gAlias = reinterpret_cast<const unsigned long long *>(d.alias);
@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
         bS1 = d.S1; bS2lo = d.S2lo; bS2hi = d.S2hi; bCount = d.bcount;
         na = d.na; W = d.W; B = static_cast<uint32_t>(d.B); ell = static_cast<uint32_t>(d.ell);
         step_limit = static_cast<uint32_t>(d.step_limit); instance = d.instance;
+        tau_audit = d.tau_audit;
         k0 = static_cast<uint32_t>(d.seed); k1 = static_cast<uint32_t>(d.seed >> 32);
         kk = d.k; LL = d.L; slot_offset = d.slot_offset;
         work_begin = d.work_begin; work_end = d.work_begin + d.P;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
     uint32_t slot_local = 0, slot_g = 0, r = 0, t = 0, S = 0, N = 0, tau = 0, abort_t = 0xFFFFFFFFu;
     unsigned long long rep_words = 0, slot_words = 0;
     unsigned long long c_prog = 0, c_started = 0, c_retained = 0, c_aborted = 0, c_zero = 0,
-                       c_limit = 0, c_sumtau = 0;
+                       c_limit = 0, c_sumtau = 0, c_audit = 0;
     uint32_t c_maxtau = 0;
 
     auto group_or64 = [&](unsigned long long v) -> unsigned long long {
@@ -221,6 +222,7 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
         c_prog += C;
         c_sumtau += tau;
         c_maxtau = max(c_maxtau, tau);
+        if (tau_audit > 0 && tau > tau_audit) ++c_audit;
         finish_rep(true, C);
         S += C;
         N += 1;
@@ -344,6 +346,7 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
         if (c_zero) atomicAdd(&bp.counters[kZeroCompletion], c_zero);
         if (c_limit) atomicAdd(&bp.counters[kStepLimitHits], c_limit);
         if (c_sumtau) atomicAdd(&bp.counters[kSumTau], c_sumtau);
+        if (c_audit) atomicAdd(&bp.counters[kTauOverAudit], c_audit);
         if (c_maxtau) atomicMax(&bp.counters[kMaxTau], static_cast<unsigned long long>(c_maxtau));
     }
 }

@@ -33,13 +33,13 @@ constexpr int64_t kMaxBuckets = 1 << 16;
 // Counter slots of the device statistics block.
 enum Counter {
     kWork = 0, kProgress, kSiteUpdates, kRepsStarted, kRepsRetained, kRepsAborted,
-    kZeroCompletion, kStepLimitHits, kMaxTau, kSumTau, kNumCounters = 16
+    kZeroCompletion, kStepLimitHits, kMaxTau, kSumTau, kTauOverAudit, kNumCounters = 16
 };
 
 // Per-pair statistics record of the one-thread-per-pair kernel, summed into the counters at exit.
 enum PairStat {
     kPsProgress = 0, kPsStarted, kPsRetained, kPsAborted, kPsZero, kPsLimit, kPsSumTau, kPsMaxTau,
-    kPairStats = 8
+    kPsTauAudit, kPairStats = 9
 };
 
 // Per-pair scratch, one contiguous block of 8-byte words per pair: the replication's sums G
@@ -75,7 +75,7 @@ struct Tables {
     int32_t dummy_word_index = 0;
     // run shape
     int64_t k = 0, ell = 0, L = 0, burn = 0, length = 0, unit = 1;
-    int64_t P = 0, B = 0, nb = 1, step_limit = 0, slot_offset = 0, trace_stride = 0;
+    int64_t P = 0, B = 0, nb = 1, step_limit = 0, slot_offset = 0, trace_stride = 0, tau_audit = 0;
     uint64_t seed = 0;
     uint32_t instance = 0;
     bool record_slots = false;
@@ -115,7 +115,7 @@ struct KParams {
     int32_t udeg, pad1;               // uniform degree (0: mixed)
     uint32_t dummy_entry, dummy_word;
     int32_t dummy_word_index, coupled;
-    long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset, trace_stride;
+    long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset, trace_stride, tau_audit;
     unsigned long long seed;
     uint32_t instance;
     int32_t warps;
@@ -148,7 +148,7 @@ struct InstDesc {
     int32_t n_init_pairs, pad0;
     int32_t na, W, wpp, deg, nb, dummy_word_index;
     uint32_t dummy_entry, dummy_word;
-    long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset;
+    long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset, tau_audit;
     long long work_begin;             // global index of this instance's first slot in the launch
     unsigned long long seed;
     uint32_t instance;

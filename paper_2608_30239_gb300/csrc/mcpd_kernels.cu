@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     MCPD_FIELD(v_B, static_cast<uint32_t>(__ldg(&desc()->B)), static_cast<uint32_t>(p.B));
     MCPD_FIELD(v_unit, static_cast<uint32_t>(__ldg(&desc()->unit)), static_cast<uint32_t>(p.unit));
     MCPD_FIELD(v_step_limit, static_cast<uint32_t>(__ldg(&desc()->step_limit)), static_cast<uint32_t>(p.step_limit));
+    MCPD_FIELD(v_tau_audit, __ldg(&desc()->tau_audit), p.tau_audit);
     MCPD_FIELD(v_k, __ldg(&desc()->k), p.k);
     MCPD_FIELD(v_L, __ldg(&desc()->L), p.L);
     MCPD_FIELD(v_burn, __ldg(&desc()->burn), p.burn);
@@ -436,6 +437,8 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         if (COUPLED) {
             red_add(reinterpret_cast<long long *>(&pst()[kPsSumTau]), tau);
             red_max(&pst()[kPsMaxTau], tau);
+            const long long audit = v_tau_audit();
+            if (audit > 0 && tau > audit) red_add(reinterpret_cast<long long *>(&pst()[kPsTauAudit]), 1);
         }
         finish_rep(true, C);
         S += C;
@@ -664,7 +667,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
 
     // Every lane of the warp is here: sum (or max) the pairs' statistics over the warp.
     const int dst[kPairStats] = {kProgress, kRepsStarted, kRepsRetained, kRepsAborted,
-                                 kZeroCompletion, kStepLimitHits, kSumTau, kMaxTau};
+                                 kZeroCompletion, kStepLimitHits, kSumTau, kMaxTau, kTauOverAudit};
 #pragma unroll
     for (int i = 0; i < kPairStats; ++i) {
         unsigned long long v = __ldcg(&pst()[i]);

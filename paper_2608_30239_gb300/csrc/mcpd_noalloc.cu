@@ -154,7 +154,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     kp.dummy_entry = t.dummy_entry; kp.dummy_word = t.dummy_word;
     kp.dummy_word_index = t.dummy_word_index; kp.coupled = t.coupled ? 1 : 0;
     kp.P = t.P; kp.B = t.B; kp.k = t.k; kp.ell = t.ell; kp.L = t.L; kp.burn = t.burn;
-    kp.length = t.length; kp.unit = t.unit; kp.step_limit = t.step_limit;
+    kp.length = t.length; kp.unit = t.unit; kp.step_limit = t.step_limit; kp.tau_audit = t.tau_audit;
     kp.slot_offset = t.slot_offset; kp.trace_stride = 0;
     kp.seed = t.seed; philox_round_keys(t.seed, kp.rk); kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
@@ -179,6 +179,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
         stats->step_limit_hits = static_cast<int64_t>(c[kStepLimitHits]);
         stats->max_tau = static_cast<int64_t>(c[kMaxTau]);
         stats->sum_tau = static_cast<int64_t>(c[kSumTau]);
+        stats->tau_over_audit = static_cast<int64_t>(c[kTauOverAudit]);
         stats->site_updates = t.coupled ? 2 * stats->progress_units - stats->reps_started : stats->progress_units;
         stats->n_buckets = t.nb;
         stats->n_active = t.na;

@@ -286,6 +286,8 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
     if (t.B < 0 || t.B > (int64_t(1) << 30)) return fail(err, "horizon must be in [0, 2^30]", MCPD_EINVAL);
     t.nb = std::max<int64_t>(1, t.B / t.unit);
     if (t.nb > kMaxBuckets) return fail(err, "too many N*_p buckets (horizon / l > 65536)", MCPD_ETOO_LARGE);
+    if (prm->tau_audit < 0) return fail(err, "tau_audit must be >= 0", MCPD_EINVAL);
+    t.tau_audit = t.coupled ? prm->tau_audit : 0;
     t.step_limit = prm->step_limit > 0 ? prm->step_limit : int64_t(10000) * na;
     if (t.step_limit > (int64_t(1) << 31)) return fail(err, "step_limit above 2^31", MCPD_EINVAL);
     if (!t.coupled) t.step_limit = std::max(t.step_limit, t.unit + 1);

@@ -44,14 +44,14 @@ class mcpd_params(C.Structure):
                 ("horizon", C.c_int64), ("budget_site_updates", C.c_double),
                 ("step_limit", C.c_int64), ("seed", C.c_uint64), ("instance_id", C.c_uint32),
                 ("record_slots", C.c_int32), ("slot_offset", C.c_int64),
-                ("trace_stride", C.c_int64)]
+                ("trace_stride", C.c_int64), ("tau_audit", C.c_int64)]
 
 
 class mcpd_stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("progress_units", "site_updates", "reps_started", "reps_retained", "reps_aborted",
                  "zero_completion_slots", "step_limit_hits", "max_tau", "sum_tau", "n_buckets",
-                 "n_active")] + [("kernel_ms", C.c_double)]
+                 "n_active")] + [("kernel_ms", C.c_double), ("tau_over_audit", C.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -152,7 +152,7 @@ def make_params(inst=None, keep: _Keep | None = None, *, fp=None, fn=None, prior
                 n_active=0, scan=MCPD_SCAN_SCORE, coupled=True, scan_weights=None,
                 init_marginals=None, k=-1, ell=-1, burn=-1, length=-1, slots=1, horizon=0,
                 budget_site_updates=0.0, step_limit=0, seed=1, instance_id=0, record_slots=False,
-                slot_offset=0, trace_stride=0, lanes_per_pair=0):
+                slot_offset=0, trace_stride=0, lanes_per_pair=0, tau_audit=0):
     keep = keep or _Keep()
     sw = keep.arr(scan_weights, np.float64)
     nu = keep.arr(init_marginals, np.float64)
@@ -166,7 +166,7 @@ def make_params(inst=None, keep: _Keep | None = None, *, fp=None, fn=None, prior
         budget_site_updates=float(budget_site_updates), step_limit=int(step_limit),
         seed=int(seed) & 0xFFFFFFFFFFFFFFFF, instance_id=int(instance_id),
         record_slots=int(bool(record_slots)), slot_offset=int(slot_offset),
-        trace_stride=int(trace_stride))
+        trace_stride=int(trace_stride), tau_audit=int(tau_audit))
 
 
 def mcpd_inspect(inst, **params):

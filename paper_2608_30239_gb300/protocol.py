@@ -1,0 +1,115 @@
+"""The five-method comparison on a synthetic instance (the protocol of the paper's experiments,
+Section "Experimental Setup", on a generated stand-in for its unpublished instance).
+
+  python -m paper_2608_30239_gb300.protocol [--noise 0.10,0.10] [--sweeps 1,3,5,10,20] [--slots 65536]
+
+Methods, at an estimator length of s sweeps (M = s n_a single-site updates, b = round(0.1 M)):
+  SS   systematic scan, uncoupled: discard b updates, average the next M - b (Algorithm 1);
+  RU   uniform random scan, uncoupled (Algorithm 1);
+  SW   score-weighted random scan, uncoupled (Algorithm 2);
+  cRU  uniform random scan, coupled pairs, k = b + 1, l = M (Algorithms 3-4);
+  cSW  score-weighted random scan, coupled pairs (Algorithms 3-4).
+Every slot has a horizon of 20 sweeps.  The uncoupled methods hold twice as many slots as the
+coupled ones (each coupled slot holds two chains), so both hold the same number of chain states.
+The reference vector is a long systematic-scan run (burn-in and sampling lengths in sweeps).
+Scores are the mean absolute error over the retained clones and over the reference's ten largest.
+The coupled runs are uncapped; the share of completed pairs whose meeting time exceeds the cap
+(20 sweeps) is reported, the pairs a finite meeting cap would have stopped.
+Prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+import synth
+
+from . import mcpd
+
+
+def _decode(ctx, inst, **kw):
+    import torch
+    plan = mcpd.Plan(ctx, inst, **kw)
+    est = torch.empty(plan.n_active, dtype=torch.float64, device=f"cuda:{ctx.device}")
+    se = torch.empty_like(est)
+    plan.run_async(est, se)
+    st = plan.collect(allow_step_limit=True)
+    out = est.cpu().numpy(), plan.active.copy(), st
+    plan.close()
+    return out
+
+
+def round_half_even(x: float) -> int:
+    return int(np.round(x))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=1298)
+    ap.add_argument("--m", type=int, default=97)
+    ap.add_argument("--deg", type=int, default=6)
+    ap.add_argument("--positives", type=int, default=3)
+    ap.add_argument("--noise", default="0.10,0.10", help="fn,fp")
+    ap.add_argument("--n-active", type=int, default=333)
+    ap.add_argument("--sweeps", default="1,3,5,10,20")
+    ap.add_argument("--horizon-sweeps", type=int, default=20)
+    ap.add_argument("--slots", type=int, default=65536, help="coupled slots (uncoupled: twice as many)")
+    ap.add_argument("--ref-burn", type=int, default=1000, help="reference burn-in, sweeps")
+    ap.add_argument("--ref-sweeps", type=int, default=10000, help="reference sampling length, sweeps")
+    ap.add_argument("--ref-chains", type=int, default=65536)
+    ap.add_argument("--seed", type=int, default=20260)
+    ap.add_argument("--cap-sweeps", type=int, default=20, help="meeting cap audited (the runs stay uncapped)")
+    a = ap.parse_args(argv)
+    fn, fp = (float(v) for v in a.noise.split(","))
+    inst = synth.make_instance(a.n, a.m, a.deg, a.positives, fp, fn, a.positives / a.n, 5007, 9007)
+    ctx = mcpd.Context(0)
+    t0 = time.perf_counter()
+    ref, active, st_ref = _decode(ctx, inst, n_active=a.n_active, coupled=False, scan=mcpd.MCPD_SCAN_SYSTEMATIC,
+                                  burn=a.ref_burn * a.n_active, length=a.ref_sweeps * a.n_active,
+                                  horizon=(a.ref_burn + a.ref_sweeps) * a.n_active, slots=a.ref_chains,
+                                  seed=a.seed + 1)
+    t_ref = time.perf_counter() - t0
+    top = np.argsort(-ref, kind="stable")[:10]
+    horizon = a.horizon_sweeps * a.n_active
+    methods = {
+        "SS": dict(coupled=False, scan=mcpd.MCPD_SCAN_SYSTEMATIC),
+        "RU": dict(coupled=False, scan=mcpd.MCPD_SCAN_UNIFORM),
+        "SW": dict(coupled=False, scan=mcpd.MCPD_SCAN_SCORE),
+        "cRU": dict(coupled=True, scan=mcpd.MCPD_SCAN_UNIFORM),
+        "cSW": dict(coupled=True, scan=mcpd.MCPD_SCAN_SCORE),
+    }
+    rows = []
+    for s in (int(v) for v in a.sweeps.split(",")):
+        M = s * a.n_active
+        b = round_half_even(0.1 * M)
+        for name, kw in methods.items():
+            if kw["coupled"]:
+                kw2 = dict(kw, k=b + 1, ell=M, slots=a.slots, tau_audit=a.cap_sweeps * a.n_active)
+            else:
+                kw2 = dict(kw, burn=b, length=M - b, slots=2 * a.slots)
+            t1 = time.perf_counter()
+            est, act, st = _decode(ctx, inst, n_active=a.n_active, horizon=horizon, seed=a.seed + 100 * s + len(rows), **kw2)
+            assert np.array_equal(act, active)
+            rows.append({"sweeps": s, "method": name, "mae_all": float(np.mean(np.abs(est - ref))),
+                         "mae_top10": float(np.mean(np.abs(est[top] - ref[top]))),
+                         "site_updates": st["site_updates"], "kernel_ms": st["kernel_ms"],
+                         "step_limit_hits": st["step_limit_hits"],
+                         "mean_tau_sweeps": (st["sum_tau"] / max(1, st["reps_retained"]) / a.n_active) if kw["coupled"] else None,
+                         "max_tau_sweeps": (st["max_tau"] / a.n_active) if kw["coupled"] else None,
+                         "cap_hit_rate": (st["tau_over_audit"] / max(1, st["reps_retained"])) if kw["coupled"] else None,
+                         "seconds": time.perf_counter() - t1})
+    out = {"instance": dict(n=a.n, m=a.m, deg=a.deg, positives=a.positives, fn=fn, fp=fp, n_active=a.n_active),
+           "reference": dict(burn_sweeps=a.ref_burn, sweeps=a.ref_sweeps, chains=a.ref_chains, seconds=t_ref,
+                             site_updates=st_ref["site_updates"], top10=[int(active[i]) for i in top]),
+           "slots_coupled": a.slots, "slots_uncoupled": 2 * a.slots, "horizon_sweeps": a.horizon_sweeps,
+           "rows": rows}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

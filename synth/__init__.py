@@ -5,9 +5,9 @@ decoding method's arithmetic (no likelihoods, no weights, no tables, no estimato
 oracle and the CUDA library receive its arrays as plain inputs.
 """
 from .designs import (Instance, SplitMix64, kset_design, tapestry_like_design, mixed_degree_design,
-                      draw_outcomes, make_instance, make_mixed_instance, tiny_config, paper_shaped_config, high_noise_config,
+                      draw_outcomes, make_instance, make_mixed_instance, make_tapestry_like_instance, tiny_config, paper_shaped_config, high_noise_config,
                       batched_configs, budget_horizon)
 
 __all__ = ["Instance", "SplitMix64", "kset_design", "tapestry_like_design", "mixed_degree_design",
-           "draw_outcomes", "make_instance", "make_mixed_instance", "tiny_config", "paper_shaped_config", "high_noise_config",
+           "draw_outcomes", "make_instance", "make_mixed_instance", "make_tapestry_like_instance", "tiny_config", "paper_shaped_config", "high_noise_config",
            "batched_configs", "budget_horizon"]

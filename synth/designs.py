@@ -175,6 +175,14 @@ def make_mixed_instance(n, m, deg_lo, deg_hi, n_pos, fp, fn, q, design_seed, out
                     positives=positives, fp=fp, fn=fn, q=q, seed=design_seed, label=label)
 
 
+def make_tapestry_like_instance(n, m, deg, n_pos, fp, fn, q, design_seed, outcome_seed, label=""):
+    """As `make_instance`, on a `tapestry_like_design` (the shape of the Tapestry designs)."""
+    clone_ptr, clone_pools = tapestry_like_design(n, m, deg, design_seed)
+    positives, y = draw_outcomes(n, m, clone_ptr, clone_pools, n_pos, fp, fn, outcome_seed)
+    return Instance(n=n, m=m, clone_ptr=clone_ptr, clone_pools=clone_pools, y=y,
+                    positives=positives, fp=fp, fn=fn, q=q, seed=design_seed, label=label)
+
+
 def tiny_config(seed: int = 1) -> Instance:
     """20 clones, 8 pools, 3 pools per clone, 2 true positives, fp .02, fn .05, prior .01."""
     return make_instance(20, 8, 3, 2, 0.02, 0.05, 0.01, 1000 + seed, 2000 + seed,

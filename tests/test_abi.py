@@ -111,6 +111,7 @@ def test_window_and_horizon_defaults(L, oracle_lib):
     (dict(instance_id=1 << 24), mcpd.MCPD_EINVAL),
     (dict(coupled=False, burn=0, length=1), mcpd.MCPD_EINVAL),
     (dict(horizon=10 ** 6, ell=1, k=0), mcpd.MCPD_ETOO_LARGE),
+    (dict(tau_audit=-1), mcpd.MCPD_EINVAL),
 ])
 def test_invalid_parameters_rejected(L, kw, code):
     inst = synth.tiny_config(1)

@@ -169,6 +169,22 @@ def test_decode_host_api_matches_plan(ctx):
     assert np.all(d["est"][pruned] == 0) and np.all(d["se"][pruned] == 0)
 
 
+@pytest.mark.parametrize("audit", [1, 5, 40])
+def test_tau_audit_counts_meetings_beyond_the_threshold(ctx, audit):
+    """With one replication per slot (B = 0), the audit count equals the number of slots whose
+    oracle replication met at tau > audit, and the sums are those of an unaudited run."""
+    inst = synth.tiny_config(4)
+    P = 4096
+    g = _gpu_run(ctx, inst, slots=P, k=3, ell=20, horizon=0, seed=55, tau_audit=audit)
+    M = oracle.Model(inst)
+    run = oracle.coupled_run(3, 20, 0, 55)
+    taus = np.array([M.replication(run, p)["tau"] for p in range(P)])
+    assert g["stats"]["tau_over_audit"] == int((taus > audit).sum())
+    assert g["stats"]["max_tau"] == int(taus.max()) and g["stats"]["sum_tau"] == int(taus.sum())
+    plain = _gpu_run(ctx, inst, slots=P, k=3, ell=20, horizon=0, seed=55)
+    assert np.array_equal(plain["S1"], g["S1"]) and plain["stats"]["tau_over_audit"] == 0
+
+
 def test_step_limit_reports_error_and_context_survives(ctx):
     from paper_2608_30239_gb300 import mcpd
     inst = synth.tiny_config(1)
@@ -188,6 +204,18 @@ def test_uniform_degree_variants(ctx, deg):
     P, B = 2500, 3 * ell + 11
     g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=313, record_slots=True)
     o = _oracle_run(inst, P, k, ell, B, 313)
+    _assert_same(g, o)
+
+
+@pytest.mark.parametrize("n,m", [(320, 48), (961, 93)])
+def test_tapestry_shaped_designs(ctx, n, m):
+    """The shapes of the paper's Tapestry designs (each sample in 3 pools; 320 x 48 and 961 x 93),
+    drawn as regular designs: coupled score-weighted decoding with refill equals the oracle."""
+    inst = synth.make_tapestry_like_instance(n, m, 3, 3, 0.05, 0.10, 3 / n, 90 + m, 91 + m)
+    k, ell = oracle.window_defaults(inst.n, 1)
+    P, B = 2000, 5 * ell
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=420, record_slots=True)
+    o = _oracle_run(inst, P, k, ell, B, 420)
     _assert_same(g, o)
 
 
