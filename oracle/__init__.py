@@ -42,7 +42,8 @@ class Run(C.Structure):
     """Mirror of `orc_run` in mcpd_oracle.c."""
     _fields_ = [("k", C.c_int64), ("ell", C.c_int64), ("burn", C.c_int64), ("length", C.c_int64),
                 ("horizon", C.c_int64), ("step_limit", C.c_int64), ("seed", C.c_uint64),
-                ("slot_offset", C.c_int64), ("instance", C.c_int32), ("coupled", C.c_int32)]
+                ("slot_offset", C.c_int64), ("instance", C.c_int32), ("coupled", C.c_int32),
+                ("pad", C.c_int32), ("meeting_cap", C.c_int64)]
 
 
 def lib():
@@ -173,7 +174,7 @@ class Model:
     def replication(self, run: Run, slot: int, rep: int = 0, literal: bool = False,
                     traj_cap: int = 0):
         G = np.zeros(self.na, dtype=np.int64)
-        o3 = np.zeros(3, dtype=np.int64)
+        o3 = np.zeros(4, dtype=np.int64)
         tx = ty = sites = None
         if traj_cap:
             tx = np.zeros((traj_cap, self.na), dtype=np.uint8)
@@ -181,7 +182,7 @@ class Model:
             sites = np.full(traj_cap, -1, dtype=np.int32)
         rc = lib().orc_replication(self.h, C.byref(run), int(slot), int(rep), int(literal), _p(G),
                                    _p(o3), _p(tx), _p(ty), _p(sites), int(traj_cap))
-        res = dict(status=rc, G=G, C=int(o3[0]), tau=int(o3[1]), draws=int(o3[2]))
+        res = dict(status=rc, G=G, C=int(o3[0]), tau=int(o3[1]), draws=int(o3[2]), capped=int(o3[3]))
         if traj_cap:
             res.update(X=tx, Y=ty, sites=sites)
         return res
@@ -199,7 +200,7 @@ class Model:
         sS = np.zeros(P, np.int64) if per_slot else None
         sr = np.zeros(P, np.int32) if per_slot else None
         sG = np.zeros((P, na), np.int64) if slot_G else None
-        st = np.zeros(6, np.int64)
+        st = np.zeros(7, np.int64)
         rc = lib().orc_run_slots(self.h, C.byref(run), int(p_begin), int(p_end), int(threads),
                                  _p(S1), _p(lo), _p(hi), _p(cnt), _p(ns), _p(sS), _p(sr), _p(sG),
                                  _p(st))
@@ -207,7 +208,7 @@ class Model:
                     slot_S=sS, slot_reps=sr, slot_G=sG,
                     stats=dict(draws=int(st[0]), reps=int(st[1]), max_tau=int(st[2]),
                                sum_tau=int(st[3]), step_limit_hits=int(st[4]),
-                               zero_completion=int(st[5])))
+                               zero_completion=int(st[5]), capped=int(st[6])))
 
     def finalize(self, res: dict, P: int, L: int):
         est = np.zeros(self.na)
@@ -217,9 +218,10 @@ class Model:
         return est, se
 
 
-def coupled_run(k, ell, horizon, seed=1, step_limit=10_000_000, slot_offset=0, instance=0) -> Run:
+def coupled_run(k, ell, horizon, seed=1, step_limit=10_000_000, slot_offset=0, instance=0,
+                meeting_cap=0) -> Run:
     return Run(k=k, ell=ell, burn=0, length=1, horizon=horizon, step_limit=step_limit, seed=seed,
-               slot_offset=slot_offset, instance=instance, coupled=1)
+               slot_offset=slot_offset, instance=instance, coupled=1, meeting_cap=meeting_cap)
 
 
 def uncoupled_run(burn, length, horizon, seed=1, slot_offset=0, instance=0) -> Run:
@@ -229,10 +231,10 @@ def uncoupled_run(burn, length, horizon, seed=1, slot_offset=0, instance=0) -> R
 
 def decode(inst, P, k, ell, horizon, seed=1, threads=None, n_active=0, scan=SCAN_SCORE,
            custom_w=None, init_marginals=None, per_slot=False, slot_G=False, coupled=True,
-           burn=0, length=1, slot_offset=0, instance=0, step_limit=10_000_000):
+           burn=0, length=1, slot_offset=0, instance=0, step_limit=10_000_000, meeting_cap=0):
     """Whole decode on the CPU: per-clone theta_CT estimates and standard errors (active order)."""
     M = Model(inst, n_active=n_active, scan=scan, custom_w=custom_w, init_marginals=init_marginals)
-    run = (coupled_run(k, ell, horizon, seed, step_limit, slot_offset, instance) if coupled
+    run = (coupled_run(k, ell, horizon, seed, step_limit, slot_offset, instance, meeting_cap) if coupled
            else uncoupled_run(burn, length, horizon, seed, slot_offset, instance))
     res = M.run_slots(run, 0, P, threads or os.cpu_count() or 1, per_slot=per_slot, slot_G=slot_G)
     L = (ell - k + 1) if coupled else length

@@ -11,6 +11,9 @@
  *   - Single-site map Phi_i(x,u) = 1{u <= p_i(1|x_-i)} (Preliminaries) and Algorithms 1-3.
  *   - H_r and H_{k:l} (Section "Coupled Estimator and Fixed-Budget GPU Execution").
  *   - Algorithm 4: fixed horizon B, slot refill, N_p(B), N*_p(B), slot mean A_p(B), theta_CT.
+ *   - The meeting cap of the experiments (Appendix, setup of the estimator lengths): a pair that
+ *     has not met when its clock reaches the cap stops there and keeps H_{k:l} with every inner
+ *     sum cut at the cap, the finite-cap approximation of the uncapped estimator.
  * Every random number is a Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11), keyed as the
  * written spec in the design doc states, so that any implementation of the same spec draws the same
  * stream.  Everything is IEEE double; build with -ffp-contract=off so that no multiply-add is fused.
@@ -374,6 +377,8 @@ typedef struct orc_run {
     int64_t slot_offset;
     int32_t instance;
     int32_t coupled;         /* 1: Algorithms 3 and 4; 0: Algorithm 1 / 2 per replication */
+    int32_t pad;
+    int64_t meeting_cap;     /* > 0 (coupled, >= max(l, 1)): stop an unmet pair at t = cap */
 } orc_run;
 
 /* Draw (I_t, U_t) for time t of replication rep in slot `slot`. */
@@ -405,9 +410,11 @@ static void initial_state(const orc_model *M, const orc_run *R, uint32_t slot, u
 typedef struct rep_result {
     int64_t C, tau, draws;
     int32_t status;
+    int32_t capped;          /* stopped at the meeting cap before meeting (tau = 0) */
 } rep_result;
 
-/* One coupled replication (Algorithm 3), run until t >= l and X_t = Y_{t-1}.
+/* One coupled replication (Algorithm 3), run until t >= l and X_t = Y_{t-1}, or, with a meeting
+ * cap c, until t = c if the pair has not met by then (C = c, tau reported as 0).
  * The estimator G_j = L * H_{k:l}(h_j), L = l - k + 1, is accumulated in one of two ways:
  *   literal = 1: store the paths and evaluate H_r = X_r + sum_{s>=1} (X_{r+s} - Y_{r+s-1}) for
  *                each r in k..l (terms with r + s > C vanish by faithfulness, since C >= tau);
@@ -415,6 +422,7 @@ typedef struct rep_result {
  *                paths are produced:  G_j = sum_{r=k}^{l} X_r[j]
  *                                         + sum_{t=k+1}^{C} min(t - k, L) (X_t[j] - Y_{t-1}[j]),
  *                because exactly min(t-k, L) window indices r in k..l satisfy r < t.
+ * A capped pair keeps exactly the terms with r + s <= C = c, in both forms.
  * trajX / trajY (optional, literal mode or tests) receive X_0..X_C and Y_0..Y_{C-1}; sites the
  * drawn I_0..I_{C-1}. */
 static rep_result coupled_replication(const orc_model *M, const orc_run *R, uint32_t slot,
@@ -422,7 +430,7 @@ static rep_result coupled_replication(const orc_model *M, const orc_run *R, uint
                                       uint8_t *trajY, int32_t *sites, int64_t traj_cap) {
     const int32_t na = M->na;
     const int64_t k = R->k, ell = R->ell, L = R->ell - R->k + 1;
-    rep_result res = {0, 0, 0, ORC_OK};
+    rep_result res = {0, 0, 0, ORC_OK, 0};
     uint8_t *X = (uint8_t *)malloc((size_t)na), *Y = (uint8_t *)malloc((size_t)na);
     initial_state(M, R, slot, rep, X);
     memcpy(Y, X, (size_t)na);                                  /* X_0 = Y_0 = Z_0 */
@@ -460,6 +468,7 @@ static rep_result coupled_replication(const orc_model *M, const orc_run *R, uint
         }
     }
     while (t < ell || !met) {
+        if (R->meeting_cap > 0 && t >= R->meeting_cap) { res.capped = 1; break; }   /* t >= l: unmet */
         if (R->step_limit > 0 && t >= R->step_limit) { res.status = ORC_ESTEP_LIMIT; break; }
         step_draw(M, R, slot, rep, t, &I, &U);
         if (sites && t < cap) sites[t] = I;
@@ -481,7 +490,7 @@ static rep_result coupled_replication(const orc_model *M, const orc_run *R, uint
             }
         }
     }
-    res.C = t;                                                   /* C = max(l, tau) */
+    res.C = t;                                     /* C = max(l, tau), or the cap if capped */
     if (literal && res.status == ORC_OK) {
         int64_t C = res.C;
         if (C >= cap) res.status = ORC_EINVAL;
@@ -509,7 +518,7 @@ static rep_result uncoupled_replication(const orc_model *M, const orc_run *R, ui
                                         uint32_t rep, int64_t *G) {
     const int32_t na = M->na;
     const int64_t b = R->burn, T = R->length;
-    rep_result res = {0, 0, 0, ORC_OK};
+    rep_result res = {0, 0, 0, ORC_OK, 0};
     uint8_t *X = (uint8_t *)malloc((size_t)na);
     initial_state(M, R, slot, rep, X);
     for (int32_t a = 0; a < na; ++a) G[a] = (b == 0) ? X[a] : 0;
@@ -546,7 +555,7 @@ typedef struct slot_out {
  * replication, which completed beyond B, is retained alone.  Gp receives the sum of the retained
  * replications' G vectors, i.e. L N*_p A_p(B). */
 static int32_t run_slot(const orc_model *M, const orc_run *R, int64_t p, int64_t *Gp, int64_t *Gr,
-                        slot_out *so, int64_t stats[6]) {
+                        slot_out *so, int64_t stats[7]) {
     const int32_t na = M->na;
     uint32_t slot = (uint32_t)(R->slot_offset + p);
     int64_t S = 0, N = 0;
@@ -563,6 +572,7 @@ static int32_t run_slot(const orc_model *M, const orc_run *R, int64_t p, int64_t
         if (rr.status != ORC_OK) { status = rr.status; if (rr.status == ORC_ESTEP_LIMIT) stats[4]++; break; }
         if (rr.tau > stats[2]) stats[2] = rr.tau;
         stats[3] += rr.tau;
+        stats[6] += rr.capped;
         S += rr.C;                                               /* S_p(r) */
         if (S <= R->horizon) {
             N += 1;
@@ -594,7 +604,7 @@ typedef struct job {
     int64_t *slot_S;
     int32_t *slot_reps;
     int64_t *slot_G;
-    int64_t stats[6];
+    int64_t stats[7];
     int32_t status;
 } job;
 
@@ -627,13 +637,15 @@ static void *job_main(void *arg) {
 
 /* Run slots [p_begin, p_end) with `threads` worker threads and sum them into the N*_p buckets:
  * S1[n-1][j] = sum_{p: N*_p = n} G_pj and S2[n-1][j] = sum G_pj^2 as 128-bit (lo, hi) words.
- * stats: [draws, replications started, max tau, sum tau, step-limit hits, zero-completion slots].
+ * stats: [draws, replications started, max tau, sum tau, step-limit hits, zero-completion slots,
+ *         replications stopped at the meeting cap].
  * Per-slot outputs are optional (NULL to skip). */
 int orc_run_slots(const orc_model *M, const orc_run *R, int64_t p_begin, int64_t p_end,
                   int32_t threads, int64_t *S1, uint64_t *S2_lo, uint64_t *S2_hi, int64_t *count,
                   int32_t *slot_nstar, int64_t *slot_S, int32_t *slot_reps, int64_t *slot_G,
-                  int64_t stats[6]) {
+                  int64_t stats[7]) {
     if (R->coupled && (R->k < 0 || R->k > R->ell)) return ORC_EINVAL;
+    if (R->coupled && R->meeting_cap != 0 && R->meeting_cap < (R->ell > 1 ? R->ell : 1)) return ORC_EINVAL;
     if (!R->coupled && (R->burn < 0 || R->length < 1 || R->burn + R->length < 2)) return ORC_EINVAL;
     if (R->horizon < 0 || p_end < p_begin) return ORC_EINVAL;
     const int32_t na = M->na;
@@ -655,7 +667,7 @@ int orc_run_slots(const orc_model *M, const orc_run *R, int64_t p_begin, int64_t
         if (threads == 1) job_main(J); else pthread_create(&tid[w], NULL, job_main, J);
     }
     int32_t status = ORC_OK;
-    for (int32_t s = 0; s < 6; ++s) stats[s] = 0;
+    for (int32_t s = 0; s < 7; ++s) stats[s] = 0;
     for (int64_t e = 0; e < nb * na; ++e) { S1[e] = 0; S2_lo[e] = 0; S2_hi[e] = 0; }
     for (int64_t b = 0; b < nb; ++b) count[b] = 0;
     for (int32_t w = 0; w < threads; ++w) {
@@ -672,6 +684,7 @@ int orc_run_slots(const orc_model *M, const orc_run *R, int64_t p_begin, int64_t
         stats[0] += J->stats[0]; stats[1] += J->stats[1];
         if (J->stats[2] > stats[2]) stats[2] = J->stats[2];
         stats[3] += J->stats[3]; stats[4] += J->stats[4]; stats[5] += J->stats[5];
+        stats[6] += J->stats[6];
         if (J->status != ORC_OK && status == ORC_OK) status = J->status;
         free(J->S1); free(J->S2); free(J->count);
     }
@@ -681,7 +694,7 @@ int orc_run_slots(const orc_model *M, const orc_run *R, int64_t p_begin, int64_t
 
 /* One replication with its paths, for tests of the coupling and of the estimator identity. */
 int orc_replication(const orc_model *M, const orc_run *R, int64_t p, int32_t rep, int32_t literal,
-                    int64_t *G, int64_t out3[3], uint8_t *trajX, uint8_t *trajY, int32_t *sites,
+                    int64_t *G, int64_t out4[4], uint8_t *trajX, uint8_t *trajY, int32_t *sites,
                     int64_t traj_cap) {
     uint32_t slot = (uint32_t)(R->slot_offset + p);
     rep_result rr;
@@ -689,7 +702,7 @@ int orc_replication(const orc_model *M, const orc_run *R, int64_t p, int32_t rep
         rr = coupled_replication(M, R, slot, (uint32_t)rep, G, literal, trajX, trajY, sites, traj_cap);
     else
         rr = uncoupled_replication(M, R, slot, (uint32_t)rep, G);
-    out3[0] = rr.C; out3[1] = rr.tau; out3[2] = rr.draws;
+    out4[0] = rr.C; out4[1] = rr.tau; out4[2] = rr.draws; out4[3] = rr.capped;
     return rr.status;
 }
 

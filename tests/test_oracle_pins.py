@@ -299,6 +299,86 @@ def test_coupling_invariants(oracle_lib):
     assert saw_late_meeting
 
 
+@pytest.mark.parametrize("cap", [20, 24, 40])
+def test_meeting_cap_follows_the_uncapped_paths(oracle_lib, cap):
+    """With a meeting cap c the chains are the uncapped chains up to c: a pair that meets at
+    tau <= c gives the uncapped replication exactly; one with tau > c stops at C = c, tau = 0,
+    and its X, Y paths are the uncapped paths cut at c."""
+    inst = _inst(20, 8, 3, 2, 0.05, 0.1, 0.03)
+    M = oracle_lib.Model(inst)
+    k, ell = 3, 20
+    free = oracle_lib.coupled_run(k, ell, 0, seed=7, step_limit=200000)
+    capd = oracle_lib.coupled_run(k, ell, 0, seed=7, step_limit=200000, meeting_cap=cap)
+    n_capped = 0
+    for slot in range(80):
+        u = M.replication(free, slot, 0, traj_cap=5000)
+        c = M.replication(capd, slot, 0, traj_cap=5000)
+        assert u["status"] == 0 and c["status"] == 0
+        if u["tau"] <= cap:
+            assert c["capped"] == 0 and c["tau"] == u["tau"] and c["C"] == u["C"]
+            assert np.array_equal(c["G"], u["G"])
+        else:
+            n_capped += 1
+            assert c["capped"] == 1 and c["tau"] == 0 and c["C"] == c["draws"] == cap
+            assert np.array_equal(c["X"][:cap + 1], u["X"][:cap + 1])
+            assert np.array_equal(c["Y"][:cap], u["Y"][:cap])
+            assert not np.array_equal(c["X"][cap], c["Y"][cap - 1])
+    assert n_capped > 0
+
+
+def test_meeting_cap_at_the_window_keeps_only_the_window_term(oracle_lib):
+    """k = l = c: every correction term of H_k has r + s > c, so a capped pair gives G = X_k
+    (closed form); the literal and the swapped-sum forms agree with the cap."""
+    inst = _inst(20, 8, 3, 2, 0.05, 0.1, 0.03)
+    M = oracle_lib.Model(inst)
+    k = 6
+    run = oracle_lib.coupled_run(k, k, 0, seed=31, step_limit=200000, meeting_cap=k)
+    seen = 0
+    for slot in range(200):
+        r = M.replication(run, slot, 0, traj_cap=100)
+        lit = M.replication(run, slot, 0, literal=True)
+        assert np.array_equal(lit["G"], r["G"]) and lit["capped"] == r["capped"]
+        if r["capped"]:
+            seen += 1
+            assert np.array_equal(r["G"], r["X"][k].astype(np.int64))
+    assert seen > 0
+
+
+@pytest.mark.parametrize("k,ell,cap", [(3, 20, 20), (3, 20, 33), (0, 1, 2)])
+def test_meeting_cap_literal_definition_equals_swapped_sum(oracle_lib, k, ell, cap):
+    """The truncated H_{k:l} (inner sums over r + s <= c) from the literal double sum equals the
+    swapped-sum form for capped and uncapped replications alike."""
+    inst = _inst(20, 8, 3, 2, 0.05, 0.1, 0.03)
+    M = oracle_lib.Model(inst)
+    run = oracle_lib.coupled_run(k, ell, 0, seed=5, step_limit=200000, meeting_cap=cap)
+    for slot in range(60):
+        a = M.replication(run, slot, 0, literal=True)
+        b = M.replication(run, slot, 0, literal=False)
+        assert a["status"] == 0 and b["status"] == 0
+        assert (a["C"], a["tau"], a["capped"]) == (b["C"], b["tau"], b["capped"])
+        assert np.array_equal(a["G"], b["G"])
+
+
+def test_meeting_cap_slot_runs(oracle_lib):
+    """A cap at or above every meeting time changes nothing; a cap below some counts those pairs
+    as capped and charges each exactly c progress units; a cap below l is rejected."""
+    inst = _inst(20, 8, 3, 2, 0.05, 0.1, 0.03)
+    M = oracle_lib.Model(inst)
+    free = M.run_slots(oracle_lib.coupled_run(3, 20, 0, seed=13), 0, 300, per_slot=True)
+    big = M.run_slots(oracle_lib.coupled_run(3, 20, 0, seed=13, meeting_cap=free["stats"]["max_tau"]),
+                      0, 300, per_slot=True)
+    for key in ("S1", "S2_lo", "S2_hi", "count", "slot_S"):
+        assert np.array_equal(free[key], big[key]), key
+    assert big["stats"]["capped"] == 0
+    cap = 21
+    taus = np.array([M.replication(oracle_lib.coupled_run(3, 20, 0, seed=13), p, 0)["tau"] for p in range(300)])
+    small = M.run_slots(oracle_lib.coupled_run(3, 20, 0, seed=13, meeting_cap=cap), 0, 300, per_slot=True)
+    assert small["stats"]["capped"] == int((taus > cap).sum()) > 0
+    assert np.all(small["slot_S"][taus > cap] == cap)
+    bad = M.run_slots(oracle_lib.coupled_run(3, 20, 0, seed=13, meeting_cap=19), 0, 10)
+    assert bad["status"] == oracle_lib.ORC_EINVAL
+
+
 def test_phi_is_inverse_transform(oracle_lib):
     """Phi_i(x, u) = 1{u < T}: U just below T sets the bit, U = T clears it."""
     inst = synth.tiny_config(1)
