@@ -43,7 +43,7 @@ class Run(C.Structure):
     _fields_ = [("k", C.c_int64), ("ell", C.c_int64), ("burn", C.c_int64), ("length", C.c_int64),
                 ("horizon", C.c_int64), ("step_limit", C.c_int64), ("seed", C.c_uint64),
                 ("slot_offset", C.c_int64), ("instance", C.c_int32), ("coupled", C.c_int32),
-                ("pad", C.c_int32), ("meeting_cap", C.c_int64)]
+                ("pad", C.c_int32), ("meeting_cap", C.c_int64), ("lag", C.c_int64)]
 
 
 def lib():
@@ -78,6 +78,8 @@ def lib():
             L.orc_replication.argtypes = [P, C.POINTER(Run), C.c_int64, C.c_int32, C.c_int32, P,
                                           P, P, P, P, C.c_int64]
             L.orc_replication.restype = C.c_int
+            L.orc_lag_weight.argtypes = [C.c_int64] * 4
+            L.orc_lag_weight.restype = C.c_int64
             L.orc_finalize.argtypes = [C.c_int32, C.c_int64, P, P, P, C.c_int64, C.c_int64, P, P]
             _lib = L
     return _lib
@@ -218,10 +220,15 @@ class Model:
         return est, se
 
 
+def lag_weight(k, ell, lag, t) -> int:
+    """Weight of X_t and Y_t in G = L H_{k:l} for the lag-L estimator (mcpd_oracle.c)."""
+    return int(lib().orc_lag_weight(int(k), int(ell), int(lag), int(t)))
+
+
 def coupled_run(k, ell, horizon, seed=1, step_limit=10_000_000, slot_offset=0, instance=0,
-                meeting_cap=0) -> Run:
+                meeting_cap=0, lag=1) -> Run:
     return Run(k=k, ell=ell, burn=0, length=1, horizon=horizon, step_limit=step_limit, seed=seed,
-               slot_offset=slot_offset, instance=instance, coupled=1, meeting_cap=meeting_cap)
+               slot_offset=slot_offset, instance=instance, coupled=1, meeting_cap=meeting_cap, lag=lag)
 
 
 def uncoupled_run(burn, length, horizon, seed=1, slot_offset=0, instance=0) -> Run:
@@ -231,10 +238,10 @@ def uncoupled_run(burn, length, horizon, seed=1, slot_offset=0, instance=0) -> R
 
 def decode(inst, P, k, ell, horizon, seed=1, threads=None, n_active=0, scan=SCAN_SCORE,
            custom_w=None, init_marginals=None, per_slot=False, slot_G=False, coupled=True,
-           burn=0, length=1, slot_offset=0, instance=0, step_limit=10_000_000, meeting_cap=0):
+           burn=0, length=1, slot_offset=0, instance=0, step_limit=10_000_000, meeting_cap=0, lag=1):
     """Whole decode on the CPU: per-clone theta_CT estimates and standard errors (active order)."""
     M = Model(inst, n_active=n_active, scan=scan, custom_w=custom_w, init_marginals=init_marginals)
-    run = (coupled_run(k, ell, horizon, seed, step_limit, slot_offset, instance, meeting_cap) if coupled
+    run = (coupled_run(k, ell, horizon, seed, step_limit, slot_offset, instance, meeting_cap, lag) if coupled
            else uncoupled_run(burn, length, horizon, seed, slot_offset, instance))
     res = M.run_slots(run, 0, P, threads or os.cpu_count() or 1, per_slot=per_slot, slot_G=slot_G)
     L = (ell - k + 1) if coupled else length

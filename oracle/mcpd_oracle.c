@@ -378,7 +378,8 @@ typedef struct orc_run {
     int32_t instance;
     int32_t coupled;         /* 1: Algorithms 3 and 4; 0: Algorithm 1 / 2 per replication */
     int32_t pad;
-    int64_t meeting_cap;     /* > 0 (coupled, >= max(l, 1)): stop an unmet pair at t = cap */
+    int64_t meeting_cap;     /* > 0 (coupled, >= max(l, L, 1)): stop an unmet pair at t = cap */
+    int64_t lag;             /* L >= 1 of the lagged pair (0 reads as 1) */
 } orc_run;
 
 /* Draw (I_t, U_t) for time t of replication rep in slot `slot`. */
@@ -413,23 +414,40 @@ typedef struct rep_result {
     int32_t capped;          /* stopped at the meeting cap before meeting (tau = 0) */
 } rep_result;
 
-/* One coupled replication (Algorithm 3), run until t >= l and X_t = Y_{t-1}, or, with a meeting
- * cap c, until t = c if the pair has not met by then (C = c, tau reported as 0).
- * The estimator G_j = L * H_{k:l}(h_j), L = l - k + 1, is accumulated in one of two ways:
- *   literal = 1: store the paths and evaluate H_r = X_r + sum_{s>=1} (X_{r+s} - Y_{r+s-1}) for
- *                each r in k..l (terms with r + s > C vanish by faithfulness, since C >= tau);
+/* Weight of X_t and of Y_t in G = L H_{k:l} once the sums over r and j are swapped: the number of
+ * window indices r in k..l with r <= t and r = t (mod lag), i.e. of j >= 0 with
+ * k <= t - j lag <= min(l, t).  For lag 1 it is min(max(t - k + 1, 0), L). */
+static int64_t lag_weight(int64_t k, int64_t ell, int64_t lag, int64_t t) {
+    if (t < k) return 0;
+    int64_t hi = t < ell ? t : ell;
+    int64_t jmax = (t - k) / lag;                     /* t - j lag >= k */
+    int64_t jmin = (t - hi + lag - 1) / lag;          /* t - j lag <= hi (ceiling) */
+    return jmax >= jmin ? jmax - jmin + 1 : 0;
+}
+
+/* One coupled replication with lag L >= 1 (Algorithm 3 and the lag coupling of the supplement for
+ * L = 1; for L > 1 the lag-L coupling of Jacob, O'Leary and Atchade (2020) that the paper's
+ * time-averaged estimator is taken from).  X_0 = Y_0 = Z_0; the pre-lag updates
+ * X_{t+1} = Phi_{I_t}(X_t, U_t), t = 0..L-1, move X alone; for t >= L the common (I_t, U_t) give
+ * X_{t+1} = Phi_{I_t}(X_t, U_t) and Y_{t+1-L} = Phi_{I_t}(Y_{t-L}, U_t).  The meeting time is
+ * tau = inf{t >= L : X_t = Y_{t-L}}, and the replication runs until t >= l and the pair has met,
+ * or, with a meeting cap c, until t = c if the pair has not met by then (C = c, tau reported 0).
+ * The estimator G_j = L_w H_{k:l}(h_j), L_w = l - k + 1, is accumulated in one of two ways:
+ *   literal = 1: store the paths and evaluate H_r = X_r + sum_{j>=1} (X_{r+jL} - Y_{r+(j-1)L}) for
+ *                each r in k..l, over the terms with r + jL <= C (the others vanish by
+ *                faithfulness, since C >= tau; a capped pair keeps exactly these terms);
  *   literal = 0: the same double sum with the order of summation swapped, accumulated as the
- *                paths are produced:  G_j = sum_{r=k}^{l} X_r[j]
- *                                         + sum_{t=k+1}^{C} min(t - k, L) (X_t[j] - Y_{t-1}[j]),
- *                because exactly min(t-k, L) window indices r in k..l satisfy r < t.
- * A capped pair keeps exactly the terms with r + s <= C = c, in both forms.
- * trajX / trajY (optional, literal mode or tests) receive X_0..X_C and Y_0..Y_{C-1}; sites the
+ *                paths are produced: G_j = sum_{t=0}^{C} w(t) X_t[j] - sum_{u=0}^{C-L} w(u) Y_u[j]
+ *                with w = lag_weight (X_t enters H_r for the r = t - jL, j >= 0, in the window;
+ *                Y_u for the r = u - (j-1)L, j >= 1).
+ * trajX / trajY (optional, literal mode or tests) receive X_0..X_C and Y_0..Y_{C-L}; sites the
  * drawn I_0..I_{C-1}. */
 static rep_result coupled_replication(const orc_model *M, const orc_run *R, uint32_t slot,
                                       uint32_t rep, int64_t *G, int literal, uint8_t *trajX,
                                       uint8_t *trajY, int32_t *sites, int64_t traj_cap) {
     const int32_t na = M->na;
-    const int64_t k = R->k, ell = R->ell, L = R->ell - R->k + 1;
+    const int64_t k = R->k, ell = R->ell;
+    const int64_t lag = R->lag > 0 ? R->lag : 1;
     rep_result res = {0, 0, 0, ORC_OK, 0};
     uint8_t *X = (uint8_t *)malloc((size_t)na), *Y = (uint8_t *)malloc((size_t)na);
     initial_state(M, R, slot, rep, X);
@@ -448,46 +466,42 @@ static rep_result coupled_replication(const orc_model *M, const orc_run *R, uint
 #define KEEP_Y(tt) do { if (store && (tt) < cap) memcpy(PY + (size_t)(tt) * na, Y, (size_t)na); } while (0)
     KEEP_X(0);
     KEEP_Y(0);
-    if (!literal && k == 0 && ell >= 0)
-        for (int32_t a = 0; a < na; ++a) G[a] += X[a];           /* r = 0 term of the window */
-    /* Pre-lag update X_1 = Phi_{I_0}(X_0, U_0). */
+    /* X_0 and Y_0 enter with the same weight and are equal: G starts at 0. */
     int32_t I;
     uint64_t U;
-    step_draw(M, R, slot, rep, 0, &I, &U);
-    if (sites && 0 < cap) sites[0] = I;
-    orc_phi(M, X, I, U);
-    int64_t t = 1;
-    res.draws = 1;
-    KEEP_X(1);
-    int met = memcmp(X, Y, (size_t)na) == 0;                     /* X_1 = Y_0 ? */
-    res.tau = met ? 1 : 0;
-    if (!literal) {
-        for (int32_t a = 0; a < na; ++a) {
-            if (k <= 1 && 1 <= ell) G[a] += X[a];
-            if (1 >= k + 1) G[a] += (1 - k < L ? 1 - k : L) * ((int64_t)X[a] - (int64_t)Y[a]);
+    int64_t t = 0;
+    for (; t < lag; ++t) {                                     /* pre-lag: X alone */
+        step_draw(M, R, slot, rep, t, &I, &U);
+        if (sites && t < cap) sites[t] = I;
+        orc_phi(M, X, I, U);
+        res.draws += 1;
+        KEEP_X(t + 1);
+        if (!literal) {
+            int64_t wx = lag_weight(k, ell, lag, t + 1);
+            for (int32_t a = 0; a < na; ++a) G[a] += wx * (int64_t)X[a];
         }
     }
+    int met = memcmp(X, Y, (size_t)na) == 0;                     /* X_L = Y_0 ? */
+    res.tau = met ? lag : 0;
     while (t < ell || !met) {
         if (R->meeting_cap > 0 && t >= R->meeting_cap) { res.capped = 1; break; }   /* t >= l: unmet */
         if (R->step_limit > 0 && t >= R->step_limit) { res.status = ORC_ESTEP_LIMIT; break; }
         step_draw(M, R, slot, rep, t, &I, &U);
         if (sites && t < cap) sites[t] = I;
-        /* X_{t+1} = Phi_{I_t}(X_t, U_t) and Y_t = Phi_{I_t}(Y_{t-1}, U_t) with common (I_t, U_t). */
+        /* X_{t+1} = Phi_{I_t}(X_t, U_t) and Y_{t+1-L} = Phi_{I_t}(Y_{t-L}, U_t), common (I_t, U_t). */
         orc_phi(M, X, I, U);
         orc_phi(M, Y, I, U);
         t += 1;
         res.draws += 1;
         KEEP_X(t);
-        KEEP_Y(t - 1);
-        int eq = memcmp(X, Y, (size_t)na) == 0;                  /* X_t = Y_{t-1} ? */
+        KEEP_Y(t - lag);
+        int eq = memcmp(X, Y, (size_t)na) == 0;                  /* X_t = Y_{t-L} ? */
         if (met && !eq) res.status = ORC_EFAITHFUL;              /* Theorem 1(d) violated */
         if (!met && eq) res.tau = t;
         met = eq;
         if (!literal) {
-            for (int32_t a = 0; a < na; ++a) {
-                if (k <= t && t <= ell) G[a] += X[a];
-                if (t >= k + 1) G[a] += (t - k < L ? t - k : L) * ((int64_t)X[a] - (int64_t)Y[a]);
-            }
+            int64_t wx = lag_weight(k, ell, lag, t), wy = lag_weight(k, ell, lag, t - lag);
+            for (int32_t a = 0; a < na; ++a) G[a] += wx * (int64_t)X[a] - wy * (int64_t)Y[a];
         }
     }
     res.C = t;                                     /* C = max(l, tau), or the cap if capped */
@@ -498,8 +512,9 @@ static rep_result coupled_replication(const orc_model *M, const orc_run *R, uint
             for (int64_t r = k; r <= ell; ++r) {
                 for (int32_t a = 0; a < na; ++a) {
                     int64_t h = PX[(size_t)r * na + a];
-                    for (int64_t s = 1; r + s <= C; ++s)
-                        h += (int64_t)PX[(size_t)(r + s) * na + a] - (int64_t)PY[(size_t)(r + s - 1) * na + a];
+                    for (int64_t j = 1; r + j * lag <= C; ++j)
+                        h += (int64_t)PX[(size_t)(r + j * lag) * na + a] -
+                             (int64_t)PY[(size_t)(r + (j - 1) * lag) * na + a];
                     G[a] += h;
                 }
             }
@@ -536,10 +551,11 @@ static rep_result uncoupled_replication(const orc_model *M, const orc_run *R, ui
     return res;
 }
 
-/* Number of N*_p buckets: every retained replication costs at least max(l, 1) (coupled) or
+/* Number of N*_p buckets: every retained replication costs at least max(l, L) (coupled) or
  * b + T - 1 (uncoupled) progress units, so 1 <= N*_p <= max(1, B / that). */
 int64_t orc_num_buckets(const orc_run *R) {
-    int64_t unit = R->coupled ? (R->ell > 1 ? R->ell : 1) : (R->burn + R->length - 1);
+    int64_t lag = R->lag > 1 ? R->lag : 1;
+    int64_t unit = R->coupled ? (R->ell > lag ? R->ell : lag) : (R->burn + R->length - 1);
     if (unit < 1) unit = 1;
     int64_t nb = R->horizon / unit;
     return nb < 1 ? 1 : nb;
@@ -645,7 +661,9 @@ int orc_run_slots(const orc_model *M, const orc_run *R, int64_t p_begin, int64_t
                   int32_t *slot_nstar, int64_t *slot_S, int32_t *slot_reps, int64_t *slot_G,
                   int64_t stats[7]) {
     if (R->coupled && (R->k < 0 || R->k > R->ell)) return ORC_EINVAL;
-    if (R->coupled && R->meeting_cap != 0 && R->meeting_cap < (R->ell > 1 ? R->ell : 1)) return ORC_EINVAL;
+    if (R->coupled && (R->lag < 0 || R->lag > (int64_t)1 << 20)) return ORC_EINVAL;
+    if (R->coupled && R->meeting_cap != 0 &&
+        (R->meeting_cap < R->ell || R->meeting_cap < (R->lag > 1 ? R->lag : 1))) return ORC_EINVAL;
     if (!R->coupled && (R->burn < 0 || R->length < 1 || R->burn + R->length < 2)) return ORC_EINVAL;
     if (R->horizon < 0 || p_end < p_begin) return ORC_EINVAL;
     const int32_t na = M->na;
@@ -691,6 +709,9 @@ int orc_run_slots(const orc_model *M, const orc_run *R, int64_t p_begin, int64_t
     free(jobs); free(tid);
     return status;
 }
+
+/* The swapped-sum weight of X_t and Y_t (tests). */
+int64_t orc_lag_weight(int64_t k, int64_t ell, int64_t lag, int64_t t) { return lag_weight(k, ell, lag, t); }
 
 /* One replication with its paths, for tests of the coupling and of the estimator identity. */
 int orc_replication(const orc_model *M, const orc_run *R, int64_t p, int32_t rep, int32_t literal,

@@ -496,3 +496,84 @@ def test_multithreaded_and_partitioned_runs_are_identical(oracle_lib):
         assert np.array_equal(a[key], b[key])
     assert np.array_equal(a["S1"], c1["S1"] + c2["S1"])
     assert np.array_equal(a["count"], c1["count"] + c2["count"])
+
+
+# ---------------------------------------------------------------------------------------------
+# Lag-L coupling (Jacob, O'Leary and Atchade 2020; the paper's estimator is the case L = 1).
+
+def test_lag_weight_counts_window_indices(oracle_lib):
+    """w(t) = #{r in k..l : r <= t, r = t mod L}, by brute-force enumeration of (r, j)."""
+    for k, ell in [(0, 0), (3, 20), (5, 5), (2, 11), (7, 40)]:
+        for lag in (1, 2, 3, 5, 8):
+            for t in range(0, 70):
+                brute = sum(1 for r in range(k, ell + 1) for j in range(0, 70) if r + j * lag == t)
+                assert oracle_lib.lag_weight(k, ell, lag, t) == brute, (k, ell, lag, t)
+
+
+@pytest.mark.parametrize("lag", [2, 3, 7])
+@pytest.mark.parametrize("cap", [0, 26])
+def test_lag_literal_definition_equals_swapped_sum(oracle_lib, lag, cap):
+    """The lag-L estimator from the literal H_r = X_r + sum_j (X_{r+jL} - Y_{r+(j-1)L}) equals the
+    swapped-sum form, uncapped and capped."""
+    inst = _inst(20, 8, 3, 2, 0.05, 0.1, 0.03)
+    M = oracle_lib.Model(inst)
+    run = oracle_lib.coupled_run(3, 20, 0, seed=17, step_limit=200000, meeting_cap=cap, lag=lag)
+    for slot in range(50):
+        a = M.replication(run, slot, 0, literal=True)
+        b = M.replication(run, slot, 0, literal=False)
+        assert a["status"] == 0 and b["status"] == 0
+        assert (a["C"], a["tau"], a["capped"]) == (b["C"], b["tau"], b["capped"])
+        assert np.array_equal(a["G"], b["G"])
+
+
+@pytest.mark.parametrize("lag", [2, 5])
+def test_lag_coupling_invariants(oracle_lib, lag):
+    """X's path does not depend on the lag (X_{t+1} = Phi_{I_t}(X_t, U_t) for every t); faithfulness
+    X_t = Y_{t-L} for t >= tau, tau the first such t >= L; C = max(l, tau); if tau <= k + L every
+    correction term vanishes and G is the plain window sum of X."""
+    inst = _inst(20, 8, 3, 2, 0.05, 0.1, 0.03)
+    M = oracle_lib.Model(inst)
+    k, ell = 3, 20
+    one = oracle_lib.coupled_run(k, ell, 0, seed=7, step_limit=200000)
+    lagged = oracle_lib.coupled_run(k, ell, 0, seed=7, step_limit=200000, lag=lag)
+    saw_late = saw_early = False
+    for slot in range(60):
+        a = M.replication(one, slot, 0, traj_cap=5000)
+        r = M.replication(lagged, slot, 0, traj_cap=5000)
+        C, tau, X, Y = r["C"], r["tau"], r["X"], r["Y"]
+        n = min(C, a["C"]) + 1
+        assert np.array_equal(X[:n], a["X"][:n])
+        assert r["draws"] == C == max(ell, tau) and tau >= lag
+        eq = [np.array_equal(X[t], Y[t - lag]) for t in range(lag, C + 1)]
+        assert eq.index(True) + lag == tau and all(eq[tau - lag:])
+        assert np.array_equal(X[0], Y[0])
+        saw_late |= tau > ell
+        if tau <= k + lag:
+            saw_early = True
+            assert np.array_equal(r["G"], X[k:ell + 1].sum(axis=0).astype(np.int64))
+    assert saw_late and saw_early
+
+
+@pytest.mark.parametrize("lag", [2, 5])
+def test_lag_estimator_unbiased(oracle_lib, lag):
+    """The lag-L estimator is unbiased too (the telescoping argument holds for any L): z-tests
+    against the 2^20 enumeration, Bonferroni over the 20 clones."""
+    inst = _noisy()
+    _, p = exact.posterior(inst)
+    res = oracle_lib.decode(inst, 120000, 3, 20, 0, seed=37 + lag, lag=lag)
+    assert res["status"] == 0
+    z = _z_scores(res["est"], res["se"], p)
+    assert z.max() < 4.5, z
+
+
+def test_lag_changes_the_estimates_and_the_cost(oracle_lib):
+    """L = 1 and L = 3 draw the same X path but pair it with different Y times: the sums differ,
+    every replication costs at least max(l, L), and a cap below L is rejected."""
+    inst = _inst(20, 8, 3, 2, 0.05, 0.1, 0.03)
+    M = oracle_lib.Model(inst)
+    a = M.run_slots(oracle_lib.coupled_run(3, 4, 0, seed=13), 0, 400, per_slot=True)
+    b = M.run_slots(oracle_lib.coupled_run(3, 4, 0, seed=13, lag=6), 0, 400, per_slot=True)
+    assert not np.array_equal(a["S1"], b["S1"])
+    assert b["slot_S"].min() >= 6 and a["slot_S"].min() >= 4
+    bad = M.run_slots(oracle_lib.coupled_run(3, 4, 0, seed=13, lag=6, meeting_cap=5), 0, 10)
+    assert bad["status"] == oracle_lib.ORC_EINVAL
