@@ -89,13 +89,27 @@ typedef struct mcpd_params {
     int64_t tau_audit;         /* > 0 (coupled): count completed replications whose meeting time
                                   tau exceeds this many progress units, the pairs a finite meeting
                                   cap at that length would have stopped (the run stays uncapped)  */
+    int64_t meeting_cap;       /* > 0 (coupled, >= max(l, 1)): the finite meeting cap of the
+                                  paper's runs.  A pair that has not met when its clock t reaches
+                                  the cap stops there and is kept as completed at C = cap, every
+                                  inner sum of its H_{k:l} cut at C (terms X_{r+s} - Y_{r+s-1}
+                                  with r + s <= C).  The cap replaces step_limit; tau_audit
+                                  defaults to the cap, so tau_over_audit counts the capped pairs
+                                  (tau_audit, if set, must not exceed the cap).  0: uncapped      */
+    int64_t lag;               /* coupled lag L (0 or 1: the paper's one-lag pair).  L > 1: the
+                                  lag-L pair of Jacob, O'Leary and Atchade (2020): L pre-lag
+                                  updates of X alone, then (I_t, U_t) moves X_{t+1} and Y_{t+1-L};
+                                  tau = inf{t >= L : X_t = Y_{t-L}} and
+                                  H_r = X_r + sum_{j>=1} (X_{r+jL} - Y_{r+(j-1)L}).  Every
+                                  replication costs max(l, tau) >= max(l, L).  At most 2^20      */
 } mcpd_params;
 
-/* Counters of one run. */
+/* Counters of one run.  site_updates, reps_started, reps_retained and tau_over_audit are -1 if a
+ * pair ran 2^32 or more progress units in one launch (this build keeps them in 32-bit halves). */
 typedef struct mcpd_stats {
     int64_t progress_units;    /* shared draws executed, aborted replications included            */
-    int64_t site_updates;      /* single-site updates executed (2 per coupled draw but the
-                                  pre-lag one, 1 per uncoupled draw)                              */
+    int64_t site_updates;      /* single-site updates executed (2 per coupled draw but the L
+                                  pre-lag ones of each replication, 1 per uncoupled draw)         */
     int64_t reps_started, reps_retained, reps_aborted;
     int64_t zero_completion_slots;  /* slots with N_p(B) = 0 (first replication kept)             */
     int64_t step_limit_hits;
@@ -103,7 +117,7 @@ typedef struct mcpd_stats {
     int64_t n_buckets;         /* number of N*_p values the integer sums are kept for             */
     int64_t n_active;
     double kernel_ms;          /* device time of the sampling kernel (CUDA events)                */
-    int64_t tau_over_audit;    /* completed replications with tau > params.tau_audit              */
+    int64_t tau_over_audit;    /* completed replications with tau > params.tau_audit             */
 } mcpd_stats;
 
 typedef struct mcpd_ctx mcpd_ctx;

@@ -164,6 +164,8 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     kp.dummy_word_index = t.dummy_word_index; kp.coupled = t.coupled ? 1 : 0;
     kp.P = t.P; kp.B = t.B; kp.k = t.k; kp.ell = t.ell; kp.L = t.L; kp.burn = t.burn;
     kp.length = t.length; kp.unit = t.unit; kp.step_limit = t.step_limit; kp.tau_audit = t.tau_audit;
+    kp.capped = t.capped ? 1 : 0;
+    kp.lag = static_cast<int32_t>(t.lag);
     kp.slot_offset = t.slot_offset; kp.trace_stride = t.trace_stride;
     kp.seed = t.seed; mcpd::philox_round_keys(t.seed, kp.rk); kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
@@ -240,17 +242,7 @@ int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *pl, mcpd_stats *stats) {
     CU(cudaEventElapsedTime(&ms, pl->ev0, pl->ev1));
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
-        stats->progress_units = static_cast<int64_t>(c[mcpd::kProgress]);
-        stats->reps_started = static_cast<int64_t>(c[mcpd::kRepsStarted]);
-        stats->reps_retained = static_cast<int64_t>(c[mcpd::kRepsRetained]);
-        stats->reps_aborted = static_cast<int64_t>(c[mcpd::kRepsAborted]);
-        stats->zero_completion_slots = static_cast<int64_t>(c[mcpd::kZeroCompletion]);
-        stats->step_limit_hits = static_cast<int64_t>(c[mcpd::kStepLimitHits]);
-        stats->max_tau = static_cast<int64_t>(c[mcpd::kMaxTau]);
-        stats->sum_tau = static_cast<int64_t>(c[mcpd::kSumTau]);
-        stats->tau_over_audit = static_cast<int64_t>(c[mcpd::kTauOverAudit]);
-        stats->site_updates = pl->t.coupled ? 2 * stats->progress_units - stats->reps_started
-                                            : stats->progress_units;
+        mcpd::counters_to_stats(c, stats);
         stats->n_buckets = pl->t.nb;
         stats->n_active = pl->t.na;
         stats->kernel_ms = ms;
@@ -650,10 +642,13 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         d.dummy_word_index = t.dummy_word_index; d.dummy_entry = t.dummy_entry; d.dummy_word = t.dummy_word;
         d.P = t.P; d.B = t.B; d.k = t.k; d.ell = t.ell; d.L = t.L; d.burn = t.burn; d.length = t.length;
         d.unit = t.unit; d.step_limit = t.step_limit; d.slot_offset = t.slot_offset; d.tau_audit = t.tau_audit;
+        d.capped = t.capped ? 1 : 0;
+        d.lag = static_cast<int32_t>(t.lag);
         d.work_begin = work; work += t.P;
         d.seed = t.seed; d.instance = t.instance;
         mcpd::BParams &bp = c.bp;
         bp.total_work = work;
+        if (t.capped || t.lag > 1) bp.ext = 1;
         bp.max_na = std::max(bp.max_na, t.na); bp.max_W = std::max(bp.max_W, t.W);
         bp.max_wpp = std::max(bp.max_wpp, t.wpp); bp.max_m = std::max(bp.max_m, t.m);
     }
@@ -773,16 +768,7 @@ int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *b, mcpd_stats *stats) {
     CU(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
-        stats->progress_units = static_cast<int64_t>(c[mcpd::kProgress]);
-        stats->reps_started = static_cast<int64_t>(c[mcpd::kRepsStarted]);
-        stats->reps_retained = static_cast<int64_t>(c[mcpd::kRepsRetained]);
-        stats->reps_aborted = static_cast<int64_t>(c[mcpd::kRepsAborted]);
-        stats->zero_completion_slots = static_cast<int64_t>(c[mcpd::kZeroCompletion]);
-        stats->step_limit_hits = static_cast<int64_t>(c[mcpd::kStepLimitHits]);
-        stats->max_tau = static_cast<int64_t>(c[mcpd::kMaxTau]);
-        stats->sum_tau = static_cast<int64_t>(c[mcpd::kSumTau]);
-        stats->tau_over_audit = static_cast<int64_t>(c[mcpd::kTauOverAudit]);
-        stats->site_updates = b->coupled ? 2 * stats->progress_units - stats->reps_started : stats->progress_units;
+        mcpd::counters_to_stats(c, stats);
         stats->n_buckets = static_cast<int64_t>(b->total_counts);
         stats->n_active = b->total_active;
         stats->kernel_ms = ms;

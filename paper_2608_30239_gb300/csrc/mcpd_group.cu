@@ -48,6 +48,8 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
     int na = 0, n_init = 0;
     uint32_t W = 0, B = 0, ell = 0, step_limit = 0, instance = 0, k0 = 0, k1 = 0, gshift = 0;
     long long kk = 0, LL = 0, work_begin = 0, work_end = 0, slot_offset = 0, tau_audit = 0;
+    bool capped = false;
+    uint32_t lag = 1;
     int cur = -1;
     auto load_instance = [&](const InstDesc &d) {
         gAlias = reinterpret_cast<const unsigned long long *>(d.alias);
@@ -57,17 +59,28 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
         bS1 = d.S1; bS2lo = d.S2lo; bS2hi = d.S2hi; bCount = d.bcount;
         na = d.na; W = d.W; B = static_cast<uint32_t>(d.B); ell = static_cast<uint32_t>(d.ell);
         step_limit = static_cast<uint32_t>(d.step_limit); instance = d.instance;
-        tau_audit = d.tau_audit;
+        tau_audit = d.tau_audit; capped = d.capped != 0; lag = static_cast<uint32_t>(d.lag);
         k0 = static_cast<uint32_t>(d.seed); k1 = static_cast<uint32_t>(d.seed >> 32);
         kk = d.k; LL = d.L; slot_offset = d.slot_offset;
         work_begin = d.work_begin; work_end = d.work_begin + d.P;
         gshift = 0;
         while (((W + (1u << gshift) - 1) >> gshift) > 64) ++gshift;
     };
+    // W(u) = sum_{v<=u} w(v), w(v) the number of window indices r = v - jL (j >= 0); for L > 1,
+    // sum_{r=k}^{min(l,u)} (floor((u - r) / L) + 1) through F(n) = sum_{d=0}^{n} floor(d / L).
     auto wpre = [&](long long u) -> long long {
         if (u < kk) return 0;
-        if (u <= static_cast<long long>(ell)) { const long long a = u - kk + 1; return a * (a + 1) / 2; }
-        return LL * (LL + 1) / 2 + (u - static_cast<long long>(ell)) * LL;
+        if (lag == 1) {
+            if (u <= static_cast<long long>(ell)) { const long long a = u - kk + 1; return a * (a + 1) / 2; }
+            return LL * (LL + 1) / 2 + (u - static_cast<long long>(ell)) * LL;
+        }
+        const long long lg = lag, m = min(u, static_cast<long long>(ell));
+        auto F = [&](long long n) -> long long {
+            if (n < 0) return 0;
+            const long long q = n / lg;
+            return lg * q * (q - 1) / 2 + q * (n - q * lg + 1);
+        };
+        return (m - kk + 1) + F(u - kk) - F(u - m - 1);
     };
     auto xc = [&](int j) -> uint8_t * { return reinterpret_cast<uint8_t *>(X + W) + j; };
     auto yc = [&](int j) -> uint8_t * { return reinterpret_cast<uint8_t *>(Y + W) + j; };
@@ -82,7 +95,7 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
     uint32_t slot_local = 0, slot_g = 0, r = 0, t = 0, S = 0, N = 0, tau = 0, abort_t = 0xFFFFFFFFu;
     unsigned long long rep_words = 0, slot_words = 0;
     unsigned long long c_prog = 0, c_started = 0, c_retained = 0, c_aborted = 0, c_zero = 0,
-                       c_limit = 0, c_sumtau = 0, c_audit = 0;
+                       c_limit = 0, c_sumtau = 0, c_audit = 0, c_prelag = 0;
     uint32_t c_maxtau = 0;
 
     auto group_or64 = [&](unsigned long long v) -> unsigned long long {
@@ -95,6 +108,7 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
         t = 0; tau = 0; met = false;
         abort_t = r > 0 ? (B - S) : 0xFFFFFFFFu;
         ++c_started;
+        c_prelag += lag;
         if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i), X_0 = Y_0 = Z_0: lanes share the listed pairs
             unsigned long long mark = 0;
             for (int e = gl; e < n_init; e += G) {
@@ -146,10 +160,12 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
     };
 
     // End of a replication (cooperative over the group's lanes, one state word each).  `move`:
-    // completed, so X_C = Y_{C-1}; close the intervals (W(C) - W(C-1) per bit set in X_C) and add
-    // the replication's sums to the slot's.
-    auto finish_rep = [&](bool move, uint32_t C) {
-        const long long wX = move ? wpre(C) - wpre(static_cast<long long>(C) - 1) : 0;
+    // completed, so X_C = Y_{C-L}; close the intervals (W(C) - W(C-L) per bit set in X_C) and add
+    // the replication's sums to the slot's.  `at_cap`: completed unmet at the meeting cap C, so X's
+    // intervals close at C and Y's at C - L: +-W(C-L) more where X_C and Y_{C-L} differ.
+    auto finish_rep = [&](bool move, uint32_t C, bool at_cap = false) {
+        const long long wX = move ? wpre(C) - wpre(static_cast<long long>(C) - lag) : 0;
+        const long long wc = at_cap ? wpre(static_cast<long long>(C) - lag) : 0;
         unsigned long long groups = rep_words, slot_mark = 0;
         while (groups) {
             const int g = __ffsll(static_cast<long long>(groups)) - 1;
@@ -166,6 +182,8 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
                     long long v = 0;
                     if (tw & bit) { v = racc[j]; racc[j] = 0; }
                     if (move && (xw & bit)) v += wX;
+                    if (xw & bit) v += wc;
+                    if (yw & bit) v -= wc;
                     if (move && v != 0) {
                         atomicAdd(reinterpret_cast<unsigned long long *>(&sacc[j]), static_cast<unsigned long long>(v));
                         moved |= bit;
@@ -222,8 +240,8 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
         c_prog += C;
         c_sumtau += tau;
         c_maxtau = max(c_maxtau, tau);
-        if (tau_audit > 0 && tau > tau_audit) ++c_audit;
-        finish_rep(true, C);
+        if (tau_audit > 0 && (tau > tau_audit || tau == 0)) ++c_audit;   // tau = 0: capped
+        finish_rep(true, C, !met);
         S += C;
         N += 1;
         ++c_retained;
@@ -268,8 +286,8 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
             if (wu == thx) nX = lo < static_cast<uint32_t>(TX) ? 1u : 0u;
             if (wu == thy) nY = lo < static_cast<uint32_t>(TY) ? 1u : 0u;
         }
-        if (t == 0) nY = yI;                                    // pre-lag: X only
-        else if (!own_y) nY = nX;                               // met: Y_t = X_{t+1}
+        if (t < lag) nY = yI;                                   // pre-lag: X only, Y stays Y_0
+        else if (!own_y) nY = nX;                               // met: Y_{t+1-L} = X_{t+1}
         const uint32_t fx = nX ^ xI, fy = nY ^ yI;
         if (fx | fy) {
             if (valid) {
@@ -280,13 +298,15 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
                 if (fx) X[q] = xw ^ bit;
                 if (fy) Y[q] = yw ^ bit;
                 long long ev = 0;
-                if (t > 0 && !own_y) {                          // met: X at t+1 and Y at t together
+                if (t > 0 && !own_y) {                          // met: X at t+1 and Y at t+1-L
+                    // together (the one-lag count of window indices r <= t; on a pre-lag step X
+                    // alone, whose W(t) is the same count)
                     const long long a = static_cast<long long>(t) - kk + 1;
                     const long long w = a < 0 ? 0 : (a > LL ? LL : a);
                     ev = nX ? -w : w;
                 } else {
                     if (fx) { const long long w = wpre(t); ev += nX ? -w : w; }
-                    if (fy) { const long long w = wpre(static_cast<long long>(t) - 1); ev += nY ? w : -w; }
+                    if (fy) { const long long w = wpre(static_cast<long long>(t) - lag); ev += nY ? w : -w; }
                 }
                 if (ev != 0) {
                     atomicAdd(reinterpret_cast<unsigned long long *>(&racc[I]), static_cast<unsigned long long>(ev));
@@ -295,8 +315,8 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
             }
             rep_words |= 1ull << (q >> gshift);
             __syncwarp(gmask);
-            if (t == 0) {
-                met = false;                                    // X_1 differs from Y_0 at I
+            if (t < lag && !own_y) {
+                met = false;                                    // X_{t+1} differs from Y_0 = X_t at I
             } else if (own_y) {                                 // ballot over XOR of the bit sets
                 bool diff = false;
                 for (uint32_t w = gl; w < W; w += G) diff |= (X[w] ^ Y[w]) != 0u;
@@ -306,10 +326,11 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
             met = true;                                         // X_1 = Y_0
         }
         ++t;
-        if (met) {
+        if (met && t >= lag) {                                  // tau = inf{t >= L : X_t = Y_{t-L}}
             if (tau == 0) tau = t;
             if (t >= ell) return 1;
         }
+        if (capped && t >= step_limit) return 1;        // unmet at the meeting cap: completed (C = t)
         if (t >= abort_t) return 2;
         return t >= step_limit ? 3 : 0;
     };
@@ -341,6 +362,7 @@ __global__ void __launch_bounds__(768, 1) group_kernel(const BParams bp) {
     if (gl == 0) {
         if (c_prog) atomicAdd(&bp.counters[kProgress], c_prog);
         if (c_started) atomicAdd(&bp.counters[kRepsStarted], c_started);
+        if (c_prog) atomicAdd(&bp.counters[kSiteUpdates], 2 * c_prog - c_prelag);
         if (c_retained) atomicAdd(&bp.counters[kRepsRetained], c_retained);
         if (c_aborted) atomicAdd(&bp.counters[kRepsAborted], c_aborted);
         if (c_zero) atomicAdd(&bp.counters[kZeroCompletion], c_zero);

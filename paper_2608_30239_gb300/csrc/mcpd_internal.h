@@ -33,13 +33,13 @@ constexpr int64_t kMaxBuckets = 1 << 16;
 // Counter slots of the device statistics block.
 enum Counter {
     kWork = 0, kProgress, kSiteUpdates, kRepsStarted, kRepsRetained, kRepsAborted,
-    kZeroCompletion, kStepLimitHits, kMaxTau, kSumTau, kTauOverAudit, kNumCounters = 16
+    kZeroCompletion, kStepLimitHits, kMaxTau, kSumTau, kTauOverAudit, kPackLost, kNumCounters = 16
 };
 
 // Per-pair statistics record of the one-thread-per-pair kernel, summed into the counters at exit.
 enum PairStat {
     kPsProgress = 0, kPsStarted, kPsRetained, kPsAborted, kPsZero, kPsLimit, kPsSumTau, kPsMaxTau,
-    kPsTauAudit, kPairStats = 9
+    kPsTauAudit, kPsSiteUpdates, kPairStats = 10
 };
 
 // Per-pair scratch, one contiguous block of 8-byte words per pair: the replication's sums G
@@ -76,6 +76,8 @@ struct Tables {
     // run shape
     int64_t k = 0, ell = 0, L = 0, burn = 0, length = 0, unit = 1;
     int64_t P = 0, B = 0, nb = 1, step_limit = 0, slot_offset = 0, trace_stride = 0, tau_audit = 0;
+    bool capped = false;              // meeting cap: step_limit is the cap, a capped pair is kept
+    int64_t lag = 1;                  // coupled lag L
     uint64_t seed = 0;
     uint32_t instance = 0;
     bool record_slots = false;
@@ -83,6 +85,22 @@ struct Tables {
 
 int build_tables(const mcpd_design *design, const uint8_t *y, const mcpd_params *params,
                  Tables *out, std::string *err);
+
+// The run's counters (summed over launches) as mcpd_stats; n_buckets, n_active and kernel_ms are
+// the caller's.
+inline void counters_to_stats(const unsigned long long *c, mcpd_stats *s) {
+    const bool lost = c[kPackLost] != 0;
+    s->progress_units = static_cast<int64_t>(c[kProgress]);
+    s->site_updates = lost ? -1 : static_cast<int64_t>(c[kSiteUpdates]);
+    s->reps_started = lost ? -1 : static_cast<int64_t>(c[kRepsStarted]);
+    s->reps_retained = lost ? -1 : static_cast<int64_t>(c[kRepsRetained]);
+    s->reps_aborted = static_cast<int64_t>(c[kRepsAborted]);
+    s->zero_completion_slots = static_cast<int64_t>(c[kZeroCompletion]);
+    s->step_limit_hits = static_cast<int64_t>(c[kStepLimitHits]);
+    s->max_tau = static_cast<int64_t>(c[kMaxTau]);
+    s->sum_tau = static_cast<int64_t>(c[kSumTau]);
+    s->tau_over_audit = lost ? -1 : static_cast<int64_t>(c[kTauOverAudit]);
+}
 
 // The rows and thresholds the single-instance kernel stages (mask-indexed when available).
 inline const std::vector<uint16_t> &kernel_rows(const Tables &t) { return t.rows_mask.empty() ? t.rows : t.rows_mask; }
@@ -112,7 +130,7 @@ struct KParams {
     int32_t *slot_reps;
     long long *trace_G;
     int32_t na, m, W, Mp, wpp, deg, nb, scan;
-    int32_t udeg, pad1;               // uniform degree (0: mixed)
+    int32_t udeg, capped;             // uniform degree (0: mixed); 1: the step limit is a meeting cap
     uint32_t dummy_entry, dummy_word;
     int32_t dummy_word_index, coupled;
     long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset, trace_stride, tau_audit;
@@ -123,6 +141,7 @@ struct KParams {
     int32_t y_regions;                // 32-column Y regions in shared memory
     uint32_t rk[20];                  // Philox round keys of the seed
     int32_t nT;                       // threshold entries staged (kTSide^2, or mask-indexed)
+    int32_t lag;                      // coupled lag L >= 1
 };
 
 // Philox4x32-10 round keys of a 64-bit seed: (lo + i 0x9E3779B9, hi + i 0xBB67AE85), i = 0..9.
@@ -145,14 +164,14 @@ struct InstDesc {
     const uint32_t *init_pairs;       // [n_init_pairs] even clone ids with a nonzero threshold
     const uint16_t *rows_pool;        // [na * kRow] pool id | y << 15 (lane-group kernels)
     unsigned long long *S1, *S2lo, *S2hi, *bcount;   // this instance's N*_p buckets
-    int32_t n_init_pairs, pad0;
+    int32_t n_init_pairs, capped;     // capped: the step limit is a meeting cap
     int32_t na, W, wpp, deg, nb, dummy_word_index;
     uint32_t dummy_entry, dummy_word;
     long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset, tau_audit;
     long long work_begin;             // global index of this instance's first slot in the launch
     unsigned long long seed;
     uint32_t instance;
-    int32_t pad;
+    int32_t lag;                      // coupled lag L >= 1
 };
 
 // Arguments of a batched launch.
@@ -168,6 +187,7 @@ struct BParams {
     int32_t max_na, max_W;
     int32_t y_regions;                // 32-column Y regions in shared memory
     int32_t wide;                     // launch the 20-warp variant of the batch kernel
+    int32_t ext;                      // some instance has a meeting cap or a lag > 1
 };
 
 // Launch shape of the one-thread-per-pair kernel (mcpd_kernels.cu).

@@ -49,7 +49,9 @@ namespace {
 // except, for DEG = 0, the padding pool's count.
 // WIDE (batches only): compiled for 20 warps per block (96 registers) rather than 12 (up to 168),
 // for size classes whose pair state leaves room for more than 12 warps.
-template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG, bool WIDE = false>
+// EXT: the meeting cap and lags L > 1 (runs that use neither launch the variant without them, whose
+// hot loop the completion path's code would otherwise perturb).
+template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG, bool WIDE = false, bool EXT = false>
 __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 : 512), 1) pairs_kernel(const KParams p, const BParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -120,6 +122,16 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     MCPD_FIELD(v_unit, static_cast<uint32_t>(__ldg(&desc()->unit)), static_cast<uint32_t>(p.unit));
     MCPD_FIELD(v_step_limit, static_cast<uint32_t>(__ldg(&desc()->step_limit)), static_cast<uint32_t>(p.step_limit));
     MCPD_FIELD(v_tau_audit, __ldg(&desc()->tau_audit), p.tau_audit);
+    auto v_capped = [&]() -> bool {
+        if constexpr (!EXT) return false;
+        else if constexpr (BATCH) return __ldg(&desc()->capped) != 0;
+        else return p.capped != 0;
+    };
+    auto v_lag = [&]() -> uint32_t {
+        if constexpr (!EXT) return 1u;
+        else if constexpr (BATCH) return static_cast<uint32_t>(__ldg(&desc()->lag));
+        else return static_cast<uint32_t>(p.lag);
+    };
     MCPD_FIELD(v_k, __ldg(&desc()->k), p.k);
     MCPD_FIELD(v_L, __ldg(&desc()->L), p.L);
     MCPD_FIELD(v_burn, __ldg(&desc()->burn), p.burn);
@@ -189,12 +201,25 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         return l < NE && (DEG > 0 || (l < deg && ent[l] != dummy_entry));
     };
     // Prefix sums of the estimator's per-time weights (see the comment on wprefix).
+    // Lag L > 1: W(u) = sum_{r=k}^{min(l,u)} (floor((u - r) / L) + 1), the weight of X_t and Y_t
+    // being the number of window indices r = t - jL (j >= 0); with F(n) = sum_{d=0}^{n} floor(d / L)
+    // = L q (q - 1) / 2 + q (n - q L + 1), q = floor(n / L), the floor sum is F(u - k) - F(u - m - 1).
     auto wpre = [&](long long u) -> long long {
         if (COUPLED) {
             const long long kk = v_k(), LL = v_L();
             if (u < kk) return 0;
-            if (u <= static_cast<long long>(ell)) { const long long a = u - kk + 1; return a * (a + 1) / 2; }
-            return LL * (LL + 1) / 2 + (u - static_cast<long long>(ell)) * LL;
+            const long long lg = v_lag();
+            if (lg == 1) {
+                if (u <= static_cast<long long>(ell)) { const long long a = u - kk + 1; return a * (a + 1) / 2; }
+                return LL * (LL + 1) / 2 + (u - static_cast<long long>(ell)) * LL;
+            }
+            const long long m = min(u, static_cast<long long>(ell));
+            auto F = [&](long long n) -> long long {
+                if (n < 0) return 0;
+                const long long q = n / lg;
+                return lg * q * (q - 1) / 2 + q * (n - q * lg + 1);
+            };
+            return (m - kk + 1) + F(u - kk) - F(u - m - 1);
         } else {
             const long long v = u - v_burn() + 1, length = v_length();
             return v < 0 ? 0 : (v > length ? length : v);
@@ -276,13 +301,17 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         }
     };
 
+    // A batched pair keeps the pre-lag updates of its replications (sum of L) in the high half of
+    // the started record, split at exit; one instance needs only the count.
     auto start_rep = [&]() {
-        t = 0; D = 0; tau = 1; sysI = 0;      // tau = 1 unless the pre-lag update moves X
+        const uint32_t lag = v_lag();
+        t = 0; D = 0; tau = lag; sysI = 0;    // tau = L unless a pre-lag update moves X
         const uint32_t step_limit = v_step_limit();
         abort_t = (COUPLED && r > 0) ? (v_B() - S) : 0xFFFFFFFFu;
         stop_unmet = min(abort_t, step_limit);
-        t_end = COUPLED ? min(max(ell, 1u), stop_unmet) : min(v_unit(), step_limit);
-        red_add(reinterpret_cast<long long *>(&pst()[kPsStarted]), 1);
+        t_end = COUPLED ? min(max(ell, lag), stop_unmet) : min(v_unit(), step_limit);
+        red_add(reinterpret_cast<long long *>(&pst()[kPsStarted]),
+                BATCH && COUPLED && EXT ? 1 + (static_cast<long long>(lag) << 32) : 1ll);
         ++reps_in_slot;
         const unsigned long long *Tnu = v_Tnu();
         if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0 (clones with nu_i = 0 stay 0)
@@ -344,7 +373,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     // out of the slot's sums.
     auto finish_rep = [&](bool move, uint32_t C) {
         const long long wX = move ? static_cast<long long>(wstep(C)) : 0;
-        if (COUPLED && D != 0) release_y();
+        if (COUPLED && (EXT ? ycol != nullptr : D != 0)) release_y();
         long long *const ra = racc();
         long long *const sa = sacc();
         uint32_t groups = rep_words;
@@ -431,19 +460,52 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
 
     // Completed at C = t: every completed replication is retained (a later one that could not
     // finish within B is aborted before it completes); then refill or end the slot.
+    // Stopped unmet at the meeting cap c = t: H_{k:l} keeps the terms up to c, so X's intervals
+    // close at c (+W(c) per bit of X_c) and Y's at c - L (-W(c-L) per bit of Y_{c-L}).  The
+    // closing in finish_rep adds W(c) - W(c-L) = w1(c) per bit of X_c (w1 the one-lag weight: the
+    // window indices r <= c); the rest is +-W(c-L) at every site where X_c and Y_{c-L} differ,
+    // added here while the Y column is still held.
+    auto cap_close = [&]() {
+        const long long wc = wpre(static_cast<long long>(t) - v_lag());
+        if (wc == 0) return;
+        uint32_t groups = rep_words;          // every X and Y bit lies in a marked group
+        while (groups) {
+            const int g = __ffs(groups) - 1;
+            groups &= groups - 1;
+            const uint32_t q0 = static_cast<uint32_t>(g) << gshift, q1 = min(W, q0 + (1u << gshift));
+            for (uint32_t q = q0; q < q1; ++q) {
+                const uint32_t xw = st[q * 32];
+                uint32_t dm = xw ^ ycol[q * 32];
+                if (!dm) continue;
+                red_or(&tslot()[q], dm);
+                slot_words |= 1u << g;
+                while (dm) {
+                    const int b = __ffs(dm) - 1;
+                    dm &= dm - 1;
+                    red_add(&sacc()[q * 32 + b], ((xw >> b) & 1u) ? wc : -wc);
+                }
+            }
+        }
+    };
+
+    // The retained record's high half counts the completions whose meeting time exceeds the audit
+    // length, capped pairs (tau = 0) included (one reduction per completion, not two; split at
+    // exit).  A pair that reaches the meeting cap c = t unmet completes with C = c.
     auto complete = [&]() {
         const uint32_t C = t;
+        long long over = 0;
+        if (COUPLED && EXT && D != 0) cap_close();
         red_add(reinterpret_cast<long long *>(&pst()[kPsProgress]), C);
         if (COUPLED) {
             red_add(reinterpret_cast<long long *>(&pst()[kPsSumTau]), tau);
             red_max(&pst()[kPsMaxTau], tau);
             const long long audit = v_tau_audit();
-            if (audit > 0 && tau > audit) red_add(reinterpret_cast<long long *>(&pst()[kPsTauAudit]), 1);
+            over = (audit > 0 && (tau > audit || tau == 0u)) ? (1ll << 32) : 0ll;
         }
         finish_rep(true, C);
         S += C;
         N += 1;
-        red_add(reinterpret_cast<long long *>(&pst()[kPsRetained]), 1);
+        red_add(reinterpret_cast<long long *>(&pst()[kPsRetained]), 1 + over);
         const uint32_t B = v_B();
         if (S > B) red_add(reinterpret_cast<long long *>(&pst()[kPsZero]), 1);   // only a slot's first replication ends beyond B
         if (S < B && B - S >= v_unit()) { ++r; start_rep(); }
@@ -465,18 +527,30 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         end_slot(false);
     };
 
-    // The clock reached t_end: 1 = completed, 2 = doomed, 3 = step limit.
+    // The clock reached t_end: 0 = go on, 1 = completed (met, or unmet at the meeting cap),
+    // 2 = doomed, 3 = step limit.  A pair at the cap completes with C = t, so it is kept even when
+    // t is also the clock at which an unfinished replication is doomed (S + C = B).  With lag L > 1
+    // a pair whose X came back to Y_0 during the pre-lag updates meets at tau = L if X_L = Y_0.
     auto classify = [&]() -> int {
         if (COUPLED) {
+            if (EXT && D == 0 && ycol != nullptr) {
+                release_y();
+                tau = t;
+                t_end = min(max(ell, tau), stop_unmet);
+                if (t < t_end) return 0;
+            }
             if (D == 0 && t >= ell) return 1;
+            if (v_capped() && t >= v_step_limit()) return 1;
             return t >= abort_t ? 2 : 3;
         }
         return t >= v_unit() ? 1 : 3;
     };
 
-    // X moved at site I on a step where Y_t = X_{t+1} (met, or the pre-lag update t = 0, where
-    // Y stays at Y_0): the counts of I's pools (from the values loaded this step), the event
-    // -+w(t) and, at t = 0, the start of an unmet stretch.
+    // X moved at site I on a step where Y_{t+1-L} = X_{t+1} (met), or on a pre-lag update t < L
+    // where Y stays at Y_0 = X_t: the counts of I's pools (from the values loaded this step), the
+    // event -+w1(t), the number of window indices r <= t (after meeting, X's -+W(t) and Y's
+    // +-W(t-L) add to it; before t = L only X moves and W(t) is the same count, W(t-L) being 0)
+    // and, on a pre-lag update, the start of an unmet stretch.
     auto met_flip = [&](uint32_t I, uint32_t q, uint32_t bit, uint32_t xw, uint32_t nX,
                         const uint32_t *ent, const uint32_t *cx) {
         st[q * 32] = xw ^ bit;
@@ -492,19 +566,25 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
             red_or(&trep()[q], bit);
         }
         rep_words |= 1u << (q >> gshift);
-        if (COUPLED && t == 0) {            // X_1 differs from Y_0 in bit I
+        if (COUPLED && t < v_lag()) {       // X_{t+1} differs from Y_0 = X_t in bit I
             D = 1; tau = 0; t_end = stop_unmet;
-            acquire_y();
-            if (v_Tnu()) copy_y0(q, bit);
+            if (!EXT || ycol == nullptr) {      // first move: Y_0 = X_t to the Y column
+                acquire_y();
+                if (v_Tnu()) copy_y0(q, bit);
+            }
         }
     };
 
-    // A pair that has not met: X and Y move separately (events -+W(t) and +-W(t-1)); D follows
-    // the Hamming distance, and at D = 0 the pair has met at tau = t + 1.
+    // A pair that has not met: X and Y move separately (events -+W(t) and +-W(t-L)); D follows
+    // the Hamming distance, and at D = 0 the pair has met at tau = t + 1 if t + 1 >= L.  Before
+    // that (t < L) Y stays at Y_0, and D = 0 means X came back to Y_0: the pair goes on (met
+    // path, Y column kept) and classify decides at t = L.
     auto unmet_flip = [&](uint32_t I, uint32_t q, uint32_t bit, uint32_t xw, uint32_t yw,
                           uint32_t xI, uint32_t yI, uint32_t nX, uint32_t nY, const uint32_t *ent,
                           const uint32_t *cx, const uint32_t *cy) {
         long long ev = 0;
+        const uint32_t lag = v_lag();
+        if (EXT && t < lag) nY = yI;
         if (nX != xI) {
             st[q * 32] = xw ^ bit;
             const uint32_t delta = nX ? 1u : 0xFFu;
@@ -521,7 +601,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
 #pragma unroll
             for (int l = 0; l < kRow; ++l)
                 if (real(l, ent)) yb[ent[l] & 0x7FFFu] = static_cast<unsigned char>(cy[l] + delta);
-            const long long w = wpre(static_cast<long long>(t) - 1);
+            const long long w = wpre(static_cast<long long>(t) - lag);
             ev += nY ? w : -w;
         }
         if (ev != 0) {
@@ -532,9 +612,13 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         rep_words |= 1u << (q >> gshift);
         D = D + (nX ^ nY) - (xI ^ yI);
         if (D == 0) {
-            release_y();
-            tau = t + 1;
-            t_end = min(max(ell, tau), stop_unmet);
+            if (!EXT || t + 1 >= lag) {
+                release_y();
+                tau = t + 1;
+                t_end = min(max(ell, tau), stop_unmet);
+            } else {
+                t_end = lag;
+            }
         }
     };
 
@@ -665,9 +749,29 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         }
     }
 
+    // Split the packed records.  Started: count (low half) and, batched, the pre-lag updates (high
+    // half).  Every replication started has ended retained, aborted or at the step limit, so the
+    // retained count is started - aborted - limit and the rest of the retained record is the audit
+    // count times 2^32.  Both splits are exact while the pair ran fewer than 2^32 progress units
+    // (every replication takes at least one, and every pre-lag update is one).
+    {
+        const unsigned long long progress = __ldcg(&pst()[kPsProgress]);
+        const unsigned long long sp = __ldcg(&pst()[kPsStarted]);
+        const unsigned long long started = sp & 0xFFFFFFFFull;
+        const unsigned long long prelag = BATCH && EXT ? sp >> 32 : started * v_lag();
+        const unsigned long long packed = __ldcg(&pst()[kPsRetained]);
+        const unsigned long long kept = started - __ldcg(&pst()[kPsAborted]) - __ldcg(&pst()[kPsLimit]);
+        pst()[kPsStarted] = started;
+        pst()[kPsRetained] = kept;
+        pst()[kPsTauAudit] = (packed - kept) >> 32;
+        pst()[kPsSiteUpdates] = COUPLED ? 2 * progress - prelag : progress;
+        if (progress >> 32) atomicAdd(&counters[kPackLost], 1ull);
+    }
+
     // Every lane of the warp is here: sum (or max) the pairs' statistics over the warp.
     const int dst[kPairStats] = {kProgress, kRepsStarted, kRepsRetained, kRepsAborted,
-                                 kZeroCompletion, kStepLimitHits, kSumTau, kMaxTau, kTauOverAudit};
+                                 kZeroCompletion, kStepLimitHits, kSumTau, kMaxTau, kTauOverAudit,
+                                 kSiteUpdates};
 #pragma unroll
     for (int i = 0; i < kPairStats; ++i) {
         unsigned long long v = __ldcg(&pst()[i]);
@@ -735,12 +839,25 @@ __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uin
 
 using PairsFn = void (*)(const KParams, const BParams);
 
-PairsFn pick(int coupled, int scan, bool batch, int udeg = 0, bool wide = false) {
+PairsFn pick(int coupled, int scan, bool batch, int udeg = 0, bool wide = false, bool ext = false) {
     if (batch) {
+        if (coupled && ext)
+            return wide ? pairs_kernel<true, false, true, 0, true, true> : pairs_kernel<true, false, true, 0, false, true>;
         if (coupled) return wide ? pairs_kernel<true, false, true, 0, true> : pairs_kernel<true, false, true, 0, false>;
         if (scan == MCPD_SCAN_SYSTEMATIC)
             return wide ? pairs_kernel<false, true, true, 0, true> : pairs_kernel<false, true, true, 0, false>;
         return wide ? pairs_kernel<false, false, true, 0, true> : pairs_kernel<false, false, true, 0, false>;
+    }
+    if (coupled && ext) {
+        switch (udeg) {
+            case 3: return pairs_kernel<true, false, false, 3, false, true>;
+            case 4: return pairs_kernel<true, false, false, 4, false, true>;
+            case 5: return pairs_kernel<true, false, false, 5, false, true>;
+            case 6: return pairs_kernel<true, false, false, 6, false, true>;
+            case 7: return pairs_kernel<true, false, false, 7, false, true>;
+            case 8: return pairs_kernel<true, false, false, 8, false, true>;
+            default: return pairs_kernel<true, false, false, 0, false, true>;
+        }
     }
     if (coupled) {
         switch (udeg) {
@@ -763,9 +880,11 @@ int set_smem(size_t bytes, bool batch) {
             for (int ud = 0; ud <= 8; ++ud) {
                 if (ud && (batch || !c || ud < 3)) continue;
                 for (int wide = 0; wide <= (batch ? 1 : 0); ++wide)
-                    if (cudaFuncSetAttribute(pick(c, sc, batch, ud, wide != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(bytes)) != cudaSuccess)
-                        return MCPD_ECUDA;
+                    for (int ext = 0; ext <= c; ++ext)
+                        if (cudaFuncSetAttribute(pick(c, sc, batch, ud, wide != 0, ext != 0),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 static_cast<int>(bytes)) != cudaSuccess)
+                            return MCPD_ECUDA;
             }
         }
     return MCPD_OK;
@@ -783,13 +902,14 @@ int pairs_max_smem(int device, size_t *bytes) {
 
 int launch_pairs(const KParams &kp, int grid, int block, size_t smem, void *stream) {
     const BParams none{};
-    pick(kp.coupled, kp.scan, false, kp.udeg)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(kp, none);
+    const bool ext = kp.capped != 0 || kp.lag > 1;
+    pick(kp.coupled, kp.scan, false, kp.udeg, false, ext)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(kp, none);
     return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
 }
 
 int launch_batch(const BParams &bp, int grid, int block, size_t smem, void *stream) {
     const KParams none{};
-    pick(bp.coupled, bp.scan, true, 0, bp.wide != 0)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(none, bp);
+    pick(bp.coupled, bp.scan, true, 0, bp.wide != 0, bp.ext != 0)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(none, bp);
     return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
 }
 

@@ -155,6 +155,8 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     kp.dummy_word_index = t.dummy_word_index; kp.coupled = t.coupled ? 1 : 0;
     kp.P = t.P; kp.B = t.B; kp.k = t.k; kp.ell = t.ell; kp.L = t.L; kp.burn = t.burn;
     kp.length = t.length; kp.unit = t.unit; kp.step_limit = t.step_limit; kp.tau_audit = t.tau_audit;
+    kp.capped = t.capped ? 1 : 0;
+    kp.lag = static_cast<int32_t>(t.lag);
     kp.slot_offset = t.slot_offset; kp.trace_stride = 0;
     kp.seed = t.seed; philox_round_keys(t.seed, kp.rk); kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
@@ -171,16 +173,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     CUN(cudaStreamSynchronize(s));
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
-        stats->progress_units = static_cast<int64_t>(c[kProgress]);
-        stats->reps_started = static_cast<int64_t>(c[kRepsStarted]);
-        stats->reps_retained = static_cast<int64_t>(c[kRepsRetained]);
-        stats->reps_aborted = static_cast<int64_t>(c[kRepsAborted]);
-        stats->zero_completion_slots = static_cast<int64_t>(c[kZeroCompletion]);
-        stats->step_limit_hits = static_cast<int64_t>(c[kStepLimitHits]);
-        stats->max_tau = static_cast<int64_t>(c[kMaxTau]);
-        stats->sum_tau = static_cast<int64_t>(c[kSumTau]);
-        stats->tau_over_audit = static_cast<int64_t>(c[kTauOverAudit]);
-        stats->site_updates = t.coupled ? 2 * stats->progress_units - stats->reps_started : stats->progress_units;
+        counters_to_stats(c, stats);
         stats->n_buckets = t.nb;
         stats->n_active = t.na;
     }

@@ -266,7 +266,9 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
         if (prm->k < 0 && t.k > t.ell) t.k = t.ell;
         if (t.k < 0 || t.k > t.ell) return fail(err, "need 0 <= k <= l", MCPD_EINVAL);
         t.L = t.ell - t.k + 1;
-        t.unit = std::max<int64_t>(t.ell, 1);
+        t.lag = prm->lag > 1 ? prm->lag : 1;
+        if (prm->lag < 0 || t.lag > (int64_t(1) << 20)) return fail(err, "lag must be in [0, 2^20]", MCPD_EINVAL);
+        t.unit = std::max<int64_t>(std::max<int64_t>(t.ell, t.lag), 1);
     } else {
         t.burn = prm->burn < 0 ? round_half_even(0.1 * static_cast<double>(na)) : prm->burn;
         t.length = prm->length < 0 ? na - t.burn : prm->length;
@@ -291,6 +293,17 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
     t.step_limit = prm->step_limit > 0 ? prm->step_limit : int64_t(10000) * na;
     if (t.step_limit > (int64_t(1) << 31)) return fail(err, "step_limit above 2^31", MCPD_EINVAL);
     if (!t.coupled) t.step_limit = std::max(t.step_limit, t.unit + 1);
+    if (t.coupled && t.step_limit < t.lag) return fail(err, "step_limit below the lag", MCPD_EINVAL);
+    if (prm->meeting_cap < 0) return fail(err, "meeting_cap must be >= 0", MCPD_EINVAL);
+    if (t.coupled && prm->meeting_cap > 0) {
+        if (prm->meeting_cap < t.unit)
+            return fail(err, "meeting_cap must be >= max(l, lag, 1)", MCPD_EINVAL);
+        if (prm->meeting_cap > (int64_t(1) << 31)) return fail(err, "meeting_cap above 2^31", MCPD_EINVAL);
+        if (t.tau_audit > prm->meeting_cap) return fail(err, "tau_audit above meeting_cap", MCPD_EINVAL);
+        t.capped = true;
+        t.step_limit = prm->meeting_cap;
+        if (t.tau_audit == 0) t.tau_audit = prm->meeting_cap;
+    }
     // Integer bounds: |G| of one replication <= L (1 + 2 tau); a slot's retained replications
     // cost at most B + step_limit draws in total.
     const long double gmax = static_cast<long double>(t.L) * (2.0L * (t.B + t.step_limit) + 1.0L);

@@ -44,7 +44,8 @@ class mcpd_params(C.Structure):
                 ("horizon", C.c_int64), ("budget_site_updates", C.c_double),
                 ("step_limit", C.c_int64), ("seed", C.c_uint64), ("instance_id", C.c_uint32),
                 ("record_slots", C.c_int32), ("slot_offset", C.c_int64),
-                ("trace_stride", C.c_int64), ("tau_audit", C.c_int64)]
+                ("trace_stride", C.c_int64), ("tau_audit", C.c_int64), ("meeting_cap", C.c_int64),
+                ("lag", C.c_int64)]
 
 
 class mcpd_stats(C.Structure):
@@ -152,7 +153,7 @@ def make_params(inst=None, keep: _Keep | None = None, *, fp=None, fn=None, prior
                 n_active=0, scan=MCPD_SCAN_SCORE, coupled=True, scan_weights=None,
                 init_marginals=None, k=-1, ell=-1, burn=-1, length=-1, slots=1, horizon=0,
                 budget_site_updates=0.0, step_limit=0, seed=1, instance_id=0, record_slots=False,
-                slot_offset=0, trace_stride=0, lanes_per_pair=0, tau_audit=0):
+                slot_offset=0, trace_stride=0, lanes_per_pair=0, tau_audit=0, meeting_cap=0, lag=0):
     keep = keep or _Keep()
     sw = keep.arr(scan_weights, np.float64)
     nu = keep.arr(init_marginals, np.float64)
@@ -166,7 +167,8 @@ def make_params(inst=None, keep: _Keep | None = None, *, fp=None, fn=None, prior
         budget_site_updates=float(budget_site_updates), step_limit=int(step_limit),
         seed=int(seed) & 0xFFFFFFFFFFFFFFFF, instance_id=int(instance_id),
         record_slots=int(bool(record_slots)), slot_offset=int(slot_offset),
-        trace_stride=int(trace_stride), tau_audit=int(tau_audit))
+        trace_stride=int(trace_stride), tau_audit=int(tau_audit), meeting_cap=int(meeting_cap),
+        lag=int(lag))
 
 
 def mcpd_inspect(inst, **params):

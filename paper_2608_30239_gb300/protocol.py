@@ -8,13 +8,18 @@ Methods, at an estimator length of s sweeps (M = s n_a single-site updates, b = 
   RU   uniform random scan, uncoupled (Algorithm 1);
   SW   score-weighted random scan, uncoupled (Algorithm 2);
   cRU  uniform random scan, coupled pairs, k = b + 1, l = M (Algorithms 3-4);
-  cSW  score-weighted random scan, coupled pairs (Algorithms 3-4).
-Every slot has a horizon of 20 sweeps.  The uncoupled methods hold twice as many slots as the
+  cSW  score-weighted random scan, coupled pairs (Algorithms 3-4);
+  cSW-nr  cSW without slot refill (the ablation of Section "Slot refill ablation"): a horizon of
+       zero progress units, so every slot keeps its first pair and runs no other.
+Every slot but those of cSW-nr has a horizon of 20 sweeps.  The uncoupled methods hold twice as many slots as the
 coupled ones (each coupled slot holds two chains), so both hold the same number of chain states.
 The reference vector is a long systematic-scan run (burn-in and sampling lengths in sweeps).
 Scores are the mean absolute error over the retained clones and over the reference's ten largest.
-The coupled runs are uncapped; the share of completed pairs whose meeting time exceeds the cap
-(20 sweeps) is reported, the pairs a finite meeting cap would have stopped.
+As in the paper's runs, the coupled runs impose a 20-sweep meeting cap (a pair unmet at the cap is
+kept with its correction cut there); the cap-hit rate is the share of the pairs attempted that
+reached it.  With --uncapped the runs are unbiased and the rate counts the kept pairs whose
+meeting time exceeded the cap.
+--lag L runs the coupled methods with lag-L pairs (L pre-lag updates; the cap must be >= L).
 Prints one JSON line.
 """
 from __future__ import annotations
@@ -61,7 +66,10 @@ def main(argv=None):
     ap.add_argument("--ref-sweeps", type=int, default=10000, help="reference sampling length, sweeps")
     ap.add_argument("--ref-chains", type=int, default=65536)
     ap.add_argument("--seed", type=int, default=20260)
-    ap.add_argument("--cap-sweeps", type=int, default=20, help="meeting cap audited (the runs stay uncapped)")
+    ap.add_argument("--cap-sweeps", type=int, default=20, help="meeting cap, sweeps")
+    ap.add_argument("--uncapped", action="store_true", help="audit the cap without imposing it")
+    ap.add_argument("--lag", type=int, default=1, help="lag of the coupled pairs")
+    ap.add_argument("--methods", default="SS,RU,SW,cRU,cSW,cSW-nr", help="subset of the methods")
     a = ap.parse_args(argv)
     fn, fp = (float(v) for v in a.noise.split(","))
     inst = synth.make_instance(a.n, a.m, a.deg, a.positives, fp, fn, a.positives / a.n, 5007, 9007)
@@ -80,31 +88,40 @@ def main(argv=None):
         "SW": dict(coupled=False, scan=mcpd.MCPD_SCAN_SCORE),
         "cRU": dict(coupled=True, scan=mcpd.MCPD_SCAN_UNIFORM),
         "cSW": dict(coupled=True, scan=mcpd.MCPD_SCAN_SCORE),
+        "cSW-nr": dict(coupled=True, scan=mcpd.MCPD_SCAN_SCORE, horizon=0),
     }
+    methods = {m: methods[m] for m in a.methods.split(",")}
     rows = []
     for s in (int(v) for v in a.sweeps.split(",")):
         M = s * a.n_active
         b = round_half_even(0.1 * M)
         for name, kw in methods.items():
             if kw["coupled"]:
-                kw2 = dict(kw, k=b + 1, ell=M, slots=a.slots, tau_audit=a.cap_sweeps * a.n_active)
+                cap = a.cap_sweeps * a.n_active
+                kw2 = dict(kw, k=b + 1, ell=M, slots=a.slots, tau_audit=cap, lag=a.lag)
+                if not a.uncapped:
+                    kw2["meeting_cap"] = cap
             else:
                 kw2 = dict(kw, burn=b, length=M - b, slots=2 * a.slots)
             t1 = time.perf_counter()
-            est, act, st = _decode(ctx, inst, n_active=a.n_active, horizon=horizon, seed=a.seed + 100 * s + len(rows), **kw2)
+            kw2.setdefault("horizon", horizon)
+            est, act, st = _decode(ctx, inst, n_active=a.n_active, seed=a.seed + 100 * s + len(rows), **kw2)
             assert np.array_equal(act, active)
             rows.append({"sweeps": s, "method": name, "mae_all": float(np.mean(np.abs(est - ref))),
                          "mae_top10": float(np.mean(np.abs(est[top] - ref[top]))),
                          "site_updates": st["site_updates"], "kernel_ms": st["kernel_ms"],
-                         "step_limit_hits": st["step_limit_hits"],
+                         "step_limit_hits": st["step_limit_hits"], "reps_retained": st["reps_retained"],
                          "mean_tau_sweeps": (st["sum_tau"] / max(1, st["reps_retained"]) / a.n_active) if kw["coupled"] else None,
                          "max_tau_sweeps": (st["max_tau"] / a.n_active) if kw["coupled"] else None,
-                         "cap_hit_rate": (st["tau_over_audit"] / max(1, st["reps_retained"])) if kw["coupled"] else None,
+                         "reps_started": st["reps_started"],
+                         "cap_hits": st["tau_over_audit"] if kw["coupled"] else None,
+                         "cap_hit_rate": (st["tau_over_audit"] / max(1, st["reps_started"])) if kw["coupled"] else None,
                          "seconds": time.perf_counter() - t1})
     out = {"instance": dict(n=a.n, m=a.m, deg=a.deg, positives=a.positives, fn=fn, fp=fp, n_active=a.n_active),
            "reference": dict(burn_sweeps=a.ref_burn, sweeps=a.ref_sweeps, chains=a.ref_chains, seconds=t_ref,
                              site_updates=st_ref["site_updates"], top10=[int(active[i]) for i in top]),
            "slots_coupled": a.slots, "slots_uncoupled": 2 * a.slots, "horizon_sweeps": a.horizon_sweeps,
+           "meeting_cap_sweeps": None if a.uncapped else a.cap_sweeps, "lag": a.lag,
            "rows": rows}
     print(json.dumps(out), flush=True)
     ctx.close()

@@ -112,6 +112,10 @@ def test_window_and_horizon_defaults(L, oracle_lib):
     (dict(coupled=False, burn=0, length=1), mcpd.MCPD_EINVAL),
     (dict(horizon=10 ** 6, ell=1, k=0), mcpd.MCPD_ETOO_LARGE),
     (dict(tau_audit=-1), mcpd.MCPD_EINVAL),
+    (dict(meeting_cap=-1), mcpd.MCPD_EINVAL),
+    (dict(k=2, ell=20, meeting_cap=19), mcpd.MCPD_EINVAL),
+    (dict(k=2, ell=20, meeting_cap=30, tau_audit=31), mcpd.MCPD_EINVAL),
+    (dict(k=2, ell=20, meeting_cap=(1 << 31) + 1), mcpd.MCPD_EINVAL),
 ])
 def test_invalid_parameters_rejected(L, kw, code):
     inst = synth.tiny_config(1)
@@ -146,3 +150,15 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(lib_build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         mcpd.lib()
+
+
+def test_meeting_cap_replaces_the_step_limit(L):
+    """A meeting cap becomes the replication's step limit (info[12]); uncoupled runs ignore it."""
+    inst = synth.tiny_config(1)
+    capped = mcpd.mcpd_inspect(inst, slots=8, horizon=100, k=2, ell=20, meeting_cap=30, step_limit=10 ** 6)
+    assert capped["info"][12] == 30
+    free = mcpd.mcpd_inspect(inst, slots=8, horizon=100, k=2, ell=20, step_limit=10 ** 6)
+    assert free["info"][12] == 10 ** 6
+    unc = mcpd.mcpd_inspect(inst, slots=8, horizon=100, coupled=False, burn=2, length=20,
+                            meeting_cap=5, step_limit=10 ** 6)
+    assert unc["info"][12] == 10 ** 6

@@ -58,7 +58,8 @@ def _params(insts, coupled=True):
 def _oracle(inst, kw):
     M = oracle.Model(inst)
     if kw.get("coupled", True):
-        run = oracle.coupled_run(kw["k"], kw["ell"], kw["horizon"], kw["seed"], instance=kw["instance_id"])
+        run = oracle.coupled_run(kw["k"], kw["ell"], kw["horizon"], kw["seed"], instance=kw["instance_id"],
+                                 meeting_cap=kw.get("meeting_cap", 0), lag=kw.get("lag", 1))
         L = kw["ell"] - kw["k"] + 1
     else:
         run = oracle.uncoupled_run(kw["burn"], kw["length"], kw["horizon"], kw["seed"],
@@ -158,6 +159,59 @@ def test_lane_groups_match_oracle(ctx, lanes):
             assert np.array_equal(got[key], ref[key]), (lanes, i, key)
         a, b = batch.offsets[i], batch.offsets[i + 1]
         assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"])
+    batch.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 16])
+def test_batch_meeting_cap(ctx, lanes):
+    """Meeting caps per instance (one instance uncapped) in one batch, one thread or a lane group
+    per pair: every instance equals the oracle with its own cap."""
+    from paper_2608_30239_gb300 import mcpd
+    insts = _uneven(5, seed=21)
+    ps = _params(insts)
+    for i in range(len(ps)):
+        if i != 2:
+            ps[i] = dict(ps[i], meeting_cap=ps[i]["ell"] + 3 * i)
+    batch = mcpd.Batch(ctx, insts, ps, classes=2)
+    if lanes > 1:
+        batch.set_shape(0, lanes)
+    est, se, st = _run(ctx, batch)
+    assert st["tau_over_audit"] > 0 and st["step_limit_hits"] == 0
+    for i, (inst, kw) in enumerate(zip(insts, ps)):
+        ref = _oracle(inst, kw)
+        got = batch.buckets(i)
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (lanes, i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"])
+    batch.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 16])
+def test_batch_lags(ctx, lanes):
+    """Different lags per instance (1, 2, 5, 9, with a cap on one) in one batch, one thread or a
+    lane group per pair: every instance equals the oracle; the site updates count each
+    replication's pre-lag updates."""
+    from paper_2608_30239_gb300 import mcpd
+    insts = _uneven(4, seed=23)
+    ps = _params(insts)
+    lags = [1, 2, 5, 9]
+    for i in range(len(ps)):
+        ps[i] = dict(ps[i], lag=lags[i])
+    ps[2] = dict(ps[2], meeting_cap=ps[2]["ell"] + 40)
+    batch = mcpd.Batch(ctx, insts, ps, classes=2)
+    if lanes > 1:
+        batch.set_shape(0, lanes)
+    est, se, st = _run(ctx, batch)
+    started = 0
+    for i, (inst, kw) in enumerate(zip(insts, ps)):
+        ref = _oracle(inst, kw)
+        got = batch.buckets(i)
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (lanes, i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"])
+    assert st["site_updates"] < 2 * st["progress_units"] - st["reps_started"]
     batch.close()
 
 

@@ -48,9 +48,10 @@ def _gpu_run(ctx, inst, **kw):
 
 
 def _oracle_run(inst, P, k, ell, B, seed, coupled=True, burn=0, length=1, n_active=0,
-                scan=oracle.SCAN_SCORE, custom_w=None, init=None, slot_offset=0, slot_G=False):
+                scan=oracle.SCAN_SCORE, custom_w=None, init=None, slot_offset=0, slot_G=False,
+                meeting_cap=0, lag=1):
     M = oracle.Model(inst, n_active=n_active, scan=scan, custom_w=custom_w, init_marginals=init)
-    run = (oracle.coupled_run(k, ell, B, seed, slot_offset=slot_offset) if coupled
+    run = (oracle.coupled_run(k, ell, B, seed, slot_offset=slot_offset, meeting_cap=meeting_cap, lag=lag) if coupled
            else oracle.uncoupled_run(burn, length, B, seed, slot_offset=slot_offset))
     res = M.run_slots(run, 0, P, THREADS, per_slot=True, slot_G=slot_G)
     L = (ell - k + 1) if coupled else length
@@ -183,6 +184,104 @@ def test_tau_audit_counts_meetings_beyond_the_threshold(ctx, audit):
     assert g["stats"]["max_tau"] == int(taus.max()) and g["stats"]["sum_tau"] == int(taus.sum())
     plain = _gpu_run(ctx, inst, slots=P, k=3, ell=20, horizon=0, seed=55)
     assert np.array_equal(plain["S1"], g["S1"]) and plain["stats"]["tau_over_audit"] == 0
+
+
+def test_tau_audit_with_refill(ctx):
+    """With refill (B = 60, several replications per slot and many slots per pair), the audit
+    count equals the number of retained oracle replications that met at tau > audit, and the
+    retained count is unchanged by the audit."""
+    inst = synth.tiny_config(4)
+    P, audit = 1500, 3
+    g = _gpu_run(ctx, inst, slots=P, k=3, ell=20, horizon=60, seed=56, tau_audit=audit)
+    M = oracle.Model(inst)
+    run = oracle.coupled_run(3, 20, 60, 56)
+    res = M.run_slots(run, 0, P, per_slot=True)
+    taus = np.array([M.replication(run, p, r)["tau"] for p in range(P) for r in range(int(res["slot_nstar"][p]))])
+    assert g["stats"]["reps_retained"] == taus.size == int(res["slot_nstar"].sum())
+    assert g["stats"]["tau_over_audit"] == int((taus > audit).sum()) > 0
+    assert g["stats"]["sum_tau"] == int(taus.sum())
+
+
+@pytest.mark.parametrize("cap,B", [(20, 0), (24, 0), (20, 60), (24, 60), (90, 400)])
+def test_meeting_cap(ctx, cap, B):
+    """The finite meeting cap: a pair unmet at t = cap is kept with every inner sum cut at the
+    cap.  Bit-exact against the oracle with the same cap, with and without refill; the audit,
+    which defaults to the cap, counts the capped pairs that were kept.  (20, 60): every
+    replication costs exactly 20, so the third one of a slot reaches the cap at the very clock
+    B - S at which an unfinished replication is doomed; capped, it is kept."""
+    inst = synth.tiny_config(4)
+    P = 3001
+    g = _gpu_run(ctx, inst, slots=P, k=3, ell=20, horizon=B, seed=57, meeting_cap=cap,
+                 record_slots=True, trace_stride=1)
+    o = _oracle_run(inst, P, 3, 20, B, 57, meeting_cap=cap, slot_G=True)
+    _assert_same(g, o)
+    assert np.array_equal(g["trace_G"], o["slot_G"])
+    assert g["stats"]["step_limit_hits"] == 0
+    if B == 0:                 # every replication is kept: the counts agree exactly
+        assert g["stats"]["tau_over_audit"] == o["stats"]["capped"] > 0
+        assert g["stats"]["sum_tau"] == o["stats"]["sum_tau"]
+    else:                      # the oracle also counts the discarded last replication of a slot
+        assert 0 < g["stats"]["tau_over_audit"] <= o["stats"]["capped"]
+
+
+def test_meeting_cap_mixed_degree_random_start(ctx):
+    """The cap on a mixed-degree design (padding pools) from a random start, where Y_0 carries
+    bits that no flip of the replication touched."""
+    inst = _mixed()
+    nu = np.random.default_rng(8).random(inst.n) * 0.2
+    k, ell = oracle.window_defaults(inst.n, 1)
+    P, B, cap = 3000, 3 * ell + 5, ell + 9
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=809, init_marginals=nu,
+                 meeting_cap=cap, record_slots=True, trace_stride=7)
+    o = _oracle_run(inst, P, k, ell, B, 809, init=nu, slot_G=True, meeting_cap=cap)
+    _assert_same(g, o)
+    assert np.array_equal(g["trace_G"], o["slot_G"][::7])
+    assert g["stats"]["tau_over_audit"] > 0
+
+
+@pytest.mark.parametrize("lag,B,cap", [(2, 0, 0), (2, 60, 0), (5, 400, 0), (5, 90, 30), (25, 200, 0)])
+def test_lag_coupling(ctx, lag, B, cap):
+    """Lag-L pairs (L pre-lag updates of X, then X_{t+1} and Y_{t+1-L} from the same draw),
+    with and without refill and a meeting cap: bit-exact against the oracle; the site updates
+    count L pre-lag updates per replication."""
+    inst = synth.tiny_config(4)
+    P = 3001
+    g = _gpu_run(ctx, inst, slots=P, k=3, ell=20, horizon=B, seed=58, lag=lag, meeting_cap=cap,
+                 record_slots=True, trace_stride=1)
+    o = _oracle_run(inst, P, 3, 20, B, 58, lag=lag, meeting_cap=cap, slot_G=True)
+    _assert_same(g, o)
+    assert np.array_equal(g["trace_G"], o["slot_G"])
+    st = g["stats"]
+    assert st["step_limit_hits"] == 0
+    assert st["site_updates"] == 2 * st["progress_units"] - lag * st["reps_started"]
+    if B == 0:
+        assert st["progress_units"] == o["stats"]["draws"] and st["sum_tau"] == o["stats"]["sum_tau"]
+        assert st["max_tau"] >= lag
+
+
+@pytest.mark.parametrize("lag", [3, 12])
+def test_lag_random_start_mixed_degree(ctx, lag):
+    """Lag on a mixed-degree design from a random start: Y_0 is copied at the first pre-lag move,
+    X may come back to Y_0 before t = L (the meeting is then decided at t = L)."""
+    inst = _mixed()
+    nu = np.random.default_rng(9).random(inst.n) * 0.2
+    k, ell = 5, 40
+    P, B = 3000, 300
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=810, init_marginals=nu, lag=lag,
+                 record_slots=True, trace_stride=5)
+    o = _oracle_run(inst, P, k, ell, B, 810, init=nu, slot_G=True, lag=lag)
+    _assert_same(g, o)
+    assert np.array_equal(g["trace_G"], o["slot_G"][::5])
+
+
+def test_lag_degree_six(ctx):
+    """The degree-6 kernel (mask-indexed thresholds) with lag 4 and the high-noise shape."""
+    inst = synth.make_instance(300, 30, 6, 3, 0.10, 0.20, 3 / 300, 71, 72)
+    k, ell = oracle.window_defaults(inst.n, 1)
+    P, B = 2000, 3 * ell
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=811, lag=4, record_slots=True)
+    o = _oracle_run(inst, P, k, ell, B, 811, lag=4)
+    _assert_same(g, o)
 
 
 def test_step_limit_reports_error_and_context_survives(ctx):
