@@ -204,7 +204,8 @@ void mcpd_batch_destroy(mcpd_batch *batch);
 /* info[0] total retained clones, [1] instances, [2] total slots, [3] largest n_active,
  * [4] warps per block, [5] blocks and [7] shared-memory bytes per block of the first class (the
  * largest pair state), [6] resident pairs of the widest class, [8] lanes per pair, [9] size
- * classes, [10] largest warps per block over the classes. */
+ * classes, [10] largest warps per block over the classes, [11] classes that launch the kernel
+ * variant with meeting caps and lags > 1. */
 int mcpd_batch_info(const mcpd_batch *batch, int64_t info[16]);
 /* offsets: [n_inst + 1] host array receiving each instance's first output index. */
 int mcpd_batch_offsets(const mcpd_batch *batch, int64_t *offsets);

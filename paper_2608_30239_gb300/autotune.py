@@ -20,7 +20,7 @@ CACHE = os.path.join(BUILD, "autotune_cache.json")
 def shape_key(gpu_name: str, batch) -> str:
     info = batch.info
     b = lambda v: 2 ** int(math.ceil(math.log2(max(1, int(v)))))   # noqa: E731
-    return f"{gpu_name}|inst{b(info[1])}|na{b(info[3])}|slots{b(info[2])}|cls{int(info[9])}"
+    return f"{gpu_name}|inst{b(info[1])}|na{b(info[3])}|slots{b(info[2])}|cls{int(info[9])}|ext{int(info[11])}"
 
 
 def load():

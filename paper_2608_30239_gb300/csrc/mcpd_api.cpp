@@ -684,16 +684,17 @@ int mcpd_batch_info(const mcpd_batch *b, int64_t info[16]) {
     if (!b || !info) return MCPD_EINVAL;
     std::memset(info, 0, 16 * sizeof(int64_t));
     int32_t max_na = 0;
-    int64_t pairs = 0, wmax = 0;
+    int64_t pairs = 0, wmax = 0, ext = 0;
     for (const BatchClass &c : b->cls) {
         max_na = std::max(max_na, c.bp.max_na);
         pairs = std::max<int64_t>(pairs, c.pairs);
         wmax = std::max<int64_t>(wmax, c.warps);
+        ext += c.bp.ext;
     }
     const BatchClass &c0 = b->cls[0];
     info[0] = b->total_active; info[1] = b->n_inst; info[2] = b->total_slots; info[3] = max_na;
     info[4] = c0.warps; info[5] = c0.grid; info[6] = pairs; info[7] = static_cast<int64_t>(c0.smem);
-    info[8] = b->lanes; info[9] = static_cast<int64_t>(b->cls.size()); info[10] = wmax;
+    info[8] = b->lanes; info[9] = static_cast<int64_t>(b->cls.size()); info[10] = wmax; info[11] = ext;
     return MCPD_OK;
 }
 

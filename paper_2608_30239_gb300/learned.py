@@ -204,9 +204,10 @@ def plain_marginals(ctx, instances, slots=256, sweeps=5, seed=1):
     return est.cpu().numpy(), se.cpu().numpy(), st
 
 
-def decode_max_se(ctx, instances, slots, sweeps, seed, weights=None, init=None, graph=False):
-    """One batched decode of `instances` with P = slots and B = sweeps * n; returns
-    (max over instances of the largest per-clone SE, kernel ms, stats)."""
+def decode_max_se(ctx, instances, slots, sweeps, seed, weights=None, init=None, graph=False, lag_sweeps=0):
+    """One batched decode of `instances` with P = slots and B = sweeps * n (lag-L pairs with
+    L = lag_sweeps * n when lag_sweeps > 0); returns (max over instances of the largest per-clone
+    SE, kernel ms, stats)."""
     import torch
     seg = segments(instances)
     params = []
@@ -216,6 +217,8 @@ def decode_max_se(ctx, instances, slots, sweeps, seed, weights=None, init=None, 
             kw.update(scan=mcpd.MCPD_SCAN_CUSTOM, scan_weights=weights[seg[i]:seg[i + 1]])
         if init is not None:
             kw.update(init_marginals=init[seg[i]:seg[i + 1]])
+        if lag_sweeps > 0:
+            kw.update(lag=max(1, int(round(lag_sweeps * inst.n))))
         params.append(kw)
     b = mcpd.Batch(ctx, instances, params)
     est = torch.empty(b.total_active, dtype=torch.float64, device=f"cuda:{ctx.device}")
@@ -227,13 +230,13 @@ def decode_max_se(ctx, instances, slots, sweeps, seed, weights=None, init=None, 
 
 
 def time_to_se(ctx, instances, target=0.005, sweeps=29.4, slots0=1024, seed=7, weights=None,
-               init=None, max_slots=1 << 22):
+               init=None, max_slots=1 << 22, lag_sweeps=0):
     """Double P from slots0 until every instance's largest per-clone SE is <= target; report the
     kernel time of the first decode that meets it (and the path of (P, max SE, ms))."""
     P = slots0
     path = []
     while True:
-        mse, ms, st = decode_max_se(ctx, instances, P, sweeps, seed, weights, init)
+        mse, ms, st = decode_max_se(ctx, instances, P, sweeps, seed, weights, init, lag_sweeps=lag_sweeps)
         path.append((P, mse, ms))
         if mse <= target or P >= max_slots:
             return dict(slots=P, max_se=mse, kernel_ms=ms, path=path, met=mse <= target)
