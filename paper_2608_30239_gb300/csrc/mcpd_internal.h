@@ -42,8 +42,9 @@ enum PairStat {
     kPsTauAudit, kPsSiteUpdates, kPairStats = 10
 };
 
-// Per-pair scratch, one contiguous block of 8-byte words per pair: the replication's sums G
-// [0, na), the slot's sums [na, 2 na), the statistics record [2 na, 2 na + kPairStats), then the
+// Per-pair scratch, one contiguous block of 8-byte words per pair: the replication's and the
+// slot's sums G in [0, 2 na) (interleaved per clone in the one-thread-per-pair kernel, in two
+// halves in the lane-group kernel), the statistics record [2 na, 2 na + kPairStats), then the
 // touched-clone bit sets of the replication and of the slot (W 32-bit words each).
 #ifdef __CUDACC__
 __host__ __device__

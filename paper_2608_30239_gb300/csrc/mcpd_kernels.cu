@@ -91,8 +91,10 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     // This pair's scratch block (see pair_words): one base pointer, the parts at fixed offsets.
     long long *const pb = (BATCH ? bp.pair_scratch : p.pair_scratch) +
                           static_cast<size_t>(gpair) * static_cast<size_t>(pair_words(stride_na, stride_W));
-    auto racc = [&]() { return pb; };
-    auto sacc = [&]() { return pb + stride_na; };
+    // Clone j's replication sum at pb[2j] and slot sum at pb[2j + 1]: a flip event reduces into
+    // both from one address.
+    auto racc = [&](uint32_t j) { return pb + 2 * static_cast<size_t>(j); };
+    auto sacc = [&](uint32_t j) { return pb + 2 * static_cast<size_t>(j) + 1; };
     auto pst = [&]() { return reinterpret_cast<unsigned long long *>(pb + 2 * stride_na); };
     auto trep = [&]() { return reinterpret_cast<uint32_t *>(pb + 2 * stride_na + kPairStats); };
     auto tslot = [&]() { return reinterpret_cast<uint32_t *>(pb + 2 * stride_na + kPairStats) + stride_W; };
@@ -374,8 +376,6 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     auto finish_rep = [&](bool move, uint32_t C) {
         const long long wX = move ? static_cast<long long>(wstep(C)) : 0;
         if (COUPLED && (EXT ? ycol != nullptr : D != 0)) release_y();
-        long long *const ra = racc();
-        long long *const sa = sacc();
         uint32_t groups = rep_words;
         while (groups) {
             const int g = __ffs(groups) - 1;
@@ -390,15 +390,15 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
                     const int b = __ffs(tm) - 1;
                     tm &= tm - 1;
                     const uint32_t j = q * 32 + b;
-                    if (!move) red_add(&sa[j], -__ldcg(&ra[j]));   // discarded: its events leave the slot
-                    ra[j] = 0;
+                    if (!move) red_add(sacc(j), -__ldcg(racc(j)));   // discarded: its events leave the slot
+                    *racc(j) = 0;
                 }
                 if (move && wX != 0) {          // closing terms of the sites set in X_C
                     uint32_t om = xw;
                     while (om) {
                         const int b = __ffs(om) - 1;
                         om &= om - 1;
-                        red_add(&sa[q * 32 + b], wX);
+                        red_add(sacc(q * 32 + b), wX);
                     }
                 }
                 uint32_t xm = xw;                 // X's counts back to zero
@@ -436,8 +436,8 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
                     const int b = __ffs(tw) - 1;
                     tw &= tw - 1;
                     const uint32_t j = q * 32 + b;
-                    const long long gsum = __ldcg(&sacc()[j]);
-                    sacc()[j] = 0;
+                    const long long gsum = __ldcg(sacc(j));
+                    *sacc(j) = 0;
                     if (valid && gsum != 0) {
                         bucket_add(v_S1(), v_S2lo(), v_S2hi(), na, bkt, static_cast<int>(j), gsum);
                         if (tr) tr[j] = gsum;
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
                 while (dm) {
                     const int b = __ffs(dm) - 1;
                     dm &= dm - 1;
-                    red_add(&sacc()[q * 32 + b], ((xw >> b) & 1u) ? wc : -wc);
+                    red_add(sacc(q * 32 + b), ((xw >> b) & 1u) ? wc : -wc);
                 }
             }
         }
@@ -561,8 +561,8 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         const uint32_t w = wstep(t);
         if (w) {
             const long long ev = nX ? -static_cast<long long>(w) : static_cast<long long>(w);
-            red_add(&racc()[I], ev);
-            red_add(&sacc()[I], ev);
+            red_add(racc(I), ev);
+            red_add(sacc(I), ev);
             red_or(&trep()[q], bit);
         }
         rep_words |= 1u << (q >> gshift);
@@ -605,8 +605,8 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
             ev += nY ? w : -w;
         }
         if (ev != 0) {
-            red_add(&racc()[I], ev);
-            red_add(&sacc()[I], ev);
+            red_add(racc(I), ev);
+            red_add(sacc(I), ev);
             red_or(&trep()[q], bit);
         }
         rep_words |= 1u << (q >> gshift);
