@@ -31,6 +31,9 @@ namespace {
 // step t is also the flip of Y at step t, and the two events add to -+(W(t) - W(t-1)) = -+w(t).
 // The uncoupled flip event W(t) has the same clamp form, so both modes use
 // wstep(u) = clamp(u - s + 1, 0, cap) with (s, cap) = (k, L) or (b, T).
+// With lag L (Y_{t+1-L} moves with X_{t+1}), the weight of X_t and Y_t is the number of window
+// indices r = t - jL (j >= 0), W is its prefix sum, a Y flip at step t adds +-W(t - L), and the
+// met flip and the closing term keep the one-lag count wstep (see wpre and met_flip).
 
 // One persistent kernel for a single instance (BATCH = false: tables staged in shared memory,
 // parameters from KParams) or for many instances in one launch (BATCH = true: tables read through
@@ -285,8 +288,8 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         yslot = -1;
         ycol = nullptr;
     };
-    // The pre-lag update flipped site I of X_0 and the start was random: Y_0 = X_0 (X_1 with bit
-    // I restored) goes to the Y column.
+    // A pre-lag update flipped site I of X_t = X_0 and the start was random: Y_0 = X_0 (X_{t+1}
+    // with bit I restored) goes to the Y column.
     auto copy_y0 = [&](uint32_t qI, uint32_t bitI) {
         unsigned char *yb = reinterpret_cast<unsigned char *>(ycol);
         uint32_t groups = rep_words;
