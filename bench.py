@@ -232,7 +232,11 @@ def learned_leg(ctx, device, train=512, slots=1 << 21):
     for name, kw in (("paper_weights_allneg_lag1sweep", dict(lag_sweeps=1.0)),
                      ("paper_weights_learned_nu_lag1sweep", dict(init=nu, lag_sweeps=1.0))):
         r = learned.time_to_se(ctx, [inst], 0.005, 29.4, slots0=1024, seed=8, **kw)
-        out[name]["measured"] = {"slots": r["slots"], "max_se": r["max_se"], "s_to_se_0.005": r["kernel_ms"] / 1000.0,
+        # a launch this small is timed by its slowest pairs: repeat the decode that met the target
+        # and keep the median
+        reps = [r["kernel_ms"]] + [learned.decode_max_se(ctx, [inst], r["slots"], 29.4, 8, **kw)[1] for _ in range(2)]
+        out[name]["measured"] = {"slots": r["slots"], "max_se": r["max_se"],
+                                 "s_to_se_0.005": statistics.median(reps) / 1000.0, "kernel_ms_runs": reps,
                                  "met": r["met"]}
     for arm in out.values():
         if isinstance(arm, dict) and "max_se" in arm:
