@@ -739,8 +739,8 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         // discarded if the replication ends
         const uint4 nxt = draw((t >> 1) + 1);
         int ended = 0;
-        if constexpr (!BATCH && DEG <= kMaskDeg) {
-            // both steps of the block inlined (the batch and degree-7/8 builds would spill)
+        if constexpr ((!BATCH && DEG <= kMaskDeg) || (BATCH && !WIDE)) {
+            // both steps of the block inlined (the 20-warp batch and degree-7/8 builds would spill)
 #pragma unroll
             for (int h = 0; h < 2; ++h)
                 if (!ended) ended = step(h ? nxt.x : blk.z, h ? blk.w : blk.y);
