@@ -735,16 +735,26 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     };
     first_site();
     while (alive) {
-        // words (0,1) at even t and (2,3) at odd t; the next block is computed ahead and
-        // discarded if the replication ends
-        const uint4 nxt = draw((t >> 1) + 1);
+        // words (0,1) at even t and (2,3) at odd t; the next block is computed ahead (its first
+        // site word is the second step's prefetch) and discarded if the replication ends
+        uint4 nxt;
         int ended = 0;
-        if constexpr ((!BATCH && DEG <= kMaskDeg) || (BATCH && !WIDE)) {
-            // both steps of the block inlined (the 20-warp batch and degree-7/8 builds would spill)
+        if constexpr (!BATCH && DEG <= kMaskDeg) {
+            // both steps of the block inlined, the next block drawn between them
+            ended = step(blk.z, blk.y);
+            if (!ended) {
+                nxt = draw((t >> 1) + 1);
+                ended = step(nxt.x, blk.w);
+            }
+        } else if constexpr (BATCH && !WIDE) {
+            // both steps inlined, the next block drawn first (measured faster here)
+            nxt = draw((t >> 1) + 1);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
                 if (!ended) ended = step(h ? nxt.x : blk.z, h ? blk.w : blk.y);
         } else {
+            // the 20-warp batch and degree-7/8 builds would spill with both steps inlined
+            nxt = draw((t >> 1) + 1);
 #pragma unroll 1
             for (int h = 0; h < 2 && !ended; ++h) ended = step(h ? nxt.x : blk.z, h ? blk.w : blk.y);
         }
