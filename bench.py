@@ -22,6 +22,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -53,7 +54,7 @@ def workload_config(extra=None):
 
 
 def algorithmic_ops_per_progress_unit(deg: int) -> float:
-    """Integer operations one coupled draw needs by the method's definition (see DESIGN.md):
+    """Integer operations one coupled draw needs by the method's definition:
     half a Philox4x32-10 block (78 ops per block), the alias draw (4), per chain and per pool of the
     drawn site the 'no other positive' test and the (n+, n-) count (2 each), and per chain the
     64-bit threshold comparison (2)."""
@@ -79,7 +80,7 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.device_index = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{device_index}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"mcpd_clocks_gpu{device_index}_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -103,7 +104,13 @@ class ClockSampler:
         self.fh.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        with open(self.path) as fh:
+            lines = fh.readlines()
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue

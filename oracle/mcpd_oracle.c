@@ -14,9 +14,10 @@
  *   - The meeting cap of the experiments (Appendix, setup of the estimator lengths): a pair that
  *     has not met when its clock reaches the cap stops there and keeps H_{k:l} with every inner
  *     sum cut at the cap, the finite-cap approximation of the uncapped estimator.
- * Every random number is a Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11), keyed as the
- * written spec in the design doc states, so that any implementation of the same spec draws the same
- * stream.  Everything is IEEE double; build with -ffp-contract=off so that no multiply-add is fused.
+ * Every random number is a Philox4x32-10 block (Salmon, Moraes, Dror, Shaw, SC'11) with the key
+ * (seed low, seed high) and the counter (block index, replication, global slot id,
+ * tag << 24 | instance), tags 0 (step words), 1 (initial state) and 2 (a uniform's low word), so
+ * that any implementation keyed the same way draws the same stream.  Everything is IEEE double; build with -ffp-contract=off so that no multiply-add is fused.
  *
  * Parity status: pinned (see tests/test_oracle_pins.py) except where a function says otherwise.
  */
