@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     // Uniform degree <= kMaskDeg, single instance: rows hold plain offsets with the clone's
     // positive-outcome pools first and their number in the last entry; thresholds are indexed
     // npos * 64 + (mask of deciding pools).
-    constexpr bool MASKT = COUPLED && !BATCH && DEG >= 3 && DEG <= kMaskDeg;
+    constexpr bool MASKT = !BATCH && DEG >= 3 && DEG <= kMaskDeg;
     auto rowAt = [&](uint32_t c) -> uint4 {
         if constexpr (BATCH) return __ldg(gRows + c); else return sRows[c];
     };
@@ -890,7 +890,22 @@ PairsFn pick(int coupled, int scan, bool batch, int udeg = 0, bool wide = false,
             default: return pairs_kernel<true, false, false, 0>;
         }
     }
-    return scan == MCPD_SCAN_SYSTEMATIC ? pairs_kernel<false, true, false, 0> : pairs_kernel<false, false, false, 0>;
+    if (scan == MCPD_SCAN_SYSTEMATIC) {
+        switch (udeg) {
+            case 3: return pairs_kernel<false, true, false, 3>;
+            case 4: return pairs_kernel<false, true, false, 4>;
+            case 5: return pairs_kernel<false, true, false, 5>;
+            case 6: return pairs_kernel<false, true, false, 6>;
+            default: return pairs_kernel<false, true, false, 0>;
+        }
+    }
+    switch (udeg) {
+        case 3: return pairs_kernel<false, false, false, 3>;
+        case 4: return pairs_kernel<false, false, false, 4>;
+        case 5: return pairs_kernel<false, false, false, 5>;
+        case 6: return pairs_kernel<false, false, false, 6>;
+        default: return pairs_kernel<false, false, false, 0>;
+    }
 }
 
 int set_smem(size_t bytes, bool batch) {
@@ -898,7 +913,7 @@ int set_smem(size_t bytes, bool batch) {
         for (int sc : {MCPD_SCAN_SCORE, MCPD_SCAN_SYSTEMATIC}) {
             if (c && sc == MCPD_SCAN_SYSTEMATIC) continue;
             for (int ud = 0; ud <= 8; ++ud) {
-                if (ud && (batch || !c || ud < 3)) continue;
+                if (ud && (batch || ud < 3 || (!c && ud > kMaskDeg))) continue;
                 for (int wide = 0; wide <= (batch ? 1 : 0); ++wide)
                     for (int ext = 0; ext <= c; ++ext)
                         if (cudaFuncSetAttribute(pick(c, sc, batch, ud, wide != 0, ext != 0),

@@ -227,14 +227,14 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
             t.rows_pool[static_cast<size_t>(a) * kRow + l] = static_cast<uint16_t>(j | (y[j] ? 0x8000u : 0u));
         }
     }
-    // Coupled runs with a uniform degree 3 <= d <= kMaskDeg (single-instance kernels compiled
-    // for d): each row lists the clone's positive-outcome pools first, as plain count offsets,
+    // Runs with a uniform degree 3 <= d <= kMaskDeg (single-instance kernels compiled for d, coupled
+    // or not): each row lists the clone's positive-outcome pools first, as plain count offsets,
     // with their number in entry kRow - 1; T_mask[npos][m] = T[9 n+ + n-] for the mask m of
     // deciding pools (n+ of them among the first npos entries, n- among the rest).  The same
     // thresholds, indexed without per-entry codes.
     t.rows_mask.clear();
     t.T_mask.clear();
-    if (t.coupled && t.udeg >= 3 && t.udeg <= kMaskDeg) {   // the kernels compiled for degree d
+    if (t.udeg >= 3 && t.udeg <= kMaskDeg) {                  // the kernels compiled for degree d
         t.rows_mask.assign(static_cast<size_t>(na) * kRow, 0);
         for (int32_t a = 0; a < na; ++a) {
             const uint16_t *src = &t.rows[static_cast<size_t>(a) * kRow];

@@ -144,6 +144,19 @@ def test_uncoupled_comparators(ctx, scan):
     _ = mcpd
 
 
+@pytest.mark.parametrize("scan,deg", [("score", 6), ("systematic", 6), ("uniform", 5), ("systematic", 3)])
+def test_uncoupled_degree_builds(ctx, scan, deg):
+    """Uncoupled comparators on uniform-degree designs (the builds compiled for the degree, with
+    mask-indexed thresholds), including the high-noise shape at degree 6."""
+    inst = synth.make_instance(300, 30, deg, 3, 0.10, 0.20, 3 / 300, 60 + deg, 61 + deg)
+    code = {"score": 0, "uniform": 1, "systematic": 2}[scan]
+    P, burn, length = 2000, 30, 270
+    g = _gpu_run(ctx, inst, slots=P, coupled=False, scan=code, burn=burn, length=length, horizon=900,
+                 seed=41 + deg, record_slots=True)
+    o = _oracle_run(inst, P, 0, 0, 900, 41 + deg, coupled=False, burn=burn, length=length, scan=code)
+    _assert_same(g, o)
+
+
 def test_custom_weights_and_pruning(ctx):
     inst = synth.high_noise_config()
     P = 600
