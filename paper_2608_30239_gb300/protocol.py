@@ -47,6 +47,22 @@ def _decode(ctx, inst, **kw):
     return out
 
 
+def _summary(rows):
+    """Mean and standard error over executions of each (sweeps, method) cell."""
+    cells = {}
+    for r in rows:
+        cells.setdefault((r["sweeps"], r["method"]), []).append(r)
+    out = []
+    for (s, m), rs in cells.items():
+        d = {"sweeps": s, "method": m, "n": len(rs)}
+        for key in ("mae_all", "mae_top10", "kernel_ms"):
+            v = np.array([r[key] for r in rs], dtype=float)
+            d[key] = float(v.mean())
+            d[key + "_se"] = float(v.std(ddof=1) / np.sqrt(len(v))) if len(v) > 1 else None
+        out.append(d)
+    return out
+
+
 def round_half_even(x: float) -> int:
     return int(np.round(x))
 
@@ -70,6 +86,8 @@ def main(argv=None):
     ap.add_argument("--uncapped", action="store_true", help="audit the cap without imposing it")
     ap.add_argument("--lag", type=int, default=1, help="lag of the coupled pairs")
     ap.add_argument("--methods", default="SS,RU,SW,cRU,cSW,cSW-nr", help="subset of the methods")
+    ap.add_argument("--executions", type=int, default=1,
+                    help="independent executions per cell (new seeds), summarised as mean and SE")
     a = ap.parse_args(argv)
     fn, fp = (float(v) for v in a.noise.split(","))
     inst = synth.make_instance(a.n, a.m, a.deg, a.positives, fp, fn, a.positives / a.n, 5007, 9007)
@@ -92,10 +110,10 @@ def main(argv=None):
     }
     methods = {m: methods[m] for m in a.methods.split(",")}
     rows = []
-    for s in (int(v) for v in a.sweeps.split(",")):
+    for e, s in ((e, s) for e in range(a.executions) for s in (int(v) for v in a.sweeps.split(","))):
         M = s * a.n_active
         b = round_half_even(0.1 * M)
-        for name, kw in methods.items():
+        for ci, (name, kw) in enumerate(methods.items()):
             if kw["coupled"]:
                 cap = a.cap_sweeps * a.n_active
                 kw2 = dict(kw, k=b + 1, ell=M, slots=a.slots, tau_audit=cap, lag=a.lag)
@@ -105,9 +123,11 @@ def main(argv=None):
                 kw2 = dict(kw, burn=b, length=M - b, slots=2 * a.slots)
             t1 = time.perf_counter()
             kw2.setdefault("horizon", horizon)
-            est, act, st = _decode(ctx, inst, n_active=a.n_active, seed=a.seed + 100 * s + len(rows), **kw2)
+            pos = [int(v) for v in a.sweeps.split(",")].index(s) * len(methods) + ci
+            seed = a.seed + 100 * s + pos + 1000003 * e
+            est, act, st = _decode(ctx, inst, n_active=a.n_active, seed=seed, **kw2)
             assert np.array_equal(act, active)
-            rows.append({"sweeps": s, "method": name, "mae_all": float(np.mean(np.abs(est - ref))),
+            rows.append({"execution": e, "sweeps": s, "method": name, "mae_all": float(np.mean(np.abs(est - ref))),
                          "mae_top10": float(np.mean(np.abs(est[top] - ref[top]))),
                          "site_updates": st["site_updates"], "kernel_ms": st["kernel_ms"],
                          "step_limit_hits": st["step_limit_hits"], "reps_retained": st["reps_retained"],
@@ -122,7 +142,7 @@ def main(argv=None):
                              site_updates=st_ref["site_updates"], top10=[int(active[i]) for i in top]),
            "slots_coupled": a.slots, "slots_uncoupled": 2 * a.slots, "horizon_sweeps": a.horizon_sweeps,
            "meeting_cap_sweeps": None if a.uncapped else a.cap_sweeps, "lag": a.lag,
-           "rows": rows}
+           "executions": a.executions, "rows": rows, "summary": _summary(rows)}
     print(json.dumps(out), flush=True)
     ctx.close()
     return out

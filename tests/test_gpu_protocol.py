@@ -12,9 +12,16 @@ def test_protocol_small():
     from paper_2608_30239_gb300 import build, protocol
     build.build()
     out = protocol.main(["--n", "200", "--m", "20", "--deg", "3", "--n-active", "100", "--sweeps", "1,3",
-                         "--slots", "2048", "--ref-burn", "50", "--ref-sweeps", "200", "--ref-chains", "2048"])
+                         "--slots", "2048", "--ref-burn", "50", "--ref-sweeps", "200", "--ref-chains", "2048",
+                         "--executions", "2"])
     rows = out["rows"]
-    assert [r["method"] for r in rows] == ["SS", "RU", "SW", "cRU", "cSW", "cSW-nr"] * 2
+    assert [r["method"] for r in rows] == ["SS", "RU", "SW", "cRU", "cSW", "cSW-nr"] * 4
+    assert [r["execution"] for r in rows] == [0] * 12 + [1] * 12
+    summ = out["summary"]
+    assert len(summ) == 12 and all(c["n"] == 2 and c["mae_all_se"] is not None for c in summ)
+    first = {(r["sweeps"], r["method"]): r["mae_all"] for r in rows if r["execution"] == 0}
+    second = {(r["sweeps"], r["method"]): r["mae_all"] for r in rows if r["execution"] == 1}
+    assert first != second                 # new seeds per execution
     assert all(np.isfinite(r["mae_all"]) and np.isfinite(r["mae_top10"]) for r in rows)
     assert all(r["mean_tau_sweeps"] is not None and r["mean_tau_sweeps"] > 0 for r in rows if r["method"][0] == "c")
     assert all(r["site_updates"] > 0 for r in rows)
