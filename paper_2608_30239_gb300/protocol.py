@@ -109,34 +109,36 @@ def main(argv=None):
         "cSW-nr": dict(coupled=True, scan=mcpd.MCPD_SCAN_SCORE, horizon=0),
     }
     methods = {m: methods[m] for m in a.methods.split(",")}
+    sweeps = [int(v) for v in a.sweeps.split(",")]
     rows = []
-    for e, s in ((e, s) for e in range(a.executions) for s in (int(v) for v in a.sweeps.split(","))):
-        M = s * a.n_active
-        b = round_half_even(0.1 * M)
-        for ci, (name, kw) in enumerate(methods.items()):
-            if kw["coupled"]:
-                cap = a.cap_sweeps * a.n_active
-                kw2 = dict(kw, k=b + 1, ell=M, slots=a.slots, tau_audit=cap, lag=a.lag)
-                if not a.uncapped:
-                    kw2["meeting_cap"] = cap
-            else:
-                kw2 = dict(kw, burn=b, length=M - b, slots=2 * a.slots)
-            t1 = time.perf_counter()
-            kw2.setdefault("horizon", horizon)
-            pos = [int(v) for v in a.sweeps.split(",")].index(s) * len(methods) + ci
-            seed = a.seed + 100 * s + pos + 1000003 * e
-            est, act, st = _decode(ctx, inst, n_active=a.n_active, seed=seed, **kw2)
-            assert np.array_equal(act, active)
-            rows.append({"execution": e, "sweeps": s, "method": name, "mae_all": float(np.mean(np.abs(est - ref))),
-                         "mae_top10": float(np.mean(np.abs(est[top] - ref[top]))),
-                         "site_updates": st["site_updates"], "kernel_ms": st["kernel_ms"],
-                         "step_limit_hits": st["step_limit_hits"], "reps_retained": st["reps_retained"],
-                         "mean_tau_sweeps": (st["sum_tau"] / max(1, st["reps_retained"]) / a.n_active) if kw["coupled"] else None,
-                         "max_tau_sweeps": (st["max_tau"] / a.n_active) if kw["coupled"] else None,
-                         "reps_started": st["reps_started"],
-                         "cap_hits": st["tau_over_audit"] if kw["coupled"] else None,
-                         "cap_hit_rate": (st["tau_over_audit"] / max(1, st["reps_started"])) if kw["coupled"] else None,
-                         "seconds": time.perf_counter() - t1})
+    for e in range(a.executions):
+        for si, s in enumerate(sweeps):
+            M = s * a.n_active
+            b = round_half_even(0.1 * M)
+            for ci, (name, kw) in enumerate(methods.items()):
+                if kw["coupled"]:
+                    cap = a.cap_sweeps * a.n_active
+                    kw2 = dict(kw, k=b + 1, ell=M, slots=a.slots, tau_audit=cap, lag=a.lag)
+                    if not a.uncapped:
+                        kw2["meeting_cap"] = cap
+                else:
+                    kw2 = dict(kw, burn=b, length=M - b, slots=2 * a.slots)
+                t1 = time.perf_counter()
+                kw2.setdefault("horizon", horizon)
+                # one seed per (length, method) cell, shifted for each further execution
+                seed = a.seed + 100 * s + si * len(methods) + ci + 1000003 * e
+                est, act, st = _decode(ctx, inst, n_active=a.n_active, seed=seed, **kw2)
+                assert np.array_equal(act, active)
+                rows.append({"execution": e, "sweeps": s, "method": name, "mae_all": float(np.mean(np.abs(est - ref))),
+                             "mae_top10": float(np.mean(np.abs(est[top] - ref[top]))),
+                             "site_updates": st["site_updates"], "kernel_ms": st["kernel_ms"],
+                             "step_limit_hits": st["step_limit_hits"], "reps_retained": st["reps_retained"],
+                             "mean_tau_sweeps": (st["sum_tau"] / max(1, st["reps_retained"]) / a.n_active) if kw["coupled"] else None,
+                             "max_tau_sweeps": (st["max_tau"] / a.n_active) if kw["coupled"] else None,
+                             "reps_started": st["reps_started"],
+                             "cap_hits": st["tau_over_audit"] if kw["coupled"] else None,
+                             "cap_hit_rate": (st["tau_over_audit"] / max(1, st["reps_started"])) if kw["coupled"] else None,
+                             "seconds": time.perf_counter() - t1})
     out = {"instance": dict(n=a.n, m=a.m, deg=a.deg, positives=a.positives, fn=fn, fp=fp, n_active=a.n_active),
            "reference": dict(burn_sweeps=a.ref_burn, sweeps=a.ref_sweeps, chains=a.ref_chains, seconds=t_ref,
                              site_updates=st_ref["site_updates"], top10=[int(active[i]) for i in top]),

@@ -1,0 +1,24 @@
+"""The method-comparison driver's per-cell summary over executions (host logic, no GPU)."""
+import math
+
+import numpy as np
+
+from paper_2608_30239_gb300.protocol import _summary
+
+
+def test_summary_mean_and_standard_error():
+    rows = []
+    vals = {("cSW", 1): [1.0, 2.0, 4.0], ("SS", 1): [3.0, 3.0, 3.0], ("cSW", 3): [5.0]}
+    for (m, s), vs in vals.items():
+        for e, v in enumerate(vs):
+            rows.append({"execution": e, "sweeps": s, "method": m, "mae_all": v, "mae_top10": 2 * v,
+                         "kernel_ms": 0.5})
+    summ = {(c["sweeps"], c["method"]): c for c in _summary(rows)}
+    c = summ[(1, "cSW")]
+    assert c["n"] == 3 and math.isclose(c["mae_all"], 7 / 3)
+    sd = math.sqrt(((1 - 7 / 3) ** 2 + (2 - 7 / 3) ** 2 + (4 - 7 / 3) ** 2) / 2)
+    assert math.isclose(c["mae_all_se"], sd / math.sqrt(3))
+    assert math.isclose(c["mae_top10"], 14 / 3) and math.isclose(c["mae_top10_se"], 2 * sd / math.sqrt(3))
+    assert summ[(1, "SS")]["mae_all_se"] == 0.0
+    assert summ[(3, "cSW")]["n"] == 1 and summ[(3, "cSW")]["mae_all_se"] is None
+    assert np.isclose(summ[(3, "cSW")]["kernel_ms"], 0.5)
