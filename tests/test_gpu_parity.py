@@ -297,6 +297,31 @@ def test_lag_degree_six(ctx):
     _assert_same(g, o)
 
 
+@pytest.mark.parametrize("case", ["one_slot", "all_negative", "all_positive", "one_active"])
+def test_degenerate_inputs(ctx, case):
+    """Edge cases: a single slot (its standard error is undefined, NaN on both sides), every pool
+    negative, every pool positive, and pruning to a single active clone; bit-exact against the
+    oracle."""
+    import dataclasses
+    inst = synth.tiny_config(3)
+    P, B, n_active = 777, 90, 0
+    if case == "one_slot":
+        P = 1
+    elif case == "all_negative":
+        inst = dataclasses.replace(inst, y=np.zeros_like(inst.y))
+    elif case == "all_positive":
+        inst = dataclasses.replace(inst, y=np.ones_like(inst.y))
+    else:
+        n_active = 1
+    g = _gpu_run(ctx, inst, slots=P, k=3, ell=20, horizon=B, seed=61, n_active=n_active, record_slots=True)
+    o = _oracle_run(inst, P, 3, 20, B, 61, n_active=n_active)
+    _assert_same(g, o)
+    if case == "one_slot":
+        assert np.all(np.isnan(g["se"])) and np.all(np.isfinite(g["est"]))
+    if case == "one_active":
+        assert g["est"].shape == (1,)
+
+
 def test_step_limit_reports_error_and_context_survives(ctx):
     from paper_2608_30239_gb300 import mcpd
     inst = synth.tiny_config(1)
