@@ -50,7 +50,10 @@ extern "C" {
 /* Pooling design as a clone -> pool CSR (the nonzeros of A by column).
  * clone_pools[clone_ptr[i] .. clone_ptr[i+1]) lists the pools holding clone i, strictly
  * increasing, each in [0, n_pools).  Limits of this build: n_clones <= 65535, n_pools <= 1022,
- * at most 8 pools per clone, at most 255 clones per pool. */
+ * at most 8 pools per clone, at most 255 clones per pool; one chain's state (ceil(n_active / 32)
+ * bit words and ceil((n_pools + 1) / 4) count words) at most 256 words, so that 15-bit offsets
+ * address it; and, for a single instance, its tables (24 bytes per active clone) and one warp's
+ * pair state within the device's shared memory per block.  MCPD_ETOO_LARGE otherwise. */
 typedef struct mcpd_design {
     int32_t n_clones;          /* n */
     int32_t n_pools;           /* m */

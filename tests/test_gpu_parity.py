@@ -322,6 +322,33 @@ def test_degenerate_inputs(ctx, case):
         assert g["est"].shape == (1,)
 
 
+def test_near_maximum_pair_state(ctx):
+    """6560 clones x 200 pools, 4 pools per clone: a chain's column is 256 words, the most that
+    15-bit count offsets address, and the staged tables (161 KB) with one warp region and one Y
+    region fill 221 KB of shared memory, so the launch runs one warp per block; bit-exact against
+    the oracle with refill."""
+    inst = synth.make_instance(6560, 200, 4, 5, 0.10, 0.20, 5 / 6560, 4401, 4402)
+    P, B = 96, 600
+    g = _gpu_run(ctx, inst, slots=P, k=20, ell=200, horizon=B, seed=71, record_slots=True)
+    o = _oracle_run(inst, P, 20, 200, B, 71)
+    _assert_same(g, o)
+    assert int(g["plan"].info[7]) == 1                  # warps per block
+
+
+def test_pair_state_too_large_is_refused(ctx):
+    """A design whose pair state is beyond 15-bit count offsets (60000 clones) is refused when the
+    plan is made (MCPD_ETOO_LARGE); the context still decodes afterwards."""
+    from paper_2608_30239_gb300 import mcpd
+    big = synth.make_instance(60000, 1022, 3, 5, 0.05, 0.10, 5 / 60000, 4403, 4404)
+    with pytest.raises(mcpd.McpdError) as ei:
+        mcpd.Plan(ctx, big, slots=64, k=20, ell=200, horizon=0, seed=1)
+    assert ei.value.code == mcpd.MCPD_ETOO_LARGE
+    inst = synth.tiny_config(2)
+    g = _gpu_run(ctx, inst, slots=256, k=3, ell=20, horizon=0, seed=5)
+    o = _oracle_run(inst, 256, 3, 20, 0, 5)
+    _assert_same(g, o, per_slot=False)
+
+
 def test_step_limit_reports_error_and_context_survives(ctx):
     from paper_2608_30239_gb300 import mcpd
     inst = synth.tiny_config(1)
