@@ -8,7 +8,27 @@
 #include <string>
 #include <vector>
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define MCPD_NVTX 1
+#endif
+
 #include "mcpd_internal.h"
+
+namespace {
+// A named NVTX range over one library call (host side; a no-op unless a profiler is attached, and
+// compiled out where the toolkit has no NVTX headers).
+struct NvtxRange {
+#ifdef MCPD_NVTX
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+#else
+    explicit NvtxRange(const char *) {}
+#endif
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 struct mcpd_plan {
     mcpd_ctx *ctx = nullptr;
@@ -87,6 +107,7 @@ void mcpd_plan_destroy(mcpd_plan *pl) {
 
 int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
                      const mcpd_params *params, mcpd_plan **out) {
+    NvtxRange nvtx_range("mcpd.plan_create");
     if (!ctx || !out) return MCPD_EINVAL;
     *out = nullptr;
     mcpd_plan *pl = new (std::nothrow) mcpd_plan();
@@ -196,6 +217,7 @@ int mcpd_plan_active(const mcpd_plan *pl, int32_t *active) {
 }
 
 int mcpd_run_async(mcpd_ctx *ctx, mcpd_plan *pl, double *est_dev, double *se_dev) {
+    NvtxRange nvtx_range("mcpd.run");
     if (!ctx || !pl || !est_dev || !se_dev) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
     const mcpd::Tables &t = pl->t;
@@ -230,6 +252,7 @@ int mcpd_run_async(mcpd_ctx *ctx, mcpd_plan *pl, double *est_dev, double *se_dev
 }
 
 int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *pl, mcpd_stats *stats) {
+    NvtxRange nvtx_range("mcpd.collect");
     if (!ctx || !pl) return MCPD_EINVAL;
     if (!pl->ran) return set_err(ctx, MCPD_EINVAL, "no run to collect");
     CU(cudaSetDevice(ctx->device));
@@ -290,6 +313,7 @@ int mcpd_fetch(mcpd_ctx *ctx, const mcpd_plan *pl, int what, void *host_dst, siz
 int mcpd_decode(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
                 const mcpd_params *params, double *est, double *se, int32_t *active,
                 mcpd_stats *stats) {
+    NvtxRange nvtx_range("mcpd.decode");
     if (!ctx || !design || !est || !se) return MCPD_EINVAL;
     mcpd_plan *pl = nullptr;
     int rc = mcpd_plan_create(ctx, design, y, params, &pl);
@@ -319,6 +343,7 @@ int mcpd_decode(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
 
 int mcpd_inspect(const mcpd_design *design, const uint8_t *y, const mcpd_params *params,
                  int64_t info[16], int32_t *active, double *w, uint64_t *alias, uint64_t *T) {
+    NvtxRange nvtx_range("mcpd.inspect");
     if (!info) return MCPD_EINVAL;
     mcpd::Tables t;
     std::string err;
@@ -504,6 +529,7 @@ void mcpd_batch_destroy(mcpd_batch *b) {
 int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
                       const uint8_t *const *ys, const mcpd_params *params, int32_t order_mode,
                       mcpd_batch **out) {
+    NvtxRange nvtx_range("mcpd.batch_create");
     if (!ctx || !out || n_inst < 1 || !designs || !ys || !params) return MCPD_EINVAL;
     const int32_t mode = order_mode & 0xFF, want_classes = (order_mode >> 8) & 0xFF;
     if (mode > 1 || want_classes > 8 || (order_mode >> 16) != 0) return set_err(ctx, MCPD_EINVAL, "order_mode: order 0 or 1, classes 0..8");
@@ -711,6 +737,7 @@ int mcpd_batch_set_shape(mcpd_ctx *ctx, mcpd_batch *b, int32_t lanes_per_pair, i
 }
 
 int mcpd_batch_run_async(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev) {
+    NvtxRange nvtx_range("mcpd.batch_run");
     if (!ctx || !b || !est_dev || !se_dev) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
     CU(cudaEventRecord(b->ev0, ctx->stream));
@@ -723,6 +750,7 @@ int mcpd_batch_run_async(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *
 }
 
 int mcpd_batch_capture_graph(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev) {
+    NvtxRange nvtx_range("mcpd.batch_capture_graph");
     if (!ctx || !b || !est_dev || !se_dev) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
     if (!ctx->stream) return set_err(ctx, MCPD_EINVAL, "graph capture needs a non-default stream");
@@ -740,6 +768,7 @@ int mcpd_batch_capture_graph(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, doub
 }
 
 int mcpd_batch_launch_graph(mcpd_ctx *ctx, mcpd_batch *b) {
+    NvtxRange nvtx_range("mcpd.batch_launch_graph");
     if (!ctx || !b || !b->graph_exec) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
     CU(cudaEventRecord(b->ev0, ctx->stream));
@@ -751,6 +780,7 @@ int mcpd_batch_launch_graph(mcpd_ctx *ctx, mcpd_batch *b) {
 }
 
 int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *b, mcpd_stats *stats) {
+    NvtxRange nvtx_range("mcpd.batch_collect");
     if (!ctx || !b) return MCPD_EINVAL;
     if (!b->ran) return set_err(ctx, MCPD_EINVAL, "no run to collect");
     CU(cudaSetDevice(ctx->device));
@@ -806,6 +836,7 @@ int mcpd_batch_fetch(mcpd_ctx *ctx, const mcpd_batch *b, int32_t inst, int what,
 int mcpd_batch_autotune(mcpd_ctx *ctx, mcpd_batch *b, const int32_t *cand_lanes,
                         const int32_t *cand_warps, int32_t n_cand, int32_t reps, double *est_dev,
                         double *se_dev, int32_t *best_index, double *times) {
+    NvtxRange nvtx_range("mcpd.batch_autotune");
     if (!ctx || !b || !cand_lanes || !cand_warps || n_cand < 1 || reps < 1 || !est_dev || !se_dev) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
     double best = 1e300;
