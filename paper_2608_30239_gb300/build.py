@@ -79,7 +79,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         sys.stdout.write("".join(logs))
     tmp = LIB + f".tmp{os.getpid()}"
     link = [nvcc, ARCH, "-shared", "-o", tmp, objs["tables"], objs["api"], objs["kernels"],
-            objs["noalloc"], objs["mlp"], objs["group"], "-cudart", "static", "-ldl"]
+            objs["noalloc"], objs["mlp"], objs["group"], "-cudart", "static"]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
     return LIB
