@@ -116,6 +116,10 @@ def test_window_and_horizon_defaults(L, oracle_lib):
     (dict(k=2, ell=20, meeting_cap=19), mcpd.MCPD_EINVAL),
     (dict(k=2, ell=20, meeting_cap=30, tau_audit=31), mcpd.MCPD_EINVAL),
     (dict(k=2, ell=20, meeting_cap=(1 << 31) + 1), mcpd.MCPD_EINVAL),
+    (dict(lag=-1), mcpd.MCPD_EINVAL),
+    (dict(lag=(1 << 20) + 1), mcpd.MCPD_EINVAL),
+    (dict(k=2, ell=20, lag=30, meeting_cap=25), mcpd.MCPD_EINVAL),
+    (dict(k=2, ell=20, lag=30, step_limit=29), mcpd.MCPD_EINVAL),
 ])
 def test_invalid_parameters_rejected(L, kw, code):
     inst = synth.tiny_config(1)
@@ -162,3 +166,14 @@ def test_meeting_cap_replaces_the_step_limit(L):
     unc = mcpd.mcpd_inspect(inst, slots=8, horizon=100, coupled=False, burn=2, length=20,
                             meeting_cap=5, step_limit=10 ** 6)
     assert unc["info"][12] == 10 ** 6
+
+
+def test_lag_sets_the_smallest_replication_cost(L):
+    """A lag L makes every replication cost at least max(l, L) progress units, so the number of
+    N*_p buckets is B // max(l, L); lag 0 and 1 are the paper's one-lag pair."""
+    inst = synth.tiny_config(1)
+    base = dict(slots=8, horizon=400, k=2, ell=20)
+    assert mcpd.mcpd_inspect(inst, **base)["info"][1] == 400 // 20
+    assert mcpd.mcpd_inspect(inst, lag=1, **base)["info"][1] == 400 // 20
+    assert mcpd.mcpd_inspect(inst, lag=0, **base)["info"][1] == 400 // 20
+    assert mcpd.mcpd_inspect(inst, lag=50, **base)["info"][1] == 400 // 50
