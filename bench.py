@@ -364,7 +364,13 @@ def main():
         total_s = float(t.item())
     su_step = stats[-1]["site_updates"]
     pu_step = stats[-1]["progress_units"]
-    value = su_step * args.steps * world / total_s
+    # every rank's site updates and retained replications per step, summed
+    su_all_step, reps_all_step = float(su_step), float(stats[-1]["reps_retained"])
+    if dist:
+        t = torch.tensor([su_all_step, reps_all_step], dtype=torch.float64, device=f"cuda:{device}")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        su_all_step, reps_all_step = float(t[0].item()), float(t[1].item())
+    value = su_all_step * args.steps / total_s
     kernel_ms = statistics.mean(s["kernel_ms"] for s in stats)
 
     # end to end through the public host-array API: plan, upload, run, download, every step
@@ -382,7 +388,12 @@ def main():
     n_thresholds = 7 * 64 if 3 <= uniform_deg <= 6 else 81   # mask-indexed for uniform degrees 3..6
     h2d = na * 8 + na * 16 + n_thresholds * 8        # alias words, clone rows, thresholds
     d2h = 2 * na * 8 + 16 * 8 + 4                    # estimates, standard errors, counters, flag
-    e2e_val = su_step * world / statistics.mean(e2e_times)
+    e2e_s = statistics.mean(e2e_times)
+    if dist:                                     # the slowest rank's end-to-end time
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{device}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = su_all_step / e2e_s
 
     peaks, peak_kind = _peaks()
     props = torch.cuda.get_device_properties(device)
@@ -407,13 +418,13 @@ def main():
                                        "progress_units_per_step": pu_step,
                                        "site_updates_per_step": su_step,
                                        "replications_per_step": stats[-1]["reps_retained"],
-                                       "estimators_per_s": stats[-1]["reps_retained"] * args.steps * world / total_s,
+                                       "estimators_per_s": reps_all_step * args.steps / total_s,
                                        "pairs_kernel_ms": kernel_ms,
                                        "max_se": float(se.max().item()),
                                        "wall_s_timed": wall}),
             "roofline": roofline,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h, "seconds_per_step": statistics.mean(e2e_times)},
+                    "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s},
             "gpu_launches": 2 * args.steps,
             "clocks": clk}
     if rank == 0 and not args.no_batched:
