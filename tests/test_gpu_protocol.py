@@ -1,4 +1,4 @@
-"""The method comparison driver (five methods and the no-refill ablation) runs end to end on a small instance (needs a GB300)."""
+"""The method comparison program (five methods and the no-refill ablation) runs end to end on a small instance (needs a GB300)."""
 import numpy as np
 import pytest
 

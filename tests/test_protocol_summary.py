@@ -1,4 +1,4 @@
-"""The method-comparison driver's per-cell summary over executions (host logic, no GPU)."""
+"""The method-comparison program's per-cell summary over executions (host logic, no GPU)."""
 import math
 
 import numpy as np
