@@ -52,12 +52,23 @@ int set_err(mcpd_ctx *ctx, int code, const std::string &msg) {
     return code;
 }
 
+int cu_status(mcpd_ctx *ctx, cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return MCPD_OK;
+    return set_err(ctx, e == cudaErrorMemoryAllocation ? MCPD_ENOMEM : MCPD_ECUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// CU returns the library's status on a failed CUDA call; CU_OR runs `cleanup` first (used where
+// the call fails after the object under construction holds device memory).
 #define CU(call)                                                                              \
     do {                                                                                      \
-        cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
-            return set_err(ctx, e_ == cudaErrorMemoryAllocation ? MCPD_ENOMEM : MCPD_ECUDA,   \
-                           std::string(#call) + ": " + cudaGetErrorString(e_));               \
+        const int r_ = cu_status(ctx, (call), #call);                                         \
+        if (r_ != MCPD_OK) return r_;                                                         \
+    } while (0)
+#define CU_OR(call, cleanup)                                                                  \
+    do {                                                                                      \
+        const int r_ = cu_status(ctx, (call), #call);                                         \
+        if (r_ != MCPD_OK) { cleanup; return r_; }                                            \
     } while (0)
 
 template <typename T>
@@ -170,13 +181,13 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
         ALLOC(kp.trace_G, static_cast<size_t>(pl->n_trace) * t.na);
     }
 #undef ALLOC
-    CU(cudaMemcpyAsync(d_alias, t.alias.data(), t.alias.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(d_rows, mcpd::kernel_rows(t).data(), mcpd::kernel_rows(t).size() * 2, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(d_T, mcpd::kernel_T(t).data(), mcpd::kernel_T(t).size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+    CU_OR(cudaMemcpyAsync(d_alias, t.alias.data(), t.alias.size() * 8, cudaMemcpyHostToDevice, ctx->stream), mcpd_plan_destroy(pl));
+    CU_OR(cudaMemcpyAsync(d_rows, mcpd::kernel_rows(t).data(), mcpd::kernel_rows(t).size() * 2, cudaMemcpyHostToDevice, ctx->stream), mcpd_plan_destroy(pl));
+    CU_OR(cudaMemcpyAsync(d_T, mcpd::kernel_T(t).data(), mcpd::kernel_T(t).size() * 8, cudaMemcpyHostToDevice, ctx->stream), mcpd_plan_destroy(pl));
     if (!t.Tnu.empty())
-        CU(cudaMemcpyAsync(d_Tnu, t.Tnu.data(), t.Tnu.size() * 8, cudaMemcpyHostToDevice, ctx->stream));
+        CU_OR(cudaMemcpyAsync(d_Tnu, t.Tnu.data(), t.Tnu.size() * 8, cudaMemcpyHostToDevice, ctx->stream), mcpd_plan_destroy(pl));
     if (!t.init_pairs.empty())
-        CU(cudaMemcpyAsync(d_init, t.init_pairs.data(), t.init_pairs.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+        CU_OR(cudaMemcpyAsync(d_init, t.init_pairs.data(), t.init_pairs.size() * 4, cudaMemcpyHostToDevice, ctx->stream), mcpd_plan_destroy(pl));
     kp.alias = d_alias; kp.rows = d_rows; kp.T = d_T; kp.Tnu = t.Tnu.empty() ? nullptr : d_Tnu;
     kp.init_pairs = d_init; kp.n_init_pairs = static_cast<int32_t>(t.init_pairs.size());
     kp.na = t.na; kp.m = t.m; kp.W = t.W; kp.Mp = t.Mp; kp.wpp = t.wpp; kp.deg = t.deg_max; kp.udeg = t.udeg;
@@ -192,9 +203,9 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     kp.smem_tables = static_cast<uint32_t>(tables);
     kp.nT = static_cast<int32_t>(mcpd::kernel_T(t).size());
     kp.y_regions = shape.y_regions;
-    CU(cudaEventCreate(&pl->ev0));
-    CU(cudaEventCreate(&pl->ev1));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU_OR(cudaEventCreate(&pl->ev0), mcpd_plan_destroy(pl));
+    CU_OR(cudaEventCreate(&pl->ev1), mcpd_plan_destroy(pl));
+    CU_OR(cudaStreamSynchronize(ctx->stream), mcpd_plan_destroy(pl));
     *out = pl;
     return MCPD_OK;
 }
@@ -694,14 +705,14 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         const int32_t i = b->order[pos];
         for (int32_t a = 0; a < b->t[i].na; ++a) { ci[b->out_offset[i] + a] = pos; cl[b->out_offset[i] + a] = a; }
     }
-    CU(cudaMemcpyAsync(d_tables, host.data(), table_bytes, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(b->d_insts, b->insts.data(), sizeof(mcpd::InstDesc) * n_inst, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(b->d_clone_inst, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
-    CU(cudaMemcpyAsync(b->d_clone_local, cl.data(), cl.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+    CU_OR(cudaMemcpyAsync(d_tables, host.data(), table_bytes, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
+    CU_OR(cudaMemcpyAsync(b->d_insts, b->insts.data(), sizeof(mcpd::InstDesc) * n_inst, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
+    CU_OR(cudaMemcpyAsync(b->d_clone_inst, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
+    CU_OR(cudaMemcpyAsync(b->d_clone_local, cl.data(), cl.size() * 4, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
     if ((rc = batch_shape(ctx, b, 0)) != MCPD_OK) { mcpd_batch_destroy(b); return rc; }
-    CU(cudaEventCreate(&b->ev0));
-    CU(cudaEventCreate(&b->ev1));
-    CU(cudaStreamSynchronize(ctx->stream));
+    CU_OR(cudaEventCreate(&b->ev0), mcpd_batch_destroy(b));
+    CU_OR(cudaEventCreate(&b->ev1), mcpd_batch_destroy(b));
+    CU_OR(cudaStreamSynchronize(ctx->stream), mcpd_batch_destroy(b));
     *out = b;
     return MCPD_OK;
 }
