@@ -280,6 +280,20 @@ def run_reference(args, rank, world):
     return 0
 
 
+def reduce_over_ranks(dist, device, total_s, su_step, reps_step, e2e_s):
+    """Whole-job figures from each rank's own: the slowest rank's timed seconds and end-to-end
+    seconds per step (MAX), and one step's site updates and retained replications summed over the
+    ranks (SUM).  `dist` is None for a single process; `device` holds the reduced tensors."""
+    if dist is None:
+        return float(total_s), float(su_step), float(reps_step), float(e2e_s)
+    import torch
+    slow = torch.tensor([float(total_s), float(e2e_s)], dtype=torch.float64, device=device)
+    dist.all_reduce(slow, op=dist.ReduceOp.MAX)
+    work = torch.tensor([float(su_step), float(reps_step)], dtype=torch.float64, device=device)
+    dist.all_reduce(work, op=dist.ReduceOp.SUM)
+    return float(slow[0].item()), float(work[0].item()), float(work[1].item()), float(slow[1].item())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -358,19 +372,8 @@ def main():
 
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1000.0
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64, device=f"cuda:{device}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
     su_step = stats[-1]["site_updates"]
     pu_step = stats[-1]["progress_units"]
-    # every rank's site updates and retained replications per step, summed
-    su_all_step, reps_all_step = float(su_step), float(stats[-1]["reps_retained"])
-    if dist:
-        t = torch.tensor([su_all_step, reps_all_step], dtype=torch.float64, device=f"cuda:{device}")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        su_all_step, reps_all_step = float(t[0].item()), float(t[1].item())
-    value = su_all_step * args.steps / total_s
     kernel_ms = statistics.mean(s["kernel_ms"] for s in stats)
 
     # end to end through the public host-array API: plan, upload, run, download, every step
@@ -388,11 +391,9 @@ def main():
     n_thresholds = 7 * 64 if 3 <= uniform_deg <= 6 else 81   # mask-indexed for uniform degrees 3..6
     h2d = na * 8 + na * 16 + n_thresholds * 8        # alias words, clone rows, thresholds
     d2h = 2 * na * 8 + 16 * 8 + 4                    # estimates, standard errors, counters, flag
-    e2e_s = statistics.mean(e2e_times)
-    if dist:                                     # the slowest rank's end-to-end time
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{device}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    total_s, su_all_step, reps_all_step, e2e_s = reduce_over_ranks(
+        dist, f"cuda:{device}", total_s, su_step, stats[-1]["reps_retained"], statistics.mean(e2e_times))
+    value = su_all_step * args.steps / total_s
     e2e_val = su_all_step / e2e_s
 
     peaks, peak_kind = _peaks()
