@@ -77,7 +77,7 @@ def lib(build_if_missing: bool = False):
         if not os.path.exists(_build.LIB):
             raise ImportError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
         L = C.CDLL(_build.LIB)
-        P, I32, I64 = C.c_void_p, C.c_int32, C.c_int64
+        P, I64 = C.c_void_p, C.c_int64
         sig = {
             "mcpd_ctx_create": (C.c_int, [C.c_int, P, C.POINTER(P)]),
             "mcpd_ctx_destroy": (None, [P]),
@@ -114,7 +114,6 @@ def lib(build_if_missing: bool = False):
             f = getattr(L, name)
             f.restype = res
             f.argtypes = args
-        _ = (I32,)
         _lib = L
     return _lib
 
@@ -125,6 +124,21 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return C.c_void_p(a.data_ptr())
     return a.ctypes.data_as(C.c_void_p)
+
+
+def _check_out(est, se, need, device):
+    """Refuses output buffers the kernels could write past: each must be a contiguous float64 CUDA
+    tensor on the context's device with at least `need` elements (one per active clone)."""
+    import torch
+    for name, a in (("est", est), ("se", se)):
+        if not isinstance(a, torch.Tensor):
+            raise TypeError(f"{name}: a torch tensor is required, got {type(a).__name__}")
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError(f"{name}: a contiguous float64 tensor is required, got {a.dtype}")
+        if a.numel() < need:
+            raise ValueError(f"{name}: {a.numel()} elements, {need} needed")
+        if not a.is_cuda or a.device.index != device:
+            raise ValueError(f"{name}: on {a.device}, the context is on cuda:{device}")
 
 
 class _Keep:
@@ -208,7 +222,7 @@ class Context:
         if rc != MCPD_OK:
             raise McpdError(rc, "mcpd_ctx_create")
         self.h = h
-        self.device = device
+        self.device = int(device)
 
     def error(self) -> str:
         return lib().mcpd_last_error(self.h).decode()
@@ -286,6 +300,7 @@ class Plan:
         lib().mcpd_plan_active(h, _ptr(self.active))
 
     def run_async(self, est_dev, se_dev):
+        _check_out(est_dev, se_dev, self.n_active, self.ctx.device)
         self.ctx.check(lib().mcpd_run_async(self.ctx.h, self.h, _ptr(est_dev), _ptr(se_dev)),
                        "mcpd_run_async")
 
@@ -375,10 +390,12 @@ class Batch:
         self.info = self._info()
 
     def run_async(self, est_dev, se_dev):
+        _check_out(est_dev, se_dev, self.total_active, self.ctx.device)
         self.ctx.check(lib().mcpd_batch_run_async(self.ctx.h, self.h, _ptr(est_dev), _ptr(se_dev)),
                        "mcpd_batch_run_async")
 
     def capture_graph(self, est_dev, se_dev):
+        _check_out(est_dev, se_dev, self.total_active, self.ctx.device)
         self.ctx.check(lib().mcpd_batch_capture_graph(self.ctx.h, self.h, _ptr(est_dev), _ptr(se_dev)),
                        "mcpd_batch_capture_graph")
 
@@ -408,6 +425,7 @@ class Batch:
     def autotune(self, est_dev, se_dev, candidates=((1, 0), (8, 0), (16, 0), (32, 0)), reps=1):
         """candidates: (lanes per pair, warps per block) pairs (0 warps: as many as fit).  Returns
         the chosen pair and {pair: mean ms} (-1 where a candidate does not fit)."""
+        _check_out(est_dev, se_dev, self.total_active, self.ctx.device)
         cand = [(int(a), int(b)) for a, b in candidates]
         lanes = np.asarray([c[0] for c in cand], np.int32)
         warps = np.asarray([c[1] for c in cand], np.int32)
