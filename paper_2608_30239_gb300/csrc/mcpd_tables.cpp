@@ -239,19 +239,19 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
         for (int32_t a = 0; a < na; ++a) {
             const uint16_t *src = &t.rows[static_cast<size_t>(a) * kRow];
             uint16_t *dst = &t.rows_mask[static_cast<size_t>(a) * kRow];
-            int32_t n = 0;
-            for (int32_t l = 0; l < t.udeg; ++l) if (src[l] & 0x8000u) dst[n++] = static_cast<uint16_t>(src[l] & 0x7FFFu);
-            const int32_t npos = n;
-            for (int32_t l = 0; l < t.udeg; ++l) if (!(src[l] & 0x8000u)) dst[n++] = src[l];
+            int32_t fill = 0;
+            for (int32_t l = 0; l < t.udeg; ++l) if (src[l] & 0x8000u) dst[fill++] = static_cast<uint16_t>(src[l] & 0x7FFFu);
+            const int32_t npos = fill;
+            for (int32_t l = 0; l < t.udeg; ++l) if (!(src[l] & 0x8000u)) dst[fill++] = src[l];
             dst[kRow - 1] = static_cast<uint16_t>(npos);
         }
         t.T_mask.assign(static_cast<size_t>(kMaskDeg + 1) * 64, 0);
         for (int32_t npos = 0; npos <= kMaskDeg; ++npos)
-            for (int32_t m = 0; m < 64; ++m) {
+            for (int32_t mask = 0; mask < 64; ++mask) {
                 int32_t np = 0, nn = 0;
                 for (int32_t l = 0; l < 6; ++l)
-                    if (m >> l & 1) { if (l < npos) ++np; else ++nn; }
-                t.T_mask[static_cast<size_t>(npos) * 64 + m] = t.T[static_cast<size_t>(np) * kTSide + nn];
+                    if (mask >> l & 1) { if (l < npos) ++np; else ++nn; }
+                t.T_mask[static_cast<size_t>(npos) * 64 + mask] = t.T[static_cast<size_t>(np) * kTSide + nn];
             }
     }
 
