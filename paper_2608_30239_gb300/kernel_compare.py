@@ -10,8 +10,8 @@ fastest kernel time, the draws (progress units) and the batch's launch facts.
 """
 from __future__ import annotations
 
+import argparse
 import json
-import sys
 
 import synth
 
@@ -53,8 +53,10 @@ def _batch(ctx, stream, inst, copies):
 
 
 def main(argv=None):
+    ap = argparse.ArgumentParser(description="single-instance kernel against the batch kernel on the same draws")
+    ap.add_argument("which", nargs="?", default="all", choices=("plan", "batch1", "batch128", "all"))
+    which = ap.parse_args(argv).which
     import torch
-    which = (argv or sys.argv[1:] or ["all"])[0]
     build.build()
     inst = synth.high_noise_config()
     stream = torch.cuda.Stream(0)
