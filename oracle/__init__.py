@@ -27,15 +27,23 @@ ORC_OK, ORC_EINVAL, ORC_ENOMEM, ORC_ESTEP_LIMIT, ORC_EFAITHFUL = 0, -1, -2, -3, 
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-ffp-contract=off keeps every double operation separate)."""
+    """Compile the oracle with gcc (-ffp-contract=off keeps every double operation separate).
+
+    With MCPD_ORACLE_SANITIZE=1 in the environment a separate copy is built and loaded under
+    AddressSanitizer and UndefinedBehaviorSanitizer (the process needs both runtimes preloaded:
+    LD_PRELOAD="$(gcc -print-file-name=libasan.so):$(gcc -print-file-name=libubsan.so)")."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
+    sanitize = os.environ.get("MCPD_ORACLE_SANITIZE") == "1"
+    lib_path = os.path.join(_BUILD, "liboracle_san.so") if sanitize else _LIB
+    if force or not os.path.exists(lib_path) or os.path.getmtime(lib_path) < os.path.getmtime(_SRC):
+        tmp = lib_path + f".tmp{os.getpid()}"
+        opt = (["-O1", "-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+                "-fno-sanitize-recover=undefined"] if sanitize else ["-O2"])
+        cmd = ["gcc", *opt, "-std=gnu11", "-fPIC", "-shared", "-pthread", "-ffp-contract=off",
                "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
         subprocess.check_call(cmd)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 class Run(C.Structure):
