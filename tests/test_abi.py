@@ -77,6 +77,53 @@ def test_host_tables_equal_oracle_tables(L, oracle_lib, case):
     assert np.array_equal(lib_t["T"][:side, :side], ref["T"])
 
 
+def _random_design(rng):
+    """A random design: clone degrees 0..8 (at most the pool count), pools strictly increasing,
+    outcomes at one of four positive rates, and rates / prior drawn from a small grid."""
+    from types import SimpleNamespace
+    n = int(rng.choice([1, 2, 3, 5, 17, 64, 300, 1298]))
+    m = int(rng.choice([1, 2, 5, 9, 48, 97, 400]))
+    dmax = min(m, int(rng.choice([1, 3, 6, 8])))
+    rows = [np.sort(rng.choice(m, size=int(rng.integers(0 if rng.random() < 0.1 else 1, dmax + 1)),
+                               replace=False)) for _ in range(n)]
+    ptr = np.zeros(n + 1, np.int32)
+    ptr[1:] = np.cumsum([len(r) for r in rows])
+    return SimpleNamespace(n=n, m=m, clone_ptr=ptr, clone_pools=np.concatenate(rows).astype(np.int32),
+                           y=(rng.random(m) < rng.choice([0.0, 0.1, 0.5, 1.0])).astype(np.uint8),
+                           fp=float(rng.choice([0.01, 0.1, 0.3, 0.49])),
+                           fn=float(rng.choice([0.01, 0.2, 0.5, 0.7])),
+                           q=float(rng.choice([1e-4, 0.01, 0.2, 0.5])))
+
+
+def test_host_tables_equal_oracle_tables_on_random_designs(L, oracle_lib):
+    """300 seeded random designs (empty clones, pools shared by many clones, all-negative and
+    all-positive outcomes, pruning, the uniform, score and custom scans): every design the library
+    accepts gives the oracle's active set, weights, alias words and thresholds bit for bit."""
+    rng = np.random.default_rng(20261203)
+    compared = 0
+    for _ in range(300):
+        inst = _random_design(rng)
+        scan = int(rng.choice([0, 0, 1, 3]))
+        na = int(rng.choice([0, 0, 1, max(1, inst.n // 3)]))
+        w = rng.random(inst.n) + 0.05 if scan == mcpd.MCPD_SCAN_CUSTOM else None
+        try:
+            lib_t = mcpd.mcpd_inspect(inst, slots=16, horizon=100, scan=scan, n_active=na, scan_weights=w)
+        except mcpd.McpdError as e:          # beyond the library's limits (a pool over 255 clones)
+            assert e.code in (mcpd.MCPD_EINVAL, mcpd.MCPD_ETOO_LARGE)
+            continue
+        M = oracle_lib.Model(inst, n_active=na, scan=scan, custom_w=w)
+        ref = M.tables()
+        assert np.array_equal(lib_t["active"], ref["active"])
+        if scan != mcpd.MCPD_SCAN_CUSTOM:
+            assert np.array_equal(lib_t["w"].view(np.uint64), ref["w"].view(np.uint64))
+        assert np.array_equal(lib_t["alias"] & np.uint64(0xFFFFFFFF), ref["prob"].astype(np.uint64))
+        assert np.array_equal(lib_t["alias"] >> np.uint64(32), ref["alias"].astype(np.uint64))
+        side = M.deg_max + 1
+        assert np.array_equal(lib_t["T"][:side, :side], ref["T"])
+        compared += 1
+    assert compared >= 200
+
+
 def test_custom_weights_tables(L, oracle_lib):
     inst = synth.tiny_config(5)
     w = np.linspace(1.0, 2.0, inst.n)
