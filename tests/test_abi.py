@@ -124,6 +124,52 @@ def test_host_tables_equal_oracle_tables_on_random_designs(L, oracle_lib):
     assert compared >= 200
 
 
+def test_window_horizon_and_buckets_on_random_parameters(L, oracle_lib):
+    """200 seeded parameter sets on the high-noise design (coupled with default or explicit
+    windows, lags, budgets or explicit horizons; uncoupled with burn-in and length): the library's
+    k and l are the paper's window recipe when left to default, its horizon is the budget split
+    over the slots, and its N*_p bucket count is the oracle's for the same run."""
+    import ctypes as C
+    inst = synth.high_noise_config()
+    rng = np.random.default_rng(7)
+    compared = 0
+    for _ in range(200):
+        coupled = bool(rng.random() < 0.7)
+        slots = int(rng.choice([1, 7, 1000, 524288]))
+        kw = dict(slots=slots, coupled=coupled, n_active=int(rng.choice([0, 50, 333])))
+        if coupled:
+            if rng.random() < 0.5:
+                ell = int(rng.integers(1, 5000))
+                kw.update(k=int(rng.integers(0, ell + 1)), ell=ell)
+            kw["lag"] = int(rng.choice([0, 1, 2, 7, 3000]))
+        else:
+            kw.update(scan=mcpd.MCPD_SCAN_UNIFORM, burn=int(rng.integers(0, 400)),
+                      length=int(rng.integers(1, 4000)))
+        if rng.random() < 0.5:
+            kw["budget_site_updates"] = float(rng.choice([1e6, 4e10, 1e12])) * slots / 524288
+        else:
+            kw["horizon"] = int(rng.integers(0, 10 ** 6))
+        try:
+            info = mcpd.mcpd_inspect(inst, **kw)["info"]
+        except mcpd.McpdError as e:
+            assert e.code in (mcpd.MCPD_ETOO_LARGE, mcpd.MCPD_EOVERFLOW)   # bucket or sum limits
+            continue
+        na, nb, B, k, ell = (int(v) for v in info[:5])
+        if coupled and "k" not in kw:
+            assert (k, ell) == oracle_lib.window_defaults(na, 1)
+        elif coupled:
+            assert (k, ell) == (kw["k"], kw["ell"])
+        if coupled and "budget_site_updates" in kw:
+            assert B == synth.budget_horizon(kw["budget_site_updates"], slots)
+        elif "horizon" in kw:
+            assert B == kw["horizon"]
+        run = oracle_lib.Run(k=k, ell=ell, burn=kw.get("burn", 0), length=kw.get("length", 0),
+                             horizon=B, coupled=int(coupled), lag=kw.get("lag", 1))
+        assert nb == int(oracle_lib.lib().orc_num_buckets(C.byref(run)))
+        compared += 1
+    assert compared >= 100
+
+
 def test_custom_weights_tables(L, oracle_lib):
     inst = synth.tiny_config(5)
     w = np.linspace(1.0, 2.0, inst.n)
