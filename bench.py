@@ -127,6 +127,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it: the model name on x86, the implementer and part
+    codes on Arm (where the kernel gives no model name); "unknown" elsewhere."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            fields = [line.split(":", 1) for line in f if ":" in line]
+    except OSError:
+        return "unknown"
+    info = {}
+    for k, v in fields:
+        info.setdefault(k.strip(), v.strip())
+    if "model name" in info:
+        return info["model name"]
+    if "CPU implementer" in info:
+        return f"implementer {info['CPU implementer']} part {info.get('CPU part', '?')}"
+    return "unknown"
+
+
 def cpu_oracle_sample(seconds: float, steps_label: str = ""):
     """The oracle as it stands on the host's cores on a bounded sample of the workload's slots."""
     import oracle
@@ -148,7 +166,7 @@ def cpu_oracle_sample(seconds: float, steps_label: str = ""):
     dt = time.perf_counter() - t0
     st = r["stats"]
     site_updates = 2 * st["draws"] - st["reps"]
-    return {"value": site_updates / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": site_updates / dt, "unit": UNIT, "cores": cores, "cpu_model": cpu_model(), "kind": "oracle",
             "sample": f"{n_slots} of the workload's {SLOTS} slots (slot ids {cores}..{cores + n_slots - 1}), "
                       f"{site_updates} site-updates in {dt:.2f} s with {cores} threads{steps_label}",
             "seconds": dt, "site_updates": site_updates}
@@ -273,7 +291,8 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "impl": "reference", "config": workload_config(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "cpu_model": cpu_model(),
+                             "kind": "oracle",
                              "sample": f"each step a bounded slot sample of ~{args.ref_seconds:.0f} s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

@@ -19,6 +19,7 @@ def test_reference_arm_json_line():
     assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
+    assert isinstance(d["cpu_baseline"]["cpu_model"], str) and d["cpu_baseline"]["cpu_model"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert "workload" in d["config"]
@@ -41,3 +42,13 @@ def test_reference_arm_under_torchrun_two_ranks():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+
+
+def test_cpu_model_on_an_arm_host(monkeypatch):
+    """Arm kernels name no model in /proc/cpuinfo: the implementer and part codes stand in."""
+    import io
+    sys.path.insert(0, ROOT)
+    import bench
+    text = "processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n"
+    monkeypatch.setattr(bench, "open", lambda *a, **k: io.StringIO(text), raising=False)
+    assert bench.cpu_model() == "implementer 0x41 part 0xd4f"
