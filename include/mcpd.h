@@ -129,7 +129,10 @@ typedef struct mcpd_plan mcpd_plan;
 /* Create a context on CUDA device `device` that issues all work on `cuda_stream` (a cudaStream_t,
  * NULL for the legacy default stream).  The context owns the device scratch memory of its plans. */
 int mcpd_ctx_create(int device, void *cuda_stream, mcpd_ctx **out);
+/* Free the context.  Plans and batches made with it may be destroyed before or after it; any other
+ * call on them needs a live context. */
 void mcpd_ctx_destroy(mcpd_ctx *ctx);
+/* Message of the last failing call made with ctx; owned by ctx, valid until its next call. */
 const char *mcpd_last_error(const mcpd_ctx *ctx);
 
 /* Build a plan: validate the inputs, compute the naive scores and pruning (Section "Knill's

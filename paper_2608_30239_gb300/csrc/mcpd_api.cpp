@@ -31,7 +31,7 @@ struct NvtxRange {
 }  // namespace
 
 struct mcpd_plan {
-    mcpd_ctx *ctx = nullptr;
+    int device = -1;                 // the creating context's device (the context may go first)
     mcpd::Tables t;
     mcpd::KParams kp{};
     int grid = 0, block = 0;
@@ -109,7 +109,7 @@ const char *mcpd_last_error(const mcpd_ctx *ctx) { return ctx ? ctx->err.c_str()
 
 void mcpd_plan_destroy(mcpd_plan *pl) {
     if (!pl) return;
-    if (pl->ctx) cudaSetDevice(pl->ctx->device);
+    if (pl->device >= 0) cudaSetDevice(pl->device);
     for (void *p : pl->allocs) cudaFree(p);
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
@@ -123,7 +123,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     *out = nullptr;
     mcpd_plan *pl = new (std::nothrow) mcpd_plan();
     if (!pl) return set_err(ctx, MCPD_ENOMEM, "host allocation");
-    pl->ctx = ctx;
+    pl->device = ctx->device;
     std::string err;
     int rc = mcpd::build_tables(design, y, params, &pl->t, &err);
     if (rc != MCPD_OK) { delete pl; return set_err(ctx, rc, err); }
@@ -397,7 +397,7 @@ struct BatchClass {
 };
 
 struct mcpd_batch {
-    mcpd_ctx *ctx = nullptr;
+    int device = -1;                       // the creating context's device (the context may go first)
     std::vector<mcpd::Tables> t;
     std::vector<int32_t> order;            // launch order of instances (class-major, then instance-major)
     std::vector<int64_t> out_offset;       // [n + 1] offsets of each instance's clones in est/se
@@ -527,7 +527,7 @@ extern "C" {
 
 void mcpd_batch_destroy(mcpd_batch *b) {
     if (!b) return;
-    if (b->ctx) cudaSetDevice(b->ctx->device);
+    if (b->device >= 0) cudaSetDevice(b->device);
     if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     free_list(b->allocs);
@@ -547,7 +547,7 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     *out = nullptr;
     mcpd_batch *b = new (std::nothrow) mcpd_batch();
     if (!b) return set_err(ctx, MCPD_ENOMEM, "host allocation");
-    b->ctx = ctx;
+    b->device = ctx->device;
     b->n_inst = n_inst;
     b->t.resize(n_inst);
     for (int32_t i = 0; i < n_inst; ++i) {
