@@ -299,6 +299,15 @@ def run_reference(args, rank, world):
     return 0
 
 
+def auxiliary_leg(leg, *args):
+    """Run one leg beside the main figure.  If it raises, the line carries the error in its place
+    (and the main figure, already measured, is still printed)."""
+    try:
+        return leg(*args)
+    except Exception as e:                  # reported in the JSON line, not hidden
+        return {"error": f"{type(e).__name__}: {e}"[:500]}
+
+
 def reduce_over_ranks(dist, device, total_s, su_step, reps_step, e2e_s):
     """Whole-job figures from each rank's own: the slowest rank's timed seconds and end-to-end
     seconds per step (MAX), and one step's site updates and retained replications summed over the
@@ -448,11 +457,11 @@ def main():
             "gpu_launches": 2 * args.steps,
             "clocks": clk}
     if rank == 0 and not args.no_batched:
-        line["batched"] = batched_leg(ctx, device)
+        line["batched"] = auxiliary_leg(batched_leg, ctx, device)
     if rank == 0 and not args.no_learned:
-        line["time_to_se"] = learned_leg(ctx, device)
+        line["time_to_se"] = auxiliary_leg(learned_leg, ctx, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_oracle_sample(args.cpu_seconds)
+        line["cpu_baseline"] = auxiliary_leg(cpu_oracle_sample, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()

@@ -52,3 +52,16 @@ def test_cpu_model_on_an_arm_host(monkeypatch):
     text = "processor\t: 0\nBogoMIPS\t: 2000.00\nCPU implementer\t: 0x41\nCPU part\t: 0xd4f\n"
     monkeypatch.setattr(bench, "open", lambda *a, **k: io.StringIO(text), raising=False)
     assert bench.cpu_model() == "implementer 0x41 part 0xd4f"
+
+
+def test_a_failing_auxiliary_leg_is_reported_in_the_line():
+    """A leg beside the main figure that raises leaves its error in the line instead of ending the
+    bench; a leg that works returns its own result."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    def broken(x):
+        raise RuntimeError(f"leg failed at {x}")
+
+    assert bench.auxiliary_leg(lambda x: {"value": x}, 3) == {"value": 3}
+    assert bench.auxiliary_leg(broken, 7) == {"error": "RuntimeError: leg failed at 7"}
