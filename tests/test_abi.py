@@ -170,6 +170,70 @@ def test_window_horizon_and_buckets_on_random_parameters(L, oracle_lib):
     assert compared >= 100
 
 
+# Perturbations of a valid design and parameter set, at most two per case.
+_PERTURB = dict(
+    fp=[0.0, 1.0, -0.1, 1e-300, 0.5, float("nan"), float("inf")], fn=[0.0, 1.0, 0.999999, float("nan")],
+    q=[0.0, 1.0, 1e-12, 0.999, float("nan")], n_active=[1, 3, -1, 10 ** 6], scan=[1, 2, 3, 4, -1],
+    k=[0, 1, 10, 2 ** 40, -5], ell=[0, 1, 5, 100, 2 ** 40], burn=[0, 3, 2 ** 40], length=[0, 1, 7, 2 ** 40],
+    slots=[0, -1, 100, 2 ** 31, 2 ** 31 + 1, 2 ** 40], horizon=[1, 100, 2 ** 40, -3],
+    budget_site_updates=[1e3, 1e12, -1.0, float("nan"), float("inf")], step_limit=[1, 10 ** 6, -1, 2 ** 62],
+    slot_offset=[5, 2 ** 32 - 1, -1], trace_stride=[1, 3, -2], tau_audit=[5, 10 ** 6, -1],
+    meeting_cap=[1, 20, 10 ** 5, -4, 2 ** 32], lag=[2, 7, 2 ** 20, 2 ** 20 + 1, -1], lanes_per_pair=[1, 8, 3],
+    record_slots=[True], coupled=[False], scan_weights=["good", "zero", "neg", "nan"],
+    init_marginals=["good", "two", "nan"], design=["dup", "range", "neg", "ptr", "empty_clone", "no_pools"])
+
+
+def test_random_inputs_are_accepted_or_refused_cleanly(L):
+    """1500 seeded cases, each a valid design and parameter set with up to two entries made odd or
+    invalid (rates at or outside (0, 1) and NaN, windows, horizons, slot counts and offsets beyond
+    their ranges, caps, lags, bad weights and marginals, duplicate or out-of-range pools, a
+    decreasing clone pointer): every call either builds the tables or returns a documented error
+    code; none crashes.  (Run under AddressSanitizer by tests/sanitize_host.)"""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(5)
+    codes = {mcpd.MCPD_EINVAL, mcpd.MCPD_ETOO_LARGE, mcpd.MCPD_EOVERFLOW}
+    accepted = 0
+    for _ in range(1500):
+        n = int(rng.choice([1, 2, 3, 5, 17, 64, 300, 1298]))
+        m = int(rng.choice([1, 2, 5, 9, 48, 97, 400]))
+        bad = {key: _PERTURB[key][rng.integers(len(_PERTURB[key]))]
+               for key in rng.choice(sorted(_PERTURB), size=int(rng.integers(0, 3)), replace=False)}
+        dmax = min(m, int(rng.choice([1, 3, 6, 8, 9, 12])))
+        rows = [np.sort(rng.choice(m, size=int(rng.integers(1, dmax + 1)), replace=False)) for _ in range(n)]
+        if bad.get("design") == "empty_clone":
+            rows[0] = rows[0][:0]
+        ptr = np.zeros(n + 1, np.int32)
+        ptr[1:] = np.cumsum([len(r) for r in rows])
+        pools = np.concatenate(rows).astype(np.int32)
+        if bad.get("design") == "dup" and len(rows[0]) > 1:
+            pools[1] = pools[0]
+        if bad.get("design") == "range":
+            pools[-1] = m
+        if bad.get("design") == "neg":
+            pools[0] = -1
+        if bad.get("design") == "ptr" and n > 1 and ptr[2] + 1 <= ptr[-1]:
+            ptr[1] = ptr[2] + 1                  # decreasing, still inside the pools array
+        inst = SimpleNamespace(n=n, m=0 if bad.get("design") == "no_pools" else m, clone_ptr=ptr,
+                               clone_pools=pools, y=(rng.random(m) < rng.choice([0.0, 0.1, 0.5, 1.0])).astype(np.uint8),
+                               fp=bad.get("fp", 0.1), fn=bad.get("fn", 0.2), q=bad.get("q", 0.01))
+        kw = {k: v for k, v in bad.items() if k not in ("fp", "fn", "q", "design", "scan_weights", "init_marginals")}
+        kw["seed"] = int(rng.integers(2 ** 63))
+        if "scan_weights" in bad or kw.get("scan") == mcpd.MCPD_SCAN_CUSTOM:
+            scale = {"zero": 0.0, "neg": -1.0, "nan": float("nan")}.get(bad.get("scan_weights"), 1.0)
+            kw["scan_weights"] = rng.random(n) * scale
+            kw.setdefault("scan", mcpd.MCPD_SCAN_CUSTOM)
+        if "init_marginals" in bad:
+            kw["init_marginals"] = rng.random(n) * {"good": 1.0, "two": 2.0, "nan": float("nan")}[bad["init_marginals"]]
+        try:
+            info = mcpd.mcpd_inspect(inst, **kw)["info"]
+        except mcpd.McpdError as e:
+            assert e.code in codes, (e, bad)
+            continue
+        accepted += 1
+        assert 1 <= info[0] <= n and info[1] >= 1 and info[6] >= 1, (info, bad)
+    assert accepted >= 300
+
+
 def test_custom_weights_tables(L, oracle_lib):
     inst = synth.tiny_config(5)
     w = np.linspace(1.0, 2.0, inst.n)
