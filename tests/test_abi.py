@@ -2,7 +2,6 @@
 struct layouts match the C compiler's, its host-built tables equal the oracle's, and it rejects
 invalid inputs."""
 import ctypes
-import os
 import subprocess
 
 import numpy as np
