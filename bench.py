@@ -262,7 +262,7 @@ def learned_leg(ctx, device, train=512, slots=1 << 21):
         reps = [r["kernel_ms"]] + [learned.decode_max_se(ctx, [inst], r["slots"], 29.4, 8, **kw)[1] for _ in range(2)]
         out[name]["measured"] = {"slots": r["slots"], "max_se": r["max_se"],
                                  "s_to_se_0.005": statistics.median(reps) / 1000.0, "kernel_ms_runs": reps,
-                                 "met": r["met"]}
+                                 "wall_s_first_decode": r["wall_ms"] / 1000.0, "met": r["met"]}
     for arm in out.values():
         if isinstance(arm, dict) and "max_se" in arm:
             arm["s_to_se_0.005"] = (arm["measured"]["s_to_se_0.005"] if arm["max_se"] <= 0.005 and "measured" in arm

@@ -220,26 +220,30 @@ def decode_max_se(ctx, instances, slots, sweeps, seed, weights=None, init=None, 
         if lag_sweeps > 0:
             kw.update(lag=max(1, int(round(lag_sweeps * inst.n))))
         params.append(kw)
+    t0 = time.perf_counter()
     b = mcpd.Batch(ctx, instances, params)
     est = torch.empty(b.total_active, dtype=torch.float64, device=f"cuda:{ctx.device}")
     se = torch.empty_like(est)
     b.run_async(est, se)
     st = b.collect()
+    max_se = float(se.cpu().numpy().max())
+    st["wall_ms"] = 1000.0 * (time.perf_counter() - t0)   # batch creation through the SE copy
     b.close()
-    return float(se.cpu().numpy().max()), st["kernel_ms"], st
+    return max_se, st["kernel_ms"], st
 
 
 def time_to_se(ctx, instances, target=0.005, sweeps=29.4, slots0=1024, seed=7, weights=None,
                init=None, max_slots=1 << 22, lag_sweeps=0):
     """Double P from slots0 until every instance's largest per-clone SE is <= target; report the
-    kernel time of the first decode that meets it (and the path of (P, max SE, ms))."""
+    kernel time and the wall time (batch creation through the SE copy) of the first decode that
+    meets it, and the path of (P, max SE, kernel ms)."""
     P = slots0
     path = []
     while True:
         mse, ms, st = decode_max_se(ctx, instances, P, sweeps, seed, weights, init, lag_sweeps=lag_sweeps)
         path.append((P, mse, ms))
         if mse <= target or P >= max_slots:
-            return dict(slots=P, max_se=mse, kernel_ms=ms, path=path, met=mse <= target)
+            return dict(slots=P, max_se=mse, kernel_ms=ms, wall_ms=st["wall_ms"], path=path, met=mse <= target)
         P *= 2
 
 
