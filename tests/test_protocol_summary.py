@@ -22,3 +22,25 @@ def test_summary_mean_and_standard_error():
     assert summ[(1, "SS")]["mae_all_se"] == 0.0
     assert summ[(3, "cSW")]["n"] == 1 and summ[(3, "cSW")]["mae_all_se"] is None
     assert np.isclose(summ[(3, "cSW")]["kernel_ms"], 0.5)
+
+
+def test_protocol_windows_follow_table_s1():
+    """The protocol's burn-in b = round_half_even(0.1 M) and averaging length M - b reproduce every
+    printed value of Table S1 (tests/golden/table_s1.txt), e.g. b = 166 at M = 1665."""
+    import os
+
+    from paper_2608_30239_gb300.protocol import round_half_even
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table_s1.txt")
+    checked = 0
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            left, right = line.split("|")
+            _, n_a, *bs = left.split()
+            rest = [int(v) for v in right.split()]
+            for s, b, mb in zip((1, 3, 5, 10, 20), (int(v) for v in bs), rest):
+                M = s * int(n_a)
+                assert round_half_even(0.1 * M) == b and M - round_half_even(0.1 * M) == mb, (n_a, s)
+                checked += 1
+    assert checked == 15
