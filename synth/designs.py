@@ -112,24 +112,29 @@ def kset_design(n: int, m: int, deg: int, seed: int):
 
 
 def tapestry_like_design(n: int, m: int, deg: int, seed: int):
-    """Regular design (every pool the same size up to one): a stand-in for the shape of the
-    Tapestry designs (each sample in `deg` pools), drawn by dealing clone-slots round robin."""
+    """Regular design, a stand-in for the shape of the Tapestry designs: each clone sits in `deg`
+    distinct pools, and the pool sizes differ by at most one (n deg / m each when m divides n deg).
+    Clone-slots are dealt to the pools round robin in a shuffled order; a clone dealt the same pool
+    twice swaps that entry with a randomly chosen entry of another clone (a swap keeps every pool's
+    size), until no clone repeats a pool."""
+    if deg > m:
+        raise ValueError("deg > m")
     rng = SplitMix64(seed)
     order = np.argsort(rng.u64(n * deg), kind="stable")
-    pools = [[] for _ in range(n)]
-    for slot, idx in enumerate(order):
-        pools[idx // deg].append(slot % m)
-    rows = []
+    rows = (np.arange(n * deg, dtype=np.int64) % m)[order].reshape(n, deg)
     for i in range(n):
-        row = sorted(set(pools[i]))
-        j = 0
-        while len(row) < deg:  # collisions: fill with the smallest unused pools
-            if j not in row:
-                row.append(j)
-            j += 1
-        rows.append(sorted(row))
+        for a in range(deg):
+            for _ in range(1 << 20):
+                if np.count_nonzero(rows[i] == rows[i, a]) == 1:
+                    break
+                j, b = (int(v) for v in rng.below(2, np.array([n, deg], dtype=np.uint64)))
+                x, y = rows[i, a], rows[j, b]
+                if j != i and y not in rows[i] and x not in rows[j]:
+                    rows[i, a], rows[j, b] = y, x
+            else:
+                raise RuntimeError("no regular design found")
     clone_ptr = np.arange(0, (n + 1) * deg, deg, dtype=np.int32)
-    return clone_ptr, np.asarray(rows, dtype=np.int32).reshape(-1)
+    return clone_ptr, np.sort(rows, axis=1).astype(np.int32).reshape(-1)
 
 
 def mixed_degree_design(n: int, m: int, deg_lo: int, deg_hi: int, seed: int):

@@ -1,0 +1,51 @@
+"""The seeded input generators (no GPU): SplitMix64 against its published outputs, and the
+designs and outcomes against the properties their docstrings state."""
+import numpy as np
+
+import synth
+from synth.designs import SplitMix64, draw_outcomes, kset_design, tapestry_like_design
+
+
+def test_splitmix64_known_answers():
+    """First outputs of SplitMix64 (Steele, Lea and Flood, OOPSLA 2014; the reference C code that
+    seeds the xoshiro generators) for seed 1234567."""
+    want = [6457827717110365317, 3203168211198807973, 9817491932198370423, 4593380528125082431,
+            16408922859458223821]
+    assert [int(v) for v in SplitMix64(1234567).u64(5)] == want
+    r = SplitMix64(1234567)                      # the stream continues across calls
+    assert [int(v) for v in np.concatenate([r.u64(2), r.u64(3)])] == want
+
+
+def test_kset_rows_are_distinct_sorted_pools():
+    ptr, pools = kset_design(1298, 97, 6, 5007)
+    rows = pools.reshape(1298, 6)
+    assert ptr.tolist() == list(range(0, 1299 * 6, 6))
+    assert (np.diff(rows, axis=1) > 0).all() and rows.min() >= 0 and rows.max() < 97
+    assert np.array_equal(kset_design(1298, 97, 6, 5007)[1], pools)
+    assert not np.array_equal(kset_design(1298, 97, 6, 5008)[1], pools)
+
+
+def test_tapestry_shapes_are_regular():
+    """Each sample in 3 pools and every pool the same size: 20 per pool at 320 x 48 and 31 per
+    pool at 961 x 93, the Tapestry designs' shapes."""
+    for n, m, size in ((320, 48, 20), (961, 93, 31)):
+        ptr, pools = tapestry_like_design(n, m, 3, 90 + m)
+        rows = pools.reshape(n, 3)
+        assert (np.diff(rows, axis=1) > 0).all()
+        assert (np.bincount(pools, minlength=m) == size).all()
+    sizes = np.bincount(tapestry_like_design(100, 7, 3, 1)[1], minlength=7)
+    assert sizes.max() - sizes.min() <= 1        # 300 slots over 7 pools: 42 or 43
+
+
+def test_noiseless_outcomes_are_the_latent_pool_states():
+    ptr, pools = kset_design(200, 30, 4, 3)
+    positives, y = draw_outcomes(200, 30, ptr, pools, 5, 0.0, 0.0, 4)
+    assert len(set(positives.tolist())) == 5
+    latent = np.zeros(30, np.uint8)
+    for i in positives:
+        latent[pools[ptr[i]:ptr[i + 1]]] = 1
+    assert np.array_equal(y, latent)
+
+
+def test_bench_horizon():
+    assert synth.budget_horizon(4e10, 524288) == 38146
