@@ -49,3 +49,16 @@ def test_noiseless_outcomes_are_the_latent_pool_states():
 
 def test_bench_horizon():
     assert synth.budget_horizon(4e10, 524288) == 38146
+
+
+def test_batched_instances_follow_their_recipe():
+    """n in [200, 5000], m = round(n / 13), k in 4..8, 1..6 positives, fp in [.005, .1],
+    fn in [.02, .25], q = positives / n; every instance valid for the library."""
+    from paper_2608_30239_gb300 import mcpd
+    for inst in synth.batched_configs(count=24, seed=11):
+        k = int(np.diff(inst.clone_ptr)[0])
+        assert 200 <= inst.n <= 5000 and inst.m == int(np.floor(inst.n / 13 + 0.5))
+        assert 4 <= k <= 8 and (np.diff(inst.clone_ptr) == k).all()
+        assert 1 <= len(inst.positives) <= 6 and np.isclose(inst.q, len(inst.positives) / inst.n)
+        assert 0.005 <= inst.fp <= 0.1 and 0.02 <= inst.fn <= 0.25
+        mcpd.mcpd_inspect(inst, slots=16, horizon=20 * inst.n)
