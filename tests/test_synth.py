@@ -62,3 +62,15 @@ def test_batched_instances_follow_their_recipe():
         assert 1 <= len(inst.positives) <= 6 and np.isclose(inst.q, len(inst.positives) / inst.n)
         assert 0.005 <= inst.fp <= 0.1 and 0.02 <= inst.fn <= 0.25
         mcpd.mcpd_inspect(inst, slots=16, horizon=20 * inst.n)
+
+
+def test_mixed_degree_rows():
+    """Each clone's degree lies in [deg_lo, deg_hi], its pools distinct and sorted; every degree
+    in the range occurs on a design of this size."""
+    from synth.designs import mixed_degree_design
+    ptr, pools = mixed_degree_design(260, 23, 2, 8, 31)
+    degs = np.diff(ptr)
+    assert degs.min() >= 2 and degs.max() <= 8 and set(degs.tolist()) == set(range(2, 9))
+    for i in range(260):
+        row = pools[ptr[i]:ptr[i + 1]]
+        assert (np.diff(row) > 0).all() and row.min() >= 0 and row.max() < 23
