@@ -121,6 +121,12 @@ typedef struct mcpd_stats {
     int64_t n_active;
     double kernel_ms;          /* device time of the sampling kernel (CUDA events)                */
     int64_t tau_over_audit;    /* completed replications with tau > params.tau_audit             */
+    int64_t resident_pairs;    /* pairs the sampling kernel held at once (grid x block; the widest
+                                  size class of a batch)                                         */
+    int64_t h2d_bytes, d2h_bytes; /* single instance: bytes the library copied host -> device and
+                                  device -> host for this plan so far (tables at creation; counters
+                                  at each collect; fetches; mcpd_decode adds its est/se copies);
+                                  0 for batches and mcpd_decode_noalloc                          */
 } mcpd_stats;
 
 typedef struct mcpd_ctx mcpd_ctx;
@@ -154,6 +160,21 @@ int mcpd_plan_active(const mcpd_plan *plan, int32_t *active);
  * est_dev, se_dev: device arrays [n_active] (active order) receiving theta_CT and its standard
  * error.  Asynchronous: returns after enqueueing on the context stream. */
 int mcpd_run_async(mcpd_ctx *ctx, mcpd_plan *plan, double *est_dev, double *se_dev);
+/* Run the sampler over `slots` slots (Algorithm 4 per slot) and finalize, like mcpd_run_async but
+ * with a slot count of the caller's choosing, so that a fixed-budget estimate can be extended
+ * until it reaches a precision.  accumulate = 0: the N*_p buckets are cleared and the slots are
+ * global ids slot_offset .. slot_offset + slots - 1.  accumulate = 1: the slots continue those
+ * already in the buckets since the last accumulate = 0 run (S of them: global ids
+ * slot_offset + S .. slot_offset + S + slots - 1) and their sums are added.  est_dev / se_dev
+ * receive theta_CT and its standard error over all S + slots slots (Theorem 2: the slot means are
+ * i.i.d., so the estimator over more slots is the same estimator with a larger P).  Every slot
+ * keeps the plan's horizon B, so the result is bit-identical to one mcpd_run_async of a plan with
+ * P = S + slots and horizon B.  The launch keeps the plan's grid with its warps per block trimmed
+ * to whole rounds of these slots.  S + slots <= 2^31 and slot_offset + S + slots <= 2^32;
+ * per-slot records and traces (record_slots, trace_stride) allow only accumulate = 0 with
+ * slots <= the plan's P.  Asynchronous; mcpd_collect reads this run's counters and kernel time. */
+int mcpd_run_slots_async(mcpd_ctx *ctx, mcpd_plan *plan, int64_t slots, int32_t accumulate,
+                         double *est_dev, double *se_dev);
 /* Wait for the last run of `plan`, read its counters and its error flag.  Returns
  * MCPD_ESTEP_LIMIT if any pair hit the safety limit. stats may be NULL. */
 int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *plan, mcpd_stats *stats);
@@ -289,11 +310,14 @@ int mcpd_mlp_heads(mcpd_ctx *ctx, int32_t n_seg, const int64_t *seg_dev, const f
  * active ids).  All other device memory comes from one 64 MiB array compiled into this library,
  * held on every GPU that loads it until the process exits.  Problems whose tables, N*_p buckets
  * and one warp of pair accumulators do not fit in it fail with MCPD_ETOO_LARGE; problems that fit
- * run with as many resident pairs as fit and give the same results as mcpd_run_async.
- * record_slots and trace_stride must be 0.  The first call on a device looks the array up (with
- * that device current), so make it before any stream capture.  Every call clears and reuses the
- * same array: calls whose GPU work overlaps on one device race, so serialise them.  Synchronous
- * on the context's stream; stats may be NULL (kernel_ms is left 0). */
+ * run with as many resident pairs as fit (stats->resident_pairs) and give the same results as
+ * mcpd_run_async.  record_slots and trace_stride must be 0.  est_dev and se_dev must be device
+ * (or managed) memory of the context's device in the runtime's primary context, else MCPD_EINVAL.
+ * Every call looks the array's address up with the context's device current (so a reset of the
+ * primary context leaves no stale address); the first call on a device may load the library's
+ * device code, so make it before any stream capture.  Every call clears and reuses the same array:
+ * calls whose GPU work overlaps on one device race, so serialise them.  Synchronous on the
+ * context's stream; stats may be NULL (kernel_ms is left 0). */
 int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
                         const mcpd_params *params, double *est_dev, double *se_dev,
                         mcpd_stats *stats);

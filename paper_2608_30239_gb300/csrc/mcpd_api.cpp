@@ -43,6 +43,9 @@ struct mcpd_plan {
     std::vector<void *> allocs;
     double *est_dev = nullptr, *se_dev = nullptr;    // used by mcpd_decode
     int64_t n_trace = 0;
+    int64_t slots_run = 0;           // slots in the buckets since the last run that cleared them
+    long long last_pairs = 0;        // pairs the last launch held (its grid x block)
+    mutable int64_t h2d_bytes = 0, d2h_bytes = 0;   // bytes copied between host and device (fetches too)
 };
 
 namespace {
@@ -135,7 +138,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     const size_t tables = mcpd::kernel_table_bytes(t);
     mcpd::PairsShape shape;
     rc = mcpd::pairs_shape(t.coupled, t.scan, t.udeg, false, tables, t.wpp, ctx->smem_optin, t.P,
-                           ctx->sm_count, 0, &shape);
+                           ctx->sm_count, 0, t.capped || t.lag > 1, &shape);
     if (rc != MCPD_OK) {
         delete pl;
         return set_err(ctx, rc, rc == MCPD_ETOO_LARGE ? "instance too large for the one-thread-per-pair layout"
@@ -188,6 +191,8 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
         CU_OR(cudaMemcpyAsync(d_Tnu, t.Tnu.data(), t.Tnu.size() * 8, cudaMemcpyHostToDevice, ctx->stream), mcpd_plan_destroy(pl));
     if (!t.init_pairs.empty())
         CU_OR(cudaMemcpyAsync(d_init, t.init_pairs.data(), t.init_pairs.size() * 4, cudaMemcpyHostToDevice, ctx->stream), mcpd_plan_destroy(pl));
+    pl->h2d_bytes += static_cast<int64_t>(t.alias.size() * 8 + mcpd::kernel_rows(t).size() * 2 +
+                                          mcpd::kernel_T(t).size() * 8 + t.Tnu.size() * 8 + t.init_pairs.size() * 4);
     kp.alias = d_alias; kp.rows = d_rows; kp.T = d_T; kp.Tnu = t.Tnu.empty() ? nullptr : d_Tnu;
     kp.init_pairs = d_init; kp.n_init_pairs = static_cast<int32_t>(t.init_pairs.size());
     kp.na = t.na; kp.m = t.m; kp.W = t.W; kp.Mp = t.Mp; kp.wpp = t.wpp; kp.deg = t.deg_max; kp.udeg = t.udeg;
@@ -227,17 +232,45 @@ int mcpd_plan_active(const mcpd_plan *pl, int32_t *active) {
     return MCPD_OK;
 }
 
-int mcpd_run_async(mcpd_ctx *ctx, mcpd_plan *pl, double *est_dev, double *se_dev) {
-    NvtxRange nvtx_range("mcpd.run");
+namespace {
+
+// Enqueue the sampler over `slots` slots and the finalize.  accumulate = 0: the buckets are cleared
+// and the slots are the plan's first (global ids slot_offset + 0 ..); accumulate = 1: the slots
+// continue the ones already in the buckets (global ids slot_offset + slots_run ..) and their sums
+// are added.  Either way est/se are finalized over every slot in the buckets.
+int run_range(mcpd_ctx *ctx, mcpd_plan *pl, int64_t slots, bool accumulate, double *est_dev, double *se_dev) {
     if (!ctx || !pl || !est_dev || !se_dev) return MCPD_EINVAL;
-    CU(cudaSetDevice(ctx->device));
     const mcpd::Tables &t = pl->t;
-    mcpd::KParams &kp = pl->kp;
+    if (slots < 1) return set_err(ctx, MCPD_EINVAL, "slots must be >= 1");
+    if (accumulate && !pl->ran) return set_err(ctx, MCPD_EINVAL, "nothing to accumulate onto: run the plan first");
+    const int64_t first = accumulate ? pl->slots_run : 0;
+    if (first + slots > (int64_t(1) << 31) || t.slot_offset + first + slots > (int64_t(1) << 32))
+        return set_err(ctx, MCPD_EINVAL, "accumulated slots beyond 2^31, or global slot ids beyond 32 bits");
+    if ((t.record_slots || t.trace_stride > 0) && (accumulate || slots > t.P))
+        return set_err(ctx, MCPD_EINVAL, "per-slot records and traces cover one run of at most the plan's slots");
+    CU(cudaSetDevice(ctx->device));
+    mcpd::KParams kp = pl->kp;
+    kp.P = slots;
+    kp.slot_offset = t.slot_offset + first;
+    // Launch shape: the plan's, with its warps per block trimmed to the fewest that need no more
+    // rounds of slots for this run (the plan's own slot count gives the plan's shape).
+    int warps = pl->block / 32;
+    {
+        const long long per_round = static_cast<long long>(pl->grid) * 32;
+        const long long rounds = (slots + per_round * warps - 1) / (per_round * warps);
+        const long long w = (slots + rounds * per_round - 1) / (rounds * per_round);
+        if (w >= 1 && w < warps) warps = static_cast<int>(w);
+    }
+    kp.warps = warps;
+    kp.y_regions = mcpd::pairs_y_regions(t.coupled, warps);
+    const size_t smem = mcpd::pairs_smem_bytes(kp.smem_tables, t.wpp, warps, kp.y_regions);
     const size_t nbna = static_cast<size_t>(t.nb) * t.na;
-    CU(cudaMemsetAsync(kp.S1, 0, nbna * 8, ctx->stream));
-    CU(cudaMemsetAsync(kp.S2lo, 0, nbna * 8, ctx->stream));
-    CU(cudaMemsetAsync(kp.S2hi, 0, nbna * 8, ctx->stream));
-    CU(cudaMemsetAsync(kp.bcount, 0, static_cast<size_t>(t.nb) * 8, ctx->stream));
+    if (!accumulate) {
+        CU(cudaMemsetAsync(kp.S1, 0, nbna * 8, ctx->stream));
+        CU(cudaMemsetAsync(kp.S2lo, 0, nbna * 8, ctx->stream));
+        CU(cudaMemsetAsync(kp.S2hi, 0, nbna * 8, ctx->stream));
+        CU(cudaMemsetAsync(kp.bcount, 0, static_cast<size_t>(t.nb) * 8, ctx->stream));
+    }
     CU(cudaMemsetAsync(kp.counters, 0, mcpd::kNumCounters * 8, ctx->stream));
     CU(cudaMemsetAsync(kp.error, 0, sizeof(int), ctx->stream));
     if (pl->dirty) {   // the kernel leaves these zeroed when it completes normally
@@ -251,15 +284,33 @@ int mcpd_run_async(mcpd_ctx *ctx, mcpd_plan *pl, double *est_dev, double *se_dev
         CU(cudaMemsetAsync(kp.slot_reps, 0, static_cast<size_t>(t.P) * 4, ctx->stream));
     }
     pl->dirty = true;
+    pl->ran = false;                 // until the launches are enqueued
     CU(cudaEventRecord(pl->ev0, ctx->stream));
-    if (mcpd::launch_pairs(kp, pl->grid, pl->block, pl->smem, ctx->stream) != MCPD_OK)
+    if (mcpd::launch_pairs(kp, pl->grid, warps * 32, smem, ctx->stream) != MCPD_OK)
         return set_err(ctx, MCPD_ECUDA, std::string("pairs kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
     CU(cudaEventRecord(pl->ev1, ctx->stream));
-    if (mcpd::launch_finalize(kp.S1, kp.S2lo, kp.S2hi, t.na, static_cast<int>(t.nb), t.P, t.L, est_dev,
+    if (mcpd::launch_finalize(kp.S1, kp.S2lo, kp.S2hi, t.na, static_cast<int>(t.nb), first + slots, t.L, est_dev,
                               se_dev, ctx->stream) != MCPD_OK)
         return set_err(ctx, MCPD_ECUDA, "finalize kernel launch");
     pl->ran = true;
+    pl->slots_run = first + slots;
+    pl->last_pairs = static_cast<long long>(pl->grid) * warps * 32;
     return MCPD_OK;
+}
+
+}  // namespace
+
+int mcpd_run_async(mcpd_ctx *ctx, mcpd_plan *pl, double *est_dev, double *se_dev) {
+    NvtxRange nvtx_range("mcpd.run");
+    if (!pl) return MCPD_EINVAL;
+    return run_range(ctx, pl, pl->t.P, false, est_dev, se_dev);
+}
+
+int mcpd_run_slots_async(mcpd_ctx *ctx, mcpd_plan *pl, int64_t slots, int32_t accumulate, double *est_dev,
+                         double *se_dev) {
+    NvtxRange nvtx_range("mcpd.run_slots");
+    if (accumulate != 0 && accumulate != 1) return set_err(ctx, MCPD_EINVAL, "accumulate must be 0 or 1");
+    return run_range(ctx, pl, slots, accumulate != 0, est_dev, se_dev);
 }
 
 int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *pl, mcpd_stats *stats) {
@@ -271,6 +322,7 @@ int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *pl, mcpd_stats *stats) {
     int error = 0;
     CU(cudaMemcpyAsync(c, pl->kp.counters, sizeof(c), cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaMemcpyAsync(&error, pl->kp.error, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    pl->d2h_bytes += static_cast<int64_t>(sizeof(c) + sizeof(int));
     CU(cudaStreamSynchronize(ctx->stream));
     float ms = 0.f;
     CU(cudaEventElapsedTime(&ms, pl->ev0, pl->ev1));
@@ -280,6 +332,9 @@ int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *pl, mcpd_stats *stats) {
         stats->n_buckets = pl->t.nb;
         stats->n_active = pl->t.na;
         stats->kernel_ms = ms;
+        stats->resident_pairs = pl->last_pairs;
+        stats->h2d_bytes = pl->h2d_bytes;
+        stats->d2h_bytes = pl->d2h_bytes;
     }
     if (error) return set_err(ctx, MCPD_ESTEP_LIMIT, "a pair reached the step limit without meeting");
     pl->dirty = false;
@@ -318,6 +373,7 @@ int mcpd_fetch(mcpd_ctx *ctx, const mcpd_plan *pl, int what, void *host_dst, siz
     CU(cudaSetDevice(ctx->device));
     CU(cudaMemcpyAsync(host_dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
+    pl->d2h_bytes += static_cast<int64_t>(bytes);
     return MCPD_OK;
 }
 
@@ -340,6 +396,7 @@ int mcpd_decode(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
         if (c1 != cudaSuccess || c2 != cudaSuccess || c3 != cudaSuccess) {
             rc = set_err(ctx, MCPD_ECUDA, "copying results to the host");
         } else {
+            if (stats) stats->d2h_bytes += static_cast<int64_t>(2 * na * 8);
             for (int32_t i = 0; i < design->n_clones; ++i) { est[i] = 0.0; se[i] = 0.0; if (active) active[i] = 0; }
             for (int32_t a = 0; a < na; ++a) {
                 const int32_t i = pl->t.active[a];
@@ -452,12 +509,12 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
         if (lanes == 1) {
             mcpd::PairsShape shape;
             int rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, 0, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
-                                       ctx->sm_count, 0, &shape);
+                                       ctx->sm_count, 0, c.bp.ext != 0, &shape);
             if (rc == MCPD_ETOO_LARGE) return set_err(ctx, rc, "largest instance does not fit one warp of pair state");
             if (rc != MCPD_OK) return set_err(ctx, rc, "cudaFuncSetAttribute / occupancy");
             if (warps > 0 && warps < shape.warps) {
                 rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, 0, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
-                                       ctx->sm_count, warps, &shape);
+                                       ctx->sm_count, warps, c.bp.ext != 0, &shape);
                 if (rc != MCPD_OK) return set_err(ctx, rc, "launch shape");
             }
             w = shape.warps;
@@ -814,6 +871,7 @@ int mcpd_batch_collect(mcpd_ctx *ctx, mcpd_batch *b, mcpd_stats *stats) {
         stats->n_buckets = static_cast<int64_t>(b->total_counts);
         stats->n_active = b->total_active;
         stats->kernel_ms = ms;
+        for (const BatchClass &cl : b->cls) stats->resident_pairs = std::max<int64_t>(stats->resident_pairs, cl.pairs);
     }
     if (error) return set_err(ctx, MCPD_ESTEP_LIMIT, "a pair reached the step limit without meeting");
     b->dirty = false;

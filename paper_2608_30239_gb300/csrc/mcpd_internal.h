@@ -202,9 +202,10 @@ struct PairsShape {
 int pairs_y_regions(int coupled, int warps);
 size_t pairs_smem_bytes(size_t tables, int wpp, int warps, int y_regions);
 // tables: bytes staged at the start of shared memory (0 for batches); wpp: words per column;
-// P: slots of a single instance (0 = do not shape by rounds); warps: requested warps (0 = auto).
+// P: slots of a single instance (0 = do not shape by rounds); warps: requested warps (0 = auto);
+// ext: the run launches the kernel variant with meeting caps and lags > 1.
 int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int wpp, size_t smem_optin,
-                long long P, int sm_count, int warps, PairsShape *out);
+                long long P, int sm_count, int warps, bool ext, PairsShape *out);
 
 // Launchers (mcpd_kernels.cu).
 int launch_batch(const BParams &bp, int grid, int block, size_t smem, void *stream);
@@ -212,7 +213,7 @@ int launch_group(const BParams &bp, int grid, int block, size_t smem, void *stre
 int set_group_smem(int lanes, size_t bytes);
 int group_max_threads(int lanes);
 int group_occupancy(int lanes, int block, size_t smem, int *blocks_per_sm);
-int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide = false);
+int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide = false, bool ext = false);
 int launch_finalize_batch(const InstDesc *insts, int n_inst, const int32_t *clone_inst,
                           const int32_t *clone_local, long long total_clones, double *est,
                           double *se, void *stream);

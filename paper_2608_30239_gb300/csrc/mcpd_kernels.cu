@@ -982,11 +982,13 @@ size_t pairs_smem_bytes(size_t tables, int wpp, int warps, int y_regions) {
 }
 
 int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int wpp, size_t smem_optin,
-                long long P, int sm_count, int warps, PairsShape *out) {
+                long long P, int sm_count, int warps, bool ext, PairsShape *out) {
     // Batches: the wide variant when the pair state leaves room for more warps than the narrow one
-    // is compiled for.
+    // is compiled for.  The thread cap and the occupancy query use the variant the run launches
+    // (ext: the one with meeting caps and lags > 1).
+    ext = ext && coupled;
     bool wide = batch;
-    int cap = pairs_max_threads(coupled, scan, udeg, batch, wide) / 32;
+    int cap = pairs_max_threads(coupled, scan, udeg, batch, wide, ext) / 32;
     auto bytes = [&](int w) { return pairs_smem_bytes(tables, wpp, w, pairs_y_regions(coupled, w)); };
     auto most = [&](size_t budget) {
         int best = 0;
@@ -995,13 +997,13 @@ int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int 
     };
     auto resident = [&](int w, int *per_sm) {
         *per_sm = 1;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pick(coupled, scan, batch, batch ? 0 : udeg, wide),
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pick(coupled, scan, batch, batch ? 0 : udeg, wide, ext),
                                                              w * 32, bytes(w)) == cudaSuccess;
     };
     int w1 = most(smem_optin);
     if (w1 < 1) return MCPD_ETOO_LARGE;
     if (batch) {
-        const int narrow = pairs_max_threads(coupled, scan, 0, true, false) / 32;
+        const int narrow = pairs_max_threads(coupled, scan, 0, true, false, ext) / 32;
         const int target = warps > 0 ? std::min(warps, w1) : w1;
         if (target <= narrow) { wide = false; cap = narrow; w1 = most(smem_optin); }
     }
@@ -1040,9 +1042,9 @@ int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int 
     return MCPD_OK;
 }
 
-int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide) {
+int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide, bool ext) {
     cudaFuncAttributes a{};
-    if (cudaFuncGetAttributes(&a, pick(coupled, scan, batch, batch ? 0 : udeg, wide)) != cudaSuccess) return 512;
+    if (cudaFuncGetAttributes(&a, pick(coupled, scan, batch, batch ? 0 : udeg, wide, ext && coupled)) != cudaSuccess) return 512;
     return a.maxThreadsPerBlock;
 }
 

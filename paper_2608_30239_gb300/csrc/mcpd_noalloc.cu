@@ -17,13 +17,16 @@
 //   - Every call uses the same array and leaves its contents behind; each call clears what must
 //     start at zero.  Two calls whose work overlaps on the GPU (other streams, other host threads,
 //     on the same device) race on the array: serialise them.
-//   - The first call on a device, with that device current, looks up the array's device address
-//     with cudaGetSymbolAddress and caches it; make that first call before any stream capture.
+//   - Every call looks the array's device address up with cudaGetSymbolAddress, with the context's
+//     device current, so the address is never stale (a primary-context reset gives the array a new
+//     one).  The first lookup on a device may load the library's device code: make the first call
+//     before any stream capture.
+//   - The output arrays must be device (or managed) memory of the context's device, in the CUDA
+//     primary context the runtime uses; the call checks their device before any launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "mcpd_internal.h"
@@ -37,24 +40,27 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_setup_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the array on `device` (current); looked up once per device.
+// Device address of the array on `device`, which the caller has made current.  Looked up on every
+// call (it costs a table lookup in the runtime): a cached address would outlive a reset of the
+// primary context.
 int scratch_address(int device, void **out, std::string *err) {
     if (device < 0 || device >= kMaxDevices) { *err = "device index out of range"; return MCPD_EINVAL; }
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[device]) {
-        void *ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr) {
-            *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
-            return MCPD_ECUDA;
-        }
-        g_scratch_addr[device] = ptr;
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+        *err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return MCPD_ECUDA;
     }
-    *out = g_scratch_addr[device];
+    *out = ptr;
     return MCPD_OK;
+}
+
+// The caller's output array lives on `device` (device or managed memory).
+bool on_device(const void *ptr, int device) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
+    return a.device == device;
 }
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
@@ -87,6 +93,8 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     if (t.record_slots || t.trace_stride > 0)
         return fail(ctx, MCPD_EINVAL, "no-alloc decode keeps no per-slot records or traces");
     CUN(cudaSetDevice(ctx->device));
+    if (!on_device(est_dev, ctx->device) || !on_device(se_dev, ctx->device))
+        return fail(ctx, MCPD_EINVAL, "est_dev and se_dev must be device memory of the context's device");
     void *base = nullptr;
     rc = scratch_address(ctx->device, &base, &err);
     if (rc != MCPD_OK) return fail(ctx, rc, err);
@@ -105,12 +113,13 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     const size_t tables = kernel_table_bytes(t);
     PairsShape shape;
     const int src = pairs_shape(t.coupled, t.scan, t.udeg, false, tables, t.wpp, ctx->smem_optin, t.P,
-                                ctx->sm_count, 0, &shape);
+                                ctx->sm_count, 0, t.capped || t.lag > 1, &shape);
     if (src == MCPD_ETOO_LARGE) return fail(ctx, src, "instance too large for the one-thread-per-pair layout");
     if (src != MCPD_OK) return fail(ctx, MCPD_ECUDA, "launch shape (cudaFuncSetAttribute / occupancy)");
     // scratch block (sums, statistics, touched sets) and Y column
     const size_t per_pair = static_cast<size_t>(pair_words(t.na, t.W)) * 8 + static_cast<size_t>(t.wpp) * 4;
-    if (fixed >= kNoAllocScratchBytes)
+    // room for the pair scratch and the Y columns, each rounded up to 256 bytes
+    if (fixed + 2 * 256 > kNoAllocScratchBytes)
         return fail(ctx, MCPD_ETOO_LARGE, "tables and N*_p buckets exceed the 64 MiB no-alloc scratch");
     const size_t fit_warps = (kNoAllocScratchBytes - fixed - 2 * 256) / (32 * per_pair);
     if (fit_warps < 1)
@@ -176,6 +185,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
         counters_to_stats(c, stats);
         stats->n_buckets = t.nb;
         stats->n_active = t.na;
+        stats->resident_pairs = static_cast<int64_t>(pairs);
     }
     if (error) return fail(ctx, MCPD_ESTEP_LIMIT, "a pair reached the step limit without meeting");
     return MCPD_OK;

@@ -12,7 +12,8 @@ trains a small model to choose both from the observed design, with the library's
 
 Only orchestration lives here (argument marshalling and the order of calls); every computation is
 a library call.  `time_to_se` measures the decode time needed to bring the largest per-clone
-standard error of a batch of instances to a target, by doubling the slot count.
+standard error of an instance to a target, extending one fixed-budget decode slot range by slot
+range until it gets there.
 """
 from __future__ import annotations
 
@@ -232,19 +233,56 @@ def decode_max_se(ctx, instances, slots, sweeps, seed, weights=None, init=None, 
     return max_se, st["kernel_ms"], st
 
 
-def time_to_se(ctx, instances, target=0.005, sweeps=29.4, slots0=1024, seed=7, weights=None,
-               init=None, max_slots=1 << 22, lag_sweeps=0):
-    """Double P from slots0 until every instance's largest per-clone SE is <= target; report the
-    kernel time and the wall time (batch creation through the SE copy) of the first decode that
-    meets it, and the path of (P, max SE, kernel ms)."""
-    P = slots0
-    path = []
+def time_to_se(ctx, inst, target=0.005, sweeps=29.4, seed=7, weights=None, init=None, lag_sweeps=0,
+               first_slots=1024, max_slots=1 << 26, plan_slots=524288):
+    """Measured time to bring the largest per-clone SE of one instance to `target`.
+
+    One fixed-budget decode (horizon B = sweeps * n progress units per slot, paper score weights
+    unless `weights`, all-negative start unless `init`, lag-L pairs with L = lag_sweeps * n when
+    lag_sweeps > 0) is extended slot range by slot range with mcpd_run_slots_async: each range adds
+    the next global slot ids into the same integer N*_p buckets and the estimate is finalized over
+    every slot so far, which is the same estimator as one decode over that many slots.  After each
+    range the largest SE is read; the run stops at the first range that meets the target.  The next
+    range's size comes from the SE's P^-1/2 law (slot means are i.i.d., Theorem 2): enough slots to
+    reach the target if the law holds, at least `first_slots` and at most 8 times the slots so far.
+
+    Returns the sampling kernels' summed CUDA-event time (`kernel_ms`), the wall time from plan
+    creation through the copy of the SEs that met the target (`wall_ms`), the slots used, the final
+    largest SE, whether it met the target, and the path [(slots so far, max SE, kernel ms so far)].
+    The plan is shaped for `plan_slots` slots (the launch shape of the bench's decode); every range
+    keeps its grid and trims its warps per block to whole rounds of the range."""
+    import torch
+    t0 = time.perf_counter()
+    kw = dict(slots=plan_slots, horizon=int(sweeps * inst.n), seed=seed)
+    if weights is not None:
+        kw.update(scan=mcpd.MCPD_SCAN_CUSTOM, scan_weights=weights)
+    if init is not None:
+        kw.update(init_marginals=init)
+    if lag_sweeps > 0:
+        kw.update(lag=max(1, int(round(lag_sweeps * inst.n))))
+    plan = mcpd.Plan(ctx, inst, **kw)
+    est = torch.empty(plan.n_active, dtype=torch.float64, device=f"cuda:{ctx.device}")
+    se = torch.empty_like(est)
+    total, kernel_ms, path, add = 0, 0.0, [], int(first_slots)
+    mean_tau_num = mean_tau_den = 0
     while True:
-        mse, ms, st = decode_max_se(ctx, instances, P, sweeps, seed, weights, init, lag_sweeps=lag_sweeps)
-        path.append((P, mse, ms))
-        if mse <= target or P >= max_slots:
-            return dict(slots=P, max_se=mse, kernel_ms=ms, wall_ms=st["wall_ms"], path=path, met=mse <= target)
-        P *= 2
+        plan.run_slots_async(add, est, se, accumulate=total > 0)
+        st = plan.collect()
+        total += add
+        kernel_ms += st["kernel_ms"]
+        mean_tau_num += st["sum_tau"]
+        mean_tau_den += st["reps_retained"]
+        mse = float(se.cpu().numpy().max())
+        path.append((total, mse, kernel_ms))
+        if mse <= target or total >= max_slots:
+            break
+        need = total * (mse / target) ** 2
+        add = int(min(max(need * 1.02 - total, first_slots), 8 * total, max_slots - total))
+        add = (add + 31) // 32 * 32
+    wall_ms = 1000.0 * (time.perf_counter() - t0)
+    plan.close()
+    return dict(slots=total, max_se=mse, kernel_ms=kernel_ms, wall_ms=wall_ms, path=path,
+                met=mse <= target, ranges=len(path), mean_tau=mean_tau_num / max(1, mean_tau_den))
 
 
 def now() -> float:

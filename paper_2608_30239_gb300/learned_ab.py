@@ -13,8 +13,9 @@
 3. Report per variant the largest per-clone standard error of each instance and the projected
    time to reach SE <= 0.005: the slot means are i.i.d., so SE scales as P^-1/2 and the decode time
    as P; projected time = (batch kernel time / instances) * (max SE / 0.005)^2 per instance.
-4. Measure time-to-SE directly on the bench instance: double P from 65536 until its largest SE is
-   <= 0.005 and report the kernel time of the first decode that meets it.
+4. With --direct, measure time-to-SE on the bench instance and the first `--direct-held` held-out
+   instances: one decode per variant extended slot range by slot range until its largest SE is
+   <= 0.005 (learned.time_to_se), reporting the summed kernel time and the wall time.
 Prints one JSON line.
 """
 from __future__ import annotations
@@ -42,7 +43,8 @@ def main(argv=None):
     ap.add_argument("--slots", type=int, default=16384)
     ap.add_argument("--nu-floor", type=float, default=0.02)
     ap.add_argument("--epochs", type=int, default=30)
-    ap.add_argument("--direct", action="store_true", help="also measure time-to-SE by doubling P")
+    ap.add_argument("--direct", action="store_true", help="also measure time-to-SE directly")
+    ap.add_argument("--direct-held", type=int, default=4, help="held-out instances measured directly")
     a = ap.parse_args(argv)
     ctx = mcpd.Context(0)
     rng = np.random.default_rng(0)
@@ -88,12 +90,20 @@ def main(argv=None):
         out["variants"][name]["speedup_vs_paper_geomean"] = float(np.exp(-np.mean(np.log(r))))
         out["variants"][name]["instances_faster"] = int(np.sum(r < 1.0))
     if a.direct:
-        inst = synth.high_noise_config()
-        Xb = learned.features(ctx, [inst])
-        wb, nub = learned.learned_inputs(model, Xb, learned.segments([inst]), nu_floor=a.nu_floor)
-        out["direct_bench_instance"] = {
-            "paper_weights_allneg": learned.time_to_se(ctx, [inst], 0.005, 29.4, 65536, 7),
-            "paper_weights_learned_nu": learned.time_to_se(ctx, [inst], 0.005, 29.4, 65536, 7, init=nub)}
+        out["direct"] = {}
+        for label, inst in [("bench", synth.high_noise_config())] + \
+                           [(f"held{i}", held[i]) for i in range(min(a.direct_held, a.held))]:
+            Xb = learned.features(ctx, [inst])
+            wb, nub = learned.learned_inputs(model, Xb, learned.segments([inst]), nu_floor=a.nu_floor)
+            arms = {}
+            for name, kw in (("paper_weights_allneg", {}), ("paper_weights_learned_nu", dict(init=nub)),
+                             ("learned_w_learned_nu", dict(weights=wb, init=nub))):
+                r = learned.time_to_se(ctx, inst, 0.005, 29.4, seed=7, **kw)
+                arms[name] = {k: r[k] for k in ("kernel_ms", "wall_ms", "slots", "max_se", "met", "mean_tau")}
+            base = arms["paper_weights_allneg"]["kernel_ms"]
+            for v in arms.values():
+                v["speedup_vs_paper"] = base / v["kernel_ms"]
+            out["direct"][label] = arms
     print(json.dumps(out), flush=True)
     ctx.close()
     return out

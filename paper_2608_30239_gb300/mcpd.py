@@ -52,7 +52,9 @@ class mcpd_stats(C.Structure):
     _fields_ = [(name, C.c_int64) for name in
                 ("progress_units", "site_updates", "reps_started", "reps_retained", "reps_aborted",
                  "zero_completion_slots", "step_limit_hits", "max_tau", "sum_tau", "n_buckets",
-                 "n_active")] + [("kernel_ms", C.c_double), ("tau_over_audit", C.c_int64)]
+                 "n_active")] + [("kernel_ms", C.c_double), ("tau_over_audit", C.c_int64),
+                                 ("resident_pairs", C.c_int64), ("h2d_bytes", C.c_int64),
+                                 ("d2h_bytes", C.c_int64)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -88,6 +90,7 @@ def lib(build_if_missing: bool = False):
             "mcpd_plan_info": (C.c_int, [P, P]),
             "mcpd_plan_active": (C.c_int, [P, P]),
             "mcpd_run_async": (C.c_int, [P, P, P, P]),
+            "mcpd_run_slots_async": (C.c_int, [P, P, C.c_int64, C.c_int32, P, P]),
             "mcpd_collect": (C.c_int, [P, P, C.POINTER(mcpd_stats)]),
             "mcpd_fetch_bytes": (C.c_size_t, [P, C.c_int]),
             "mcpd_fetch": (C.c_int, [P, P, C.c_int, P, C.c_size_t]),
@@ -303,6 +306,13 @@ class Plan:
         _check_out(est_dev, se_dev, self.n_active, self.ctx.device)
         self.ctx.check(lib().mcpd_run_async(self.ctx.h, self.h, _ptr(est_dev), _ptr(se_dev)),
                        "mcpd_run_async")
+
+    def run_slots_async(self, slots, est_dev, se_dev, accumulate=False):
+        """mcpd_run_slots_async: `slots` slots with the plan's horizon; accumulate=True adds them
+        to the slots already run (the next global slot ids) and finalizes over all of them."""
+        _check_out(est_dev, se_dev, self.n_active, self.ctx.device)
+        self.ctx.check(lib().mcpd_run_slots_async(self.ctx.h, self.h, int(slots), int(bool(accumulate)),
+                                                  _ptr(est_dev), _ptr(se_dev)), "mcpd_run_slots_async")
 
     def collect(self, allow_step_limit=False):
         st = mcpd_stats()

@@ -57,6 +57,8 @@ CASES = {
                       dict(slots=7777, k=41, ell=400, horizon=2017, seed=2024)),
     "library-high-noise": (lambda: synth.high_noise_config(),
                            dict(slots=4096, budget_site_updates=4e10 * 4096 / 524288, seed=20260)),
+    "capped-lag": (lambda: synth.make_instance(400, 31, 5, 3, 0.05, 0.1, 3 / 400, 43, 44),
+                   dict(slots=5000, k=41, ell=400, horizon=1600, seed=77, meeting_cap=800, lag=2)),
 }
 
 
@@ -72,6 +74,27 @@ def test_noalloc_equals_allocating_path_twice(ctx, case):
         assert np.array_equal(s, s_ref), (case, call)
         assert st["reps_retained"] == st_ref["reps_retained"]
         assert st["site_updates"] == st_ref["site_updates"]
+        assert 0 < st["resident_pairs"] <= st_ref["resident_pairs"]
+    if case == "library-high-noise":
+        # 1298 clones need about 21 KB of pair accumulators per pair: the 64 MiB array holds fewer
+        # pairs than the allocating path runs, and the results above were still identical
+        assert st["resident_pairs"] < st_ref["resident_pairs"]
+
+
+def test_noalloc_refuses_outputs_not_on_the_device(ctx):
+    """Host arrays passed as outputs are refused before any launch; the context stays usable."""
+    import torch
+    from paper_2608_30239_gb300 import mcpd
+    inst = synth.tiny_config(1)
+    kw = dict(slots=256, k=3, ell=20, horizon=60, seed=5)
+    est = torch.zeros(inst.n, dtype=torch.float64)
+    se = torch.zeros_like(est)
+    with pytest.raises(mcpd.McpdError) as ei:
+        ctx.decode_noalloc(inst, est, se, **kw)
+    assert ei.value.code == mcpd.MCPD_EINVAL
+    e, s, st = _noalloc_path(ctx, inst, **kw)
+    e_ref, s_ref, _ = _plan_path(ctx, inst, **kw)
+    assert np.array_equal(e, e_ref) and np.array_equal(s, s_ref)
 
 
 def test_noalloc_rejects_problems_beyond_its_array(ctx):
