@@ -36,6 +36,19 @@ def log_posterior_table(inst, active):
     return prior + lik, Z
 
 
+def log_posterior(inst, active, Z):
+    """Unnormalised log pi_A(z) for the states given as rows of Z ([S, n_a] 0/1), any n_a."""
+    Z = np.asarray(Z, dtype=np.int64).reshape(-1, len(active))
+    A = _incidence(inst, active)
+    xi = (Z @ A) > 0
+    y = inst.y.astype(bool)[None, :]
+    fp, fn, q = inst.fp, inst.fn, inst.q
+    lik = np.where(xi, np.where(y, np.log1p(-fn), np.log(fn)),
+                   np.where(y, np.log(fp), np.log1p(-fp))).sum(axis=1)
+    k = Z.sum(axis=1)
+    return k * np.log(q) + (len(active) - k) * np.log1p(-q) + lik
+
+
 def posterior(inst, active=None):
     """(pi over states, marginals p_j = E_pi[Z_j]) of the pruned posterior."""
     if active is None:

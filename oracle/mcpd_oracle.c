@@ -188,13 +188,17 @@ int orc_model_new(int32_t n, int32_t m, const int32_t *clone_ptr, const int32_t 
     M->y = (uint8_t *)malloc((size_t)m + 1);
     for (int32_t j = 0; j < m; ++j) M->y[j] = y[j] ? 1 : 0;
 
-    /* Naive ranking as a log score: eta_i = log(q/(1-q)) + sum_{j in P(i)} a_j, ascending j. */
+    /* Naive ranking (Knill et al.) as a log score: eta_i = log(q/(1-q)) + log R_i, where R_i, the
+     * product over the pools of i of Pr(y_j|xi_j=1)/Pr(y_j|xi_j=0), is a+ per positive and a- per
+     * negative pool: eta_i = (lambda + n+_i a+) + n-_i a-.  Equal counts give exactly equal
+     * scores, so ties are broken by index as the reading of the pruning rule says. */
     M->eta = (double *)malloc(sizeof(double) * (size_t)n);
     for (int32_t i = 0; i < n; ++i) {
-        double s = M->lambda;
-        for (int32_t e = clone_ptr[i]; e < clone_ptr[i + 1]; ++e)
-            s = s + (M->y[clone_pools[e]] ? M->a_plus : M->a_minus);
-        M->eta[i] = s;
+        int32_t npos = 0, nneg = 0;
+        for (int32_t e = clone_ptr[i]; e < clone_ptr[i + 1]; ++e) {
+            if (M->y[clone_pools[e]]) npos++; else nneg++;
+        }
+        M->eta[i] = (M->lambda + (double)npos * M->a_plus) + (double)nneg * M->a_minus;
     }
     /* Pruning: keep the top n_active clones by eta (ties: lower index), relabel ascending. */
     int32_t na = (n_active <= 0 || n_active >= n) ? n : n_active;
@@ -529,21 +533,26 @@ static rep_result coupled_replication(const orc_model *M, const orc_run *R, uint
 }
 
 /* One uncoupled chain (Algorithms 1 and 2): X_0 ~ nu, X_{t+1} = Phi_{I_t}(X_t, U_t) for
- * t = 0..b+T-2, G_j = sum_{t=b}^{b+T-1} X_t[j]; cost C = b + T - 1 draws. */
+ * t = 0..b+T-2, G_j = sum_{t=b}^{b+T-1} X_t[j]; cost C = b + T - 1 draws.
+ * trajX (optional, tests) receives X_0..X_C and sites the drawn I_0..I_{C-1}, up to traj_cap. */
 static rep_result uncoupled_replication(const orc_model *M, const orc_run *R, uint32_t slot,
-                                        uint32_t rep, int64_t *G) {
+                                        uint32_t rep, int64_t *G, uint8_t *trajX, int32_t *sites,
+                                        int64_t traj_cap) {
     const int32_t na = M->na;
     const int64_t b = R->burn, T = R->length;
     rep_result res = {0, 0, 0, ORC_OK, 0};
     uint8_t *X = (uint8_t *)malloc((size_t)na);
     initial_state(M, R, slot, rep, X);
+    if (trajX && traj_cap > 0) memcpy(trajX, X, (size_t)na);
     for (int32_t a = 0; a < na; ++a) G[a] = (b == 0) ? X[a] : 0;
     for (int64_t t = 0; t <= b + T - 2; ++t) {
         int32_t I;
         uint64_t U;
         step_draw(M, R, slot, rep, t, &I, &U);
+        if (sites && t < traj_cap) sites[t] = I;
         orc_phi(M, X, I, U);
         res.draws += 1;
+        if (trajX && t + 1 < traj_cap) memcpy(trajX + (size_t)(t + 1) * na, X, (size_t)na);
         if (t + 1 >= b && t + 1 <= b + T - 1)
             for (int32_t a = 0; a < na; ++a) G[a] += X[a];
     }
@@ -582,7 +591,7 @@ static int32_t run_slot(const orc_model *M, const orc_run *R, int64_t p, int64_t
     so->S_retained = 0;
     for (uint32_t r = 0;; ++r) {
         rep_result rr = R->coupled ? coupled_replication(M, R, slot, r, Gr, 0, NULL, NULL, NULL, 0)
-                                   : uncoupled_replication(M, R, slot, r, Gr);
+                                   : uncoupled_replication(M, R, slot, r, Gr, NULL, NULL, 0);
         so->reps_started++;
         stats[0] += rr.draws;
         stats[1] += 1;
@@ -723,7 +732,7 @@ int orc_replication(const orc_model *M, const orc_run *R, int64_t p, int32_t rep
     if (R->coupled)
         rr = coupled_replication(M, R, slot, (uint32_t)rep, G, literal, trajX, trajY, sites, traj_cap);
     else
-        rr = uncoupled_replication(M, R, slot, (uint32_t)rep, G);
+        rr = uncoupled_replication(M, R, slot, (uint32_t)rep, G, trajX, sites, traj_cap);
     out4[0] = rr.C; out4[1] = rr.tau; out4[2] = rr.draws; out4[3] = rr.capped;
     return rr.status;
 }

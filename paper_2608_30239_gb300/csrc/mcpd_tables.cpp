@@ -76,12 +76,15 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
     const double lam = std::log(q) - std::log(1.0 - q);
     auto a_of = [&](int32_t j) { return y[j] ? a_pos : a_neg; };
 
-    // Naive log score eta_i = lambda + sum_{j in P(i)} a_j and pruning to the top n_active.
+    // Naive log score eta_i = lambda + log R_i = (lambda + n+_i a+) + n-_i a- (R_i, the product of
+    // the likelihood ratios of the pools holding i, depends on its positive and negative pool
+    // counts only, so clones with equal counts tie exactly and go to the lower index), and
+    // pruning to the top n_active.
     std::vector<double> eta(n);
     for (int32_t i = 0; i < n; ++i) {
-        double s = lam;
-        for (int32_t e = d->clone_ptr[i]; e < d->clone_ptr[i + 1]; ++e) s = s + a_of(d->clone_pools[e]);
-        eta[i] = s;
+        int32_t npos = 0, nneg = 0;
+        for (int32_t e = d->clone_ptr[i]; e < d->clone_ptr[i + 1]; ++e) (y[d->clone_pools[e]] ? npos : nneg) += 1;
+        eta[i] = (lam + static_cast<double>(npos) * a_pos) + static_cast<double>(nneg) * a_neg;
     }
     int32_t na = (prm->n_active <= 0 || prm->n_active >= n) ? n : prm->n_active;
     std::vector<char> keep(n, 1);

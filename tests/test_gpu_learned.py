@@ -131,3 +131,18 @@ def test_learned_initial_marginals_gain(ctx):
     print("max SE plain", plain_se.max(), "learned nu", nu_se.max(), "mean tau", tau(plain_st), tau(nu_st))
     assert nu_se.max() < plain_se.max()
     assert tau(nu_st) < 0.5 * tau(plain_st)
+
+
+def test_forward_on_the_hand_worked_network(ctx):
+    """The GPU forward pass on the integer network of the oracle's hand-worked pin gives exactly the
+    numbers read off that network (every value is a small integer or half-integer: exact in fp32)."""
+    import torch
+    from test_learned_oracle import _readable_network
+    from paper_2608_30239_gb300 import learned
+    model = learned.MLP(ctx, seed=0)
+    model.master.copy_(torch.from_numpy(_readable_network().astype(np.float32)))
+    model.cast()
+    X = torch.tensor([[(k + 1) * (-1) ** k for k in range(16)], [0.5] * 16], dtype=torch.float32,
+                     device=f"cuda:{ctx.device}")
+    O = model.forward(X).cpu().numpy()
+    assert np.array_equal(O, np.array([[-14.5, -8.0], [2.0, -6.0]], dtype=np.float32))

@@ -577,3 +577,112 @@ def test_lag_changes_the_estimates_and_the_cost(oracle_lib):
     assert b["slot_S"].min() >= 6 and a["slot_S"].min() >= 4
     bad = M.run_slots(oracle_lib.coupled_run(3, 4, 0, seed=13, lag=6, meeting_cap=5), 0, 10)
     assert bad["status"] == oracle_lib.ORC_EINVAL
+
+
+# ---------------------------------------------------------------------------------------------
+# The uncoupled comparators (Algorithms 1 and 2), step by step against their definition.
+def _step_words(seed, instance, slot, rep, t, oracle_lib):
+    """(w_site, U) of draw t: Philox4x32-10 (pinned by its known-answer vectors) at counter
+    (floor(t/2), rep, slot, instance) gives the site word and the uniform's high word (words 0, 1
+    at even t, 2, 3 at odd t); the low word is word 0 of the tag-2 block at counter t."""
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    b = [int(v) for v in oracle_lib.philox([t >> 1, rep, slot, instance], key)]
+    lo = int(oracle_lib.philox([t, rep, slot, (2 << 24) | instance], key)[0])
+    ws, wu = (b[2], b[3]) if t & 1 else (b[0], b[1])
+    return ws, (wu << 32) | lo
+
+
+def _site(ws, na, prob, alias):
+    """Alias draw written out: column floor(ws n_a / 2^32), kept if the low 32 bits of ws n_a are
+    below its probability word, else its alias."""
+    prod = ws * na
+    col, coin = prod >> 32, prod & 0xFFFFFFFF
+    return col if coin < int(prob[col]) else int(alias[col])
+
+
+@pytest.mark.parametrize("scan,burn,length,start", [
+    ("systematic", 0, 5, "zero"), ("systematic", 7, 1, "zero"), ("score", 3, 12, "zero"),
+    ("uniform", 20, 20, "random"), ("score", 0, 1, "random"), ("score", 4, 9, "random")])
+def test_uncoupled_path_follows_algorithms_1_and_2(oracle_lib, scan, burn, length, start):
+    """Against a restatement from the posterior itself, not the oracle's own update: the stored
+    path X_0..X_C of one chain has C = b + T - 1 draws, G_j = sum_{t=b}^{b+T-1} X_t[j] summed from
+    the path, the site I_t = t mod n_a (systematic) or the alias draw of the step word (score,
+    uniform), X_{t+1} differs from X_t at most at I_t, and its new bit is 1{U_t / 2^64 < p} with
+    p = sigmoid(log pi(x^{I<-1}) - log pi(x^{I<-0})) from the unnormalised posterior (draws within
+    1e-9 of p are not judged).  A chain that averages X_{b+1}..X_{b+T}, charges b + T draws or
+    visits I_t = (t + 1) mod n_a fails here."""
+    inst = _noisy()
+    sc = {"systematic": oracle_lib.SCAN_SYSTEMATIC, "score": oracle_lib.SCAN_SCORE,
+          "uniform": oracle_lib.SCAN_UNIFORM}[scan]
+    nu = np.random.default_rng(5).uniform(0.0, 0.6, inst.n) if start == "random" else None
+    M = oracle_lib.Model(inst, scan=sc, init_marginals=nu)
+    tab = M.tables()
+    na, seed = M.na, 0xABCDEF0123
+    active = np.arange(inst.n)
+    run = oracle_lib.uncoupled_run(burn, length, 0, seed=seed)
+    C = burn + length - 1
+    judged = 0
+    for slot in range(40):
+        rr = M.replication(run, slot, 0, traj_cap=C + 1)
+        assert rr["status"] == 0 and rr["C"] == C and rr["draws"] == C
+        X = rr["X"][:C + 1].astype(np.int64)
+        assert np.array_equal(rr["G"], X[burn:burn + length].sum(axis=0))
+        for t in range(C):
+            ws, U = _step_words(seed, 0, slot, 0, t, oracle_lib)
+            I = t % na if scan == "systematic" else _site(ws, na, tab["prob"], tab["alias"])
+            assert rr["sites"][t] == I, (slot, t)
+            diff = np.flatnonzero(X[t + 1] != X[t])
+            assert set(diff.tolist()) <= {I}
+            hi, lo = X[t].copy(), X[t].copy()
+            hi[I], lo[I] = 1, 0
+            lp = exact.log_posterior(inst, active, np.stack([hi, lo]))
+            p = 1.0 / (1.0 + math.exp(-(lp[0] - lp[1])))
+            u = U / 2.0 ** 64
+            if abs(u - p) > 1e-9:
+                assert X[t + 1][I] == (1 if u < p else 0), (slot, t)
+                judged += 1
+    assert judged >= 40 * C * 0.99
+
+
+def test_uncoupled_long_chain_agrees_with_enumeration(oracle_lib):
+    """Algorithm 2 with a long burn-in: the average over X_b..X_{b+T-1} of a score-weighted chain
+    started all-negative is, after 100 sweeps of burn-in, within sampling error of the exact
+    marginals of the 2^20 enumeration (z-tests over the 20 clones; the short-window control
+    above fails the same test)."""
+    inst = _noisy()
+    _, p = exact.posterior(inst)
+    res = oracle_lib.decode(inst, 4000, 0, 0, 0, seed=77, coupled=False, burn=2000, length=2000)
+    assert res["status"] == 0
+    z = _z_scores(res["est"], res["se"], p)
+    assert z.max() < 4.5, z
+
+
+# ---------------------------------------------------------------------------------------------
+# The naive score and the pruning of Knill's method.
+@pytest.mark.parametrize("which", ["tiny", "noisy", "library"])
+def test_naive_score_is_the_posterior_log_ratio(oracle_lib, which):
+    """eta_i = log pi(e_i | y) - log pi(0 | y) from the unnormalised posterior (Section "Knill's
+    Method": the naive ranking scores a clone by the posterior odds of it alone being positive),
+    for every clone, to 1e-12 relative.  A swapped a+ / a- or a weight that belongs to s_i fails."""
+    inst = {"tiny": lambda: synth.tiny_config(1), "noisy": _noisy,
+            "library": synth.high_noise_config}[which]()
+    eta = oracle_lib.Model(inst).tables()["eta"]
+    active = np.arange(inst.n)
+    Z = np.vstack([np.zeros((1, inst.n), np.int64), np.eye(inst.n, dtype=np.int64)])
+    lp = exact.log_posterior(inst, active, Z)
+    ref = lp[1:] - lp[0]
+    assert np.allclose(eta, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n_active", [1, 7, 333, 1297])
+def test_pruning_keeps_the_top_clones_by_the_independent_score(oracle_lib, n_active):
+    """The retained clones are the n_active largest by the posterior log ratio above (ties, which
+    the score's few distinct values make common, to the lower original index), listed ascending."""
+    inst = synth.high_noise_config()
+    Z = np.vstack([np.zeros((1, inst.n), np.int64), np.eye(inst.n, dtype=np.int64)])
+    lp = exact.log_posterior(inst, np.arange(inst.n), Z)
+    ref = np.round(lp[1:] - lp[0], 9)                   # exact ties stay ties
+    order = sorted(range(inst.n), key=lambda i: (-ref[i], i))
+    want = np.sort(np.array(order[:n_active]))
+    got = oracle_lib.Model(inst, n_active=n_active).tables()["active"]
+    assert np.array_equal(got, want)
