@@ -105,6 +105,12 @@ typedef struct mcpd_params {
                                   tau = inf{t >= L : X_t = Y_{t-L}} and
                                   H_r = X_r + sum_{j>=1} (X_{r+jL} - Y_{r+(j-1)L}).  Every
                                   replication costs max(l, tau) >= max(l, L).  At most 2^20      */
+    int64_t trace_steps;       /* > 0 (coupled, trace_stride > 0): also record, for the first
+                                  trace_reps replications of every traced slot, the meeting time,
+                                  the completion time and, for the first trace_steps draws, the
+                                  site and which chains flipped (MCPD_FETCH_TRACE_REC).  Runs that
+                                  set it launch a recording variant of the sampler; at most 2^20   */
+    int64_t trace_reps;        /* replications recorded per traced slot (0: 8); at most 1024      */
 } mcpd_params;
 
 /* Counters of one run.  site_updates, reps_started, reps_retained and tau_over_audit are -1 if a
@@ -189,6 +195,15 @@ int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *plan, mcpd_stats *stats);
 #define MCPD_FETCH_SLOT_S 5    /* int64  [slots] retained progress units (record_slots = 1)         */
 #define MCPD_FETCH_SLOT_REPS 6 /* int32  [slots] replications started (record_slots = 1)            */
 #define MCPD_FETCH_TRACE_G 7   /* int64  [ceil(slots/stride)][n_active] (trace_stride > 0)          */
+#define MCPD_FETCH_TRACE_REC 8 /* int32  [ceil(slots/stride)][trace_reps][4 + trace_steps]
+                                  (trace_steps > 0): per replication r of traced slot p: [0] its
+                                  meeting time tau (0: stopped unmet at the meeting cap), [1] its
+                                  completion time C (or the clock when it was stopped), [2] 1
+                                  completed, 2 stopped as doomed (Algorithm 4: it could not finish
+                                  within the horizon), 3 step limit, 0 not started; [3] r; then for
+                                  draw t < min(C, trace_steps): the site I_t | X flipped << 16 |
+                                  Y flipped << 17 (the chain that draw t moves: X_{t+1} and, from
+                                  t = L on, Y_{t+1-L})                                           */
 size_t mcpd_fetch_bytes(const mcpd_plan *plan, int what);
 int mcpd_fetch(mcpd_ctx *ctx, const mcpd_plan *plan, int what, void *host_dst, size_t bytes);
 
@@ -232,7 +247,9 @@ void mcpd_batch_destroy(mcpd_batch *batch);
  * [4] warps per block, [5] blocks and [7] shared-memory bytes per block of the first class (the
  * largest pair state), [6] resident pairs of the widest class, [8] lanes per pair, [9] size
  * classes, [10] largest warps per block over the classes, [11] classes that launch the kernel
- * variant with meeting caps and lags > 1. */
+ * variant with meeting caps and lags > 1, [12] classes that launch a build with a compile-time
+ * degree and mask-indexed thresholds (coupled classes, without caps or lags, whose instances all
+ * sit in exactly 3 or exactly 6 pools per clone). */
 int mcpd_batch_info(const mcpd_batch *batch, int64_t info[16]);
 /* offsets: [n_inst + 1] host array receiving each instance's first output index. */
 int mcpd_batch_offsets(const mcpd_batch *batch, int64_t *offsets);

@@ -1,8 +1,10 @@
 """Build the in-tree shared library `_build/libmcpd.so` for sm_103a (GB300).
 
-Three translation units compiled in parallel: the host table builder (g++, -ffp-contract=off so
-every double expression keeps its written order), the C ABI (g++), and the kernels (nvcc,
-`-gencode arch=compute_103a,code=sm_103a`).  No cmake; a rebuild happens only when a source is
+Translation units compiled in parallel: the host table builder (g++, -ffp-contract=off so every
+double expression keeps its written order), the C ABI (g++), and the kernels (nvcc,
+`-gencode arch=compute_103a,code=sm_103a`: the sampling kernel's single-instance variants, its
+batched variants, its trajectory-recording variants, the no-allocation entry point, the learned model, the lane-group
+kernel).  No cmake; a rebuild happens only when a source is
 newer than the library.
 """
 from __future__ import annotations
@@ -33,8 +35,8 @@ def _cuda_home() -> str:
 
 def sources():
     return [os.path.join(SRC, f) for f in ("mcpd_tables.cpp", "mcpd_api.cpp", "mcpd_kernels.cu",
-                                           "mcpd_noalloc.cu", "mcpd_mlp.cu", "mcpd_group.cu", "mcpd_internal.h",
-                                           "mcpd_device.cuh")] + \
+                                           "mcpd_trace.cu", "mcpd_batch.cu", "mcpd_noalloc.cu", "mcpd_mlp.cu", "mcpd_group.cu",
+                                           "mcpd_internal.h", "mcpd_device.cuh", "mcpd_pairs.cuh")] + \
         [os.path.join(INCLUDE, "mcpd.h")]
 
 
@@ -52,7 +54,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     inc = ["-I" + INCLUDE, "-I" + SRC, "-I" + os.path.join(cuda, "include")]
-    objs = {name: os.path.join(BUILD, name + ".o") for name in ("tables", "api", "kernels", "noalloc", "mlp", "group")}
+    objs = {name: os.path.join(BUILD, name + ".o")
+            for name in ("tables", "api", "kernels", "trace", "batch", "noalloc", "mlp", "group")}
     cxx = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-Wall"]
     jobs = [
         cxx + inc + ["-c", os.path.join(SRC, "mcpd_tables.cpp"), "-o", objs["tables"]],
@@ -60,6 +63,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
         + (["-Xptxas", "-v"] if ptxas_info else []) + inc
         + ["-c", os.path.join(SRC, "mcpd_kernels.cu"), "-o", objs["kernels"]],
+        [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
+        + inc + ["-c", os.path.join(SRC, "mcpd_trace.cu"), "-o", objs["trace"]],
+        [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
+        + inc + ["-c", os.path.join(SRC, "mcpd_batch.cu"), "-o", objs["batch"]],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
         + inc + ["-c", os.path.join(SRC, "mcpd_noalloc.cu"), "-o", objs["noalloc"]],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
@@ -78,8 +85,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if verbose or ptxas_info:
         sys.stdout.write("".join(logs))
     tmp = LIB + f".tmp{os.getpid()}"
-    link = [nvcc, ARCH, "-shared", "-o", tmp, objs["tables"], objs["api"], objs["kernels"],
-            objs["noalloc"], objs["mlp"], objs["group"], "-cudart", "static"]
+    link = [nvcc, ARCH, "-shared", "-o", tmp, objs["tables"], objs["api"], objs["kernels"], objs["trace"],
+            objs["batch"], objs["noalloc"], objs["mlp"], objs["group"], "-cudart", "static"]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
     return LIB

@@ -182,6 +182,8 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     if (t.trace_stride > 0) {
         pl->n_trace = (t.P + t.trace_stride - 1) / t.trace_stride;
         ALLOC(kp.trace_G, static_cast<size_t>(pl->n_trace) * t.na);
+        if (t.trace_steps > 0)
+            ALLOC(kp.trace_rec, static_cast<size_t>(pl->n_trace) * t.trace_reps * (4 + t.trace_steps));
     }
 #undef ALLOC
     CU_OR(cudaMemcpyAsync(d_alias, t.alias.data(), t.alias.size() * 8, cudaMemcpyHostToDevice, ctx->stream), mcpd_plan_destroy(pl));
@@ -204,6 +206,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     kp.capped = t.capped ? 1 : 0;
     kp.lag = static_cast<int32_t>(t.lag);
     kp.slot_offset = t.slot_offset; kp.trace_stride = t.trace_stride;
+    kp.trace_reps = static_cast<int32_t>(t.trace_reps); kp.trace_steps = static_cast<int32_t>(t.trace_steps);
     kp.seed = t.seed; mcpd::philox_round_keys(t.seed, kp.rk); kp.instance = t.instance; kp.warps = warps;
     kp.smem_tables = static_cast<uint32_t>(tables);
     kp.nT = static_cast<int32_t>(mcpd::kernel_T(t).size());
@@ -278,6 +281,9 @@ int run_range(mcpd_ctx *ctx, mcpd_plan *pl, int64_t slots, bool accumulate, doub
         CU(cudaMemsetAsync(kp.y_state, 0, static_cast<size_t>(pl->pairs) * t.wpp * 4, ctx->stream));
     }
     if (kp.trace_G) CU(cudaMemsetAsync(kp.trace_G, 0, static_cast<size_t>(pl->n_trace) * t.na * 8, ctx->stream));
+    if (kp.trace_rec)
+        CU(cudaMemsetAsync(kp.trace_rec, 0, static_cast<size_t>(pl->n_trace) * t.trace_reps * (4 + t.trace_steps) * 4,
+                           ctx->stream));
     if (kp.slot_nstar) {
         CU(cudaMemsetAsync(kp.slot_nstar, 0, static_cast<size_t>(t.P) * 4, ctx->stream));
         CU(cudaMemsetAsync(kp.slot_S, 0, static_cast<size_t>(t.P) * 8, ctx->stream));
@@ -351,6 +357,8 @@ size_t mcpd_fetch_bytes(const mcpd_plan *pl, int what) {
         case MCPD_FETCH_SLOT_S: return pl->kp.slot_S ? static_cast<size_t>(pl->t.P) * 8 : 0;
         case MCPD_FETCH_SLOT_REPS: return pl->kp.slot_reps ? static_cast<size_t>(pl->t.P) * 4 : 0;
         case MCPD_FETCH_TRACE_G: return pl->kp.trace_G ? static_cast<size_t>(pl->n_trace) * pl->t.na * 8 : 0;
+        case MCPD_FETCH_TRACE_REC:
+            return pl->kp.trace_rec ? static_cast<size_t>(pl->n_trace) * pl->t.trace_reps * (4 + pl->t.trace_steps) * 4 : 0;
         default: return 0;
     }
 }
@@ -369,6 +377,7 @@ int mcpd_fetch(mcpd_ctx *ctx, const mcpd_plan *pl, int what, void *host_dst, siz
         case MCPD_FETCH_SLOT_S: src = pl->kp.slot_S; break;
         case MCPD_FETCH_SLOT_REPS: src = pl->kp.slot_reps; break;
         case MCPD_FETCH_TRACE_G: src = pl->kp.trace_G; break;
+        case MCPD_FETCH_TRACE_REC: src = pl->kp.trace_rec; break;
     }
     CU(cudaSetDevice(ctx->device));
     CU(cudaMemcpyAsync(host_dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
@@ -508,12 +517,12 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
         int per_sm = 1, w = 0;
         if (lanes == 1) {
             mcpd::PairsShape shape;
-            int rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, 0, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
+            int rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, c.bp.udeg, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
                                        ctx->sm_count, 0, c.bp.ext != 0, &shape);
             if (rc == MCPD_ETOO_LARGE) return set_err(ctx, rc, "largest instance does not fit one warp of pair state");
             if (rc != MCPD_OK) return set_err(ctx, rc, "cudaFuncSetAttribute / occupancy");
             if (warps > 0 && warps < shape.warps) {
-                rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, 0, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
+                rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, c.bp.udeg, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
                                        ctx->sm_count, warps, c.bp.ext != 0, &shape);
                 if (rc != MCPD_OK) return set_err(ctx, rc, "launch shape");
             }
@@ -679,7 +688,8 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     for (int32_t i = 0; i < n_inst; ++i) {
         const mcpd::Tables &t = b->t[i];
         table_bytes += up16(t.alias.size() * 8) + up16(t.rows.size() * 2) + up16(t.T.size() * 8) + up16(t.Tnu.size() * 8) +
-                       up16(t.init_pairs.size() * 4) + up16(t.rows_pool.size() * 2);
+                       up16(t.init_pairs.size() * 4) + up16(t.rows_pool.size() * 2) + up16(t.rows_mask.size() * 2) +
+                       up16(t.T_mask.size() * 8);
         b->out_offset[i + 1] = b->out_offset[i] + t.na;
         b->bucket_offset[i] = static_cast<int64_t>(b->total_bucket_words);
         b->total_bucket_words += static_cast<size_t>(t.nb) * t.na;
@@ -728,6 +738,8 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         d.init_pairs = static_cast<const uint32_t *>(put(t.init_pairs.data(), t.init_pairs.size() * 4));
         d.n_init_pairs = static_cast<int32_t>(t.init_pairs.size());
         d.rows_pool = static_cast<const uint16_t *>(put(t.rows_pool.data(), t.rows_pool.size() * 2));
+        d.rows_mask = static_cast<const uint16_t *>(put(t.rows_mask.data(), t.rows_mask.size() * 2));
+        d.T_mask = static_cast<const uint64_t *>(put(t.T_mask.data(), t.T_mask.size() * 8));
         d.S1 = b->d_buckets + b->bucket_offset[i];
         d.S2lo = b->d_buckets + b->total_bucket_words + b->bucket_offset[i];
         d.S2hi = b->d_buckets + 2 * b->total_bucket_words + b->bucket_offset[i];
@@ -743,6 +755,9 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         mcpd::BParams &bp = c.bp;
         bp.total_work = work;
         if (t.capped || t.lag > 1) bp.ext = 1;
+        // the class's uniform degree: the first instance's, kept while every instance shares it
+        if (d.work_begin == 0) bp.udeg = t.udeg;
+        else if (bp.udeg != t.udeg) bp.udeg = 0;
         bp.max_na = std::max(bp.max_na, t.na); bp.max_W = std::max(bp.max_W, t.W);
         bp.max_wpp = std::max(bp.max_wpp, t.wpp); bp.max_m = std::max(bp.max_m, t.m);
     }
@@ -778,17 +793,19 @@ int mcpd_batch_info(const mcpd_batch *b, int64_t info[16]) {
     if (!b || !info) return MCPD_EINVAL;
     std::memset(info, 0, 16 * sizeof(int64_t));
     int32_t max_na = 0;
-    int64_t pairs = 0, wmax = 0, ext = 0;
+    int64_t pairs = 0, wmax = 0, ext = 0, degree_builds = 0;
     for (const BatchClass &c : b->cls) {
         max_na = std::max(max_na, c.bp.max_na);
         pairs = std::max<int64_t>(pairs, c.pairs);
         wmax = std::max<int64_t>(wmax, c.warps);
         ext += c.bp.ext;
+        if (b->lanes == 1 && mcpd::batch_kernel_degree(c.bp.coupled, c.bp.ext, c.bp.udeg) > 0) ++degree_builds;
     }
     const BatchClass &c0 = b->cls[0];
     info[0] = b->total_active; info[1] = b->n_inst; info[2] = b->total_slots; info[3] = max_na;
     info[4] = c0.warps; info[5] = c0.grid; info[6] = pairs; info[7] = static_cast<int64_t>(c0.smem);
     info[8] = b->lanes; info[9] = static_cast<int64_t>(b->cls.size()); info[10] = wmax; info[11] = ext;
+    info[12] = degree_builds;
     return MCPD_OK;
 }
 

@@ -79,6 +79,7 @@ struct Tables {
     int64_t P = 0, B = 0, nb = 1, step_limit = 0, slot_offset = 0, trace_stride = 0, tau_audit = 0;
     bool capped = false;              // meeting cap: step_limit is the cap, a capped pair is kept
     int64_t lag = 1;                  // coupled lag L
+    int64_t trace_steps = 0, trace_reps = 0;   // per-replication trajectory records (tests)
     uint64_t seed = 0;
     uint32_t instance = 0;
     bool record_slots = false;
@@ -143,6 +144,8 @@ struct KParams {
     uint32_t rk[20];                  // Philox round keys of the seed
     int32_t nT;                       // threshold entries staged (kTSide^2, or mask-indexed)
     int32_t lag;                      // coupled lag L >= 1
+    int32_t *trace_rec;               // [n_trace][trace_reps][4 + trace_steps] or null
+    int32_t trace_reps, trace_steps;
 };
 
 // Philox4x32-10 round keys of a 64-bit seed: (lo + i 0x9E3779B9, hi + i 0xBB67AE85), i = 0..9.
@@ -164,6 +167,8 @@ struct InstDesc {
     const uint64_t *Tnu;              // [na] or null
     const uint32_t *init_pairs;       // [n_init_pairs] even clone ids with a nonzero threshold
     const uint16_t *rows_pool;        // [na * kRow] pool id | y << 15 (lane-group kernels)
+    const uint16_t *rows_mask;        // [na * kRow] mask-indexed rows (uniform degree 3..kMaskDeg) or null
+    const uint64_t *T_mask;           // [(kMaskDeg + 1) * 64] or null
     unsigned long long *S1, *S2lo, *S2hi, *bcount;   // this instance's N*_p buckets
     int32_t n_init_pairs, capped;     // capped: the step limit is a meeting cap
     int32_t na, W, wpp, deg, nb, dummy_word_index;
@@ -189,6 +194,7 @@ struct BParams {
     int32_t y_regions;                // 32-column Y regions in shared memory
     int32_t wide;                     // launch the 20-warp variant of the batch kernel
     int32_t ext;                      // some instance has a meeting cap or a lag > 1
+    int32_t udeg;                     // every instance of the class has this uniform degree (0: mixed)
 };
 
 // Launch shape of the one-thread-per-pair kernel (mcpd_kernels.cu).
@@ -207,6 +213,12 @@ size_t pairs_smem_bytes(size_t tables, int wpp, int warps, int y_regions);
 int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int wpp, size_t smem_optin,
                 long long P, int sm_count, int warps, bool ext, PairsShape *out);
 
+// The batched sampling-kernel variants (mcpd_batch.cu): the kernel for a class, and the
+// compile-time degree a class of uniform degree udeg runs with (0: the generic build).
+using PairsKernelFn = void (*)(const KParams, const BParams);
+PairsKernelFn pick_batch(int coupled, int scan, int udeg, bool wide, bool ext);
+int batch_kernel_degree(int coupled, int ext, int udeg);
+
 // Launchers (mcpd_kernels.cu).
 int launch_batch(const BParams &bp, int grid, int block, size_t smem, void *stream);
 int launch_group(const BParams &bp, int grid, int block, size_t smem, void *stream);
@@ -218,6 +230,9 @@ int launch_finalize_batch(const InstDesc *insts, int n_inst, const int32_t *clon
                           const int32_t *clone_local, long long total_clones, double *est,
                           double *se, void *stream);
 int launch_pairs(const KParams &kp, int grid, int block, size_t smem, void *stream);
+// The recording variants (mcpd_trace.cu): launched by launch_pairs when kp.trace_rec is set.
+int launch_pairs_trace(const KParams &kp, int grid, int block, size_t smem, void *stream);
+int set_trace_smem(size_t bytes);
 int launch_finalize(const unsigned long long *S1, const unsigned long long *S2lo,
                     const unsigned long long *S2hi, int na, int nb, long long P, long long L,
                     double *est, double *se, void *stream);

@@ -314,6 +314,13 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
         return fail(err, "integer sums could overflow for this window, horizon and slot count", MCPD_EOVERFLOW);
     t.slot_offset = prm->slot_offset;
     t.trace_stride = prm->trace_stride > 0 ? prm->trace_stride : 0;
+    if (prm->trace_steps < 0 || prm->trace_steps > (int64_t(1) << 20) || prm->trace_reps < 0 ||
+        prm->trace_reps > 1024)
+        return fail(err, "trace_steps must be in [0, 2^20] and trace_reps in [0, 1024]", MCPD_EINVAL);
+    if (prm->trace_steps > 0 && (!t.coupled || t.trace_stride == 0))
+        return fail(err, "trajectory records need a coupled run with trace_stride > 0", MCPD_EINVAL);
+    t.trace_steps = prm->trace_steps;
+    t.trace_reps = prm->trace_steps > 0 ? (prm->trace_reps > 0 ? prm->trace_reps : 8) : 0;
     t.record_slots = prm->record_slots != 0;
     t.seed = prm->seed;
     if (prm->instance_id >= (1u << 24)) return fail(err, "instance_id must be < 2^24", MCPD_EINVAL);

@@ -18,7 +18,7 @@ MCPD_OK, MCPD_EINVAL, MCPD_ETOO_LARGE, MCPD_ENOMEM, MCPD_ECUDA, MCPD_ESTEP_LIMIT
     0, -1, -2, -3, -4, -5, -6
 MCPD_SCAN_SCORE, MCPD_SCAN_UNIFORM, MCPD_SCAN_SYSTEMATIC, MCPD_SCAN_CUSTOM = 0, 1, 2, 3
 (MCPD_FETCH_S1, MCPD_FETCH_S2_LO, MCPD_FETCH_S2_HI, MCPD_FETCH_COUNT, MCPD_FETCH_SLOT_NSTAR,
- MCPD_FETCH_SLOT_S, MCPD_FETCH_SLOT_REPS, MCPD_FETCH_TRACE_G) = range(8)
+ MCPD_FETCH_SLOT_S, MCPD_FETCH_SLOT_REPS, MCPD_FETCH_TRACE_G, MCPD_FETCH_TRACE_REC) = range(9)
 
 _ERRNAMES = {0: "MCPD_OK", -1: "MCPD_EINVAL", -2: "MCPD_ETOO_LARGE", -3: "MCPD_ENOMEM",
              -4: "MCPD_ECUDA", -5: "MCPD_ESTEP_LIMIT", -6: "MCPD_EOVERFLOW"}
@@ -45,7 +45,7 @@ class mcpd_params(C.Structure):
                 ("step_limit", C.c_int64), ("seed", C.c_uint64), ("instance_id", C.c_uint32),
                 ("record_slots", C.c_int32), ("slot_offset", C.c_int64),
                 ("trace_stride", C.c_int64), ("tau_audit", C.c_int64), ("meeting_cap", C.c_int64),
-                ("lag", C.c_int64)]
+                ("lag", C.c_int64), ("trace_steps", C.c_int64), ("trace_reps", C.c_int64)]
 
 
 class mcpd_stats(C.Structure):
@@ -170,7 +170,8 @@ def make_params(inst=None, keep: _Keep | None = None, *, fp=None, fn=None, prior
                 n_active=0, scan=MCPD_SCAN_SCORE, coupled=True, scan_weights=None,
                 init_marginals=None, k=-1, ell=-1, burn=-1, length=-1, slots=1, horizon=0,
                 budget_site_updates=0.0, step_limit=0, seed=1, instance_id=0, record_slots=False,
-                slot_offset=0, trace_stride=0, lanes_per_pair=0, tau_audit=0, meeting_cap=0, lag=0):
+                slot_offset=0, trace_stride=0, lanes_per_pair=0, tau_audit=0, meeting_cap=0, lag=0,
+                trace_steps=0, trace_reps=0):
     keep = keep or _Keep()
     sw = keep.arr(scan_weights, np.float64)
     nu = keep.arr(init_marginals, np.float64)
@@ -185,7 +186,7 @@ def make_params(inst=None, keep: _Keep | None = None, *, fp=None, fn=None, prior
         seed=int(seed) & 0xFFFFFFFFFFFFFFFF, instance_id=int(instance_id),
         record_slots=int(bool(record_slots)), slot_offset=int(slot_offset),
         trace_stride=int(trace_stride), tau_audit=int(tau_audit), meeting_cap=int(meeting_cap),
-        lag=int(lag))
+        lag=int(lag), trace_steps=int(trace_steps), trace_reps=int(trace_reps))
 
 
 def mcpd_inspect(inst, **params):
@@ -301,6 +302,8 @@ class Plan:
         self.horizon, self.k, self.ell, self.L, self.slots = (int(v) for v in info[2:7])
         self.active = np.zeros(self.n_active, np.int32)
         lib().mcpd_plan_active(h, _ptr(self.active))
+        self.trace_steps = int(params.get("trace_steps", 0))
+        self.trace_reps = (int(params.get("trace_reps", 0)) or 8) if self.trace_steps > 0 else 0
 
     def run_async(self, est_dev, se_dev):
         _check_out(est_dev, se_dev, self.n_active, self.ctx.device)
@@ -327,7 +330,7 @@ class Plan:
         dt = {MCPD_FETCH_S1: np.int64, MCPD_FETCH_S2_LO: np.uint64, MCPD_FETCH_S2_HI: np.uint64,
               MCPD_FETCH_COUNT: np.int64, MCPD_FETCH_SLOT_NSTAR: np.int32,
               MCPD_FETCH_SLOT_S: np.int64, MCPD_FETCH_SLOT_REPS: np.int32,
-              MCPD_FETCH_TRACE_G: np.int64}[what]
+              MCPD_FETCH_TRACE_G: np.int64, MCPD_FETCH_TRACE_REC: np.int32}[what]
         nbytes = lib().mcpd_fetch_bytes(self.h, what)
         out = np.zeros(nbytes // np.dtype(dt).itemsize, dtype=dt)
         self.ctx.check(lib().mcpd_fetch(self.ctx.h, self.h, what, _ptr(out), nbytes), "mcpd_fetch")
@@ -335,6 +338,8 @@ class Plan:
             out = out.reshape(self.n_buckets, self.n_active)
         if what == MCPD_FETCH_TRACE_G:
             out = out.reshape(-1, self.n_active)
+        if what == MCPD_FETCH_TRACE_REC:
+            out = out.reshape(-1, self.trace_reps, 4 + self.trace_steps)
         return out
 
     def buckets(self):

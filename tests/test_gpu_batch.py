@@ -297,3 +297,44 @@ def test_batch_systematic_uncoupled(ctx):
         a, b = batch.offsets[i], batch.offsets[i + 1]
         assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"])
     batch.close()
+
+
+@pytest.mark.parametrize("deg", [3, 6])
+@pytest.mark.parametrize("warps", [0, 12, 20])
+def test_uniform_degree_batches(ctx, deg, warps):
+    """Coupled batches whose instances all sit in `deg` pools per clone launch the build with that
+    compile-time degree and mask-indexed thresholds (info[12]); every instance, of its own size,
+    rates, window, random start or scan weights, equals the oracle alone, in the 12-warp build and
+    the 20-warp one."""
+    from paper_2608_30239_gb300 import mcpd
+    insts, ps = [], []
+    rng = np.random.default_rng(deg)
+    for i in range(5):
+        n = 120 + 173 * i
+        inst = synth.make_instance(n, max(deg + 2, n // 13), deg, 1 + i % 3, 0.03 + 0.02 * i, 0.1 + 0.03 * i,
+                                   (1 + i % 3) / n, 60 + i, 70 + i)
+        k, ell = oracle.window_defaults(n, 1)
+        kw = dict(slots=400 + 61 * i, k=k, ell=ell, horizon=3 * ell + 7 * i, seed=90 + i, instance_id=i)
+        if i == 1:
+            kw["init_marginals"] = rng.uniform(0.0, 0.2, n)
+        if i == 3:
+            kw.update(scan=mcpd.MCPD_SCAN_CUSTOM, scan_weights=rng.uniform(0.5, 2.0, n))
+        insts.append(inst)
+        ps.append(kw)
+    batch = mcpd.Batch(ctx, insts, ps, classes=1)
+    if warps:
+        batch.set_shape(warps)
+    assert int(batch.info[12]) == 1
+    est, se, st = _run(ctx, batch)
+    for i, (inst, kw) in enumerate(zip(insts, ps)):
+        M = oracle.Model(inst, scan=kw.get("scan", oracle.SCAN_SCORE), custom_w=kw.get("scan_weights"),
+                         init_marginals=kw.get("init_marginals"))
+        run = oracle.coupled_run(kw["k"], kw["ell"], kw["horizon"], kw["seed"], instance=kw["instance_id"])
+        ref = M.run_slots(run, 0, kw["slots"], THREADS)
+        ref["est"], ref["se"] = M.finalize(ref, kw["slots"], kw["ell"] - kw["k"] + 1)
+        got = batch.buckets(i)
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"]), i
+    batch.close()
