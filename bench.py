@@ -172,14 +172,19 @@ def cpu_oracle_sample(seconds: float, steps_label: str = ""):
             "seconds": dt, "site_updates": site_updates}
 
 
-def batched_leg(ctx, device, slots_per_instance=1024, count=512, sweeps=20, seed=11, cap_sweeps=20):
+def batched_leg(ctx, device, count=512, budget_slots=1024, budget_sweeps=20, seed=11, cap_sweeps=20,
+                slot_candidates=(512, 1024, 2048), uncapped_limit_sweeps=None):
     """The uneven batch: `count` instances with n ~ U[200, 5000], m = round(n / 13), k ~ U{4..8},
-    1-6 positives, fp ~ U[.005, .1], fn ~ U[.02, .25], q = positives / n; each with its own slots
-    and a horizon of `sweeps` sweeps; one persistent launch per size class (automatic classes),
-    launch shape (lanes per pair, warps per block) chosen by the autotuner (cached per GPU and
-    shape).  As in the paper's runs, pairs have a meeting cap of `cap_sweeps` sweeps (a pair unmet
-    there is kept with its correction cut at the cap, and counted): some low-noise instances have
-    meeting times far beyond the horizon."""
+    1-6 positives, fp ~ U[.005, .1], fn ~ U[.02, .25], q = positives / n.  Every instance gets the
+    same budget in its own sweeps: `budget_slots` x `budget_sweeps` x n progress units, split into
+    P slots of horizon budget_slots x budget_sweeps / P sweeps, with P (slots per instance) chosen by
+    the autotuner among `slot_candidates` together with the launch shape (lanes per pair, warps per
+    block; cached per GPU and shape).  One persistent launch per size class (automatic classes),
+    captured in one CUDA graph.  As in the paper's runs, pairs have a meeting cap of `cap_sweeps`
+    sweeps (a pair unmet there is kept with its correction cut at the cap, and counted).  With
+    `uncapped_limit_sweeps` the same batch is also decoded uncapped (the unbiased estimator), with a
+    safety step limit of that many sweeps; its step-limit hits are reported (0 means the result is
+    exactly the unbiased estimator)."""
     import torch
 
     import synth
@@ -188,14 +193,20 @@ def batched_leg(ctx, device, slots_per_instance=1024, count=512, sweeps=20, seed
     ctx = mcpd.Context(device, stream=stream)
     t0 = time.perf_counter()
     insts = synth.batched_configs(count, seed=seed)
-    params = [dict(slots=slots_per_instance, horizon=sweeps * inst.n, seed=5000 + i, instance_id=i,
-                   meeting_cap=cap_sweeps * inst.n) for i, inst in enumerate(insts)]
-    batch = mcpd.Batch(ctx, insts, params, order_mode=1)
+    name = torch.cuda.get_device_name(device)
+
+    def params_for(P, capped=True):
+        sweeps = budget_slots * budget_sweeps / P
+        return [dict(slots=P, horizon=int(round(sweeps * inst.n)), seed=5000 + i, instance_id=i,
+                     **(dict(meeting_cap=cap_sweeps * inst.n) if capped else
+                        dict(step_limit=uncapped_limit_sweeps * inst.n, tau_audit=cap_sweeps * inst.n)))
+                for i, inst in enumerate(insts)]
+
+    with torch.cuda.stream(stream):
+        P, batch, shape, slot_times, cached = autotune.tuned_slots(ctx, insts, params_for, slot_candidates, name)
     t_setup = time.perf_counter() - t0
     est = torch.empty(batch.total_active, dtype=torch.float64, device=f"cuda:{device}")
     se = torch.empty_like(est)
-    name = torch.cuda.get_device_name(device)
-    shape, times, cached = autotune.tuned_shape(batch, est, se, name)
     batch.run_async(est, se)                     # warm-up with the chosen shape
     batch.collect(allow_step_limit=True)
     batch.capture_graph(est, se)
@@ -204,17 +215,29 @@ def batched_leg(ctx, device, slots_per_instance=1024, count=512, sweeps=20, seed
         batch.launch_graph()
         st = batch.collect(allow_step_limit=True)
         ms.append(st["kernel_ms"])
-    out = {"instances": count, "slots_per_instance": slots_per_instance, "horizon_sweeps": sweeps,
-           "clones_total": int(sum(inst.n for inst in insts)), "setup_s": t_setup,
+    out = {"instances": count, "budget_per_instance": f"{budget_slots} x {budget_sweeps} sweeps of its n",
+           "slots_per_instance": P, "horizon_sweeps": budget_slots * budget_sweeps / P,
+           "slots_autotune_ms": {str(k): v for k, v in slot_times.items()}, "autotune_cached": cached,
+           "shape_lanes_warps": list(shape), "clones_total": int(sum(inst.n for inst in insts)),
+           "setup_s": t_setup, "size_classes": batch.classes, "degree_build_classes": int(batch.info[12]),
            "graph_ms": statistics.mean(ms), "site_updates_per_step": st["site_updates"],
            "site_updates_per_s": st["site_updates"] / (statistics.mean(ms) / 1000.0),
            "replications_per_s": st["reps_retained"] / (statistics.mean(ms) / 1000.0),
            "meeting_cap_sweeps": cap_sweeps, "capped_pairs": st["tau_over_audit"],
-           "pairs_attempted": st["reps_started"],
-           "slots_total": count * slots_per_instance,
-           "shape_lanes_warps": list(shape), "autotune_ms": {str(k): v for k, v in times.items()},
-           "autotune_cached": cached}
+           "pairs_attempted": st["reps_started"], "slots_total": count * P}
     batch.close()
+    if uncapped_limit_sweeps:
+        ub = mcpd.Batch(ctx, insts, params_for(P, capped=False), order_mode=1)
+        ub.set_shape(shape[1], shape[0])
+        with torch.cuda.stream(stream):
+            ub.run_async(est, se)
+            ust = ub.collect(allow_step_limit=True)
+        out["uncapped"] = {"step_limit_sweeps": uncapped_limit_sweeps, "kernel_ms": ust["kernel_ms"],
+                           "site_updates_per_s": ust["site_updates"] / (ust["kernel_ms"] / 1000.0),
+                           "step_limit_hits": ust["step_limit_hits"], "status": ust["status"],
+                           "pairs_with_tau_over_cap": ust["tau_over_audit"], "max_tau": ust["max_tau"],
+                           "pairs_attempted": ust["reps_started"]}
+        ub.close()
     stream.synchronize()
     ctx.close()
     return out
@@ -462,7 +485,8 @@ def main():
             "gpu_launches": 2 * args.steps,
             "clocks": clk}
     if rank == 0 and not args.no_batched:
-        line["batched"] = auxiliary_leg(batched_leg, ctx, device)
+        line["batched"] = auxiliary_leg(batched_leg, ctx, device, 512, 1024, 20, 11, 20, (512, 1024, 2048),
+                                        10000)
     if rank == 0 and not args.no_learned:
         line["time_to_se"] = auxiliary_leg(learned_leg, ctx, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

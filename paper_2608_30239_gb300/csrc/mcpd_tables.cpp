@@ -307,9 +307,11 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
         t.step_limit = prm->meeting_cap;
         if (t.tau_audit == 0) t.tau_audit = prm->meeting_cap;
     }
-    // Integer bounds: |G| of one replication <= L (1 + 2 tau); a slot's retained replications
-    // cost at most B + step_limit draws in total.
-    const long double gmax = static_cast<long double>(t.L) * (2.0L * (t.B + t.step_limit) + 1.0L);
+    // Integer bounds on a slot's sum G_p: coupled, |G| of one replication <= L (1 + 2 tau) and a
+    // slot's retained replications cost at most B + step_limit draws in total; uncoupled, each
+    // replication's G lies in [0, T] (T = L) and a slot keeps at most nb of them.
+    const long double gmax = t.coupled ? static_cast<long double>(t.L) * (2.0L * (t.B + t.step_limit) + 1.0L)
+                                       : static_cast<long double>(t.L) * static_cast<long double>(t.nb);
     if (gmax * t.P > 9.0e18L || gmax * gmax * t.P > 3.0e38L)
         return fail(err, "integer sums could overflow for this window, horizon and slot count", MCPD_EOVERFLOW);
     t.slot_offset = prm->slot_offset;

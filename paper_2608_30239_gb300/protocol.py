@@ -67,12 +67,56 @@ def round_half_even(x: float) -> int:
     return int(np.round(x))
 
 
+METHODS = {
+    "SS": dict(coupled=False, scan=mcpd.MCPD_SCAN_SYSTEMATIC),
+    "RU": dict(coupled=False, scan=mcpd.MCPD_SCAN_UNIFORM),
+    "SW": dict(coupled=False, scan=mcpd.MCPD_SCAN_SCORE),
+    "cRU": dict(coupled=True, scan=mcpd.MCPD_SCAN_UNIFORM),
+    "cSW": dict(coupled=True, scan=mcpd.MCPD_SCAN_SCORE),
+    "cSW-nr": dict(coupled=True, scan=mcpd.MCPD_SCAN_SCORE, horizon=0),
+}
+
+
+def cell_params(method, sweeps, n_active, slots, horizon_sweeps=20, cap_sweeps=20, uncapped=False, lag=1):
+    """Decode parameters of one cell (method at an estimator length of `sweeps` sweeps), the
+    paper's recipe (Section "Experimental Setup"; Table S1): M = s n_a, b = round(0.1 M); uncoupled
+    methods discard b updates and average M - b over 2 `slots` chains; coupled methods use k = b + 1,
+    l = M over `slots` pairs with a meeting cap of `cap_sweeps` sweeps (audited, not imposed, when
+    `uncapped`); every slot has a horizon of `horizon_sweeps` sweeps except the no-refill ablation."""
+    kw = dict(METHODS[method])
+    M = sweeps * n_active
+    b = round_half_even(0.1 * M)
+    if kw["coupled"]:
+        cap = cap_sweeps * n_active
+        kw.update(k=b + 1, ell=M, slots=slots, tau_audit=cap, lag=lag)
+        if not uncapped:
+            kw["meeting_cap"] = cap
+    else:
+        kw.update(burn=b, length=M - b, slots=2 * slots)
+    kw.setdefault("horizon", horizon_sweeps * n_active)
+    kw["n_active"] = n_active
+    return kw
+
+
+def top_clones(ref, count=10):
+    """The reference's `count` largest marginals (ties to the lower position)."""
+    return np.argsort(-np.asarray(ref), kind="stable")[:count]
+
+
+def scores(est, ref, top):
+    """(all-clone MAE, top-10 MAE): mean |est - ref| over every retained clone and over `top`."""
+    est, ref = np.asarray(est, float), np.asarray(ref, float)
+    return float(np.mean(np.abs(est - ref))), float(np.mean(np.abs(est[top] - ref[top])))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=1298)
     ap.add_argument("--m", type=int, default=97)
     ap.add_argument("--deg", type=int, default=6)
     ap.add_argument("--positives", type=int, default=3)
+    ap.add_argument("--prior", type=float, default=0.0,
+                    help="prior q (0: positives / n; the paper's synthetic runs use 2.6 / 1298)")
     ap.add_argument("--noise", default="0.10,0.10", help="fn,fp")
     ap.add_argument("--n-active", type=int, default=333)
     ap.add_argument("--sweeps", default="1,3,5,10,20")
@@ -90,7 +134,8 @@ def main(argv=None):
                     help="independent executions per cell (new seeds), summarised as mean and SE")
     a = ap.parse_args(argv)
     fn, fp = (float(v) for v in a.noise.split(","))
-    inst = synth.make_instance(a.n, a.m, a.deg, a.positives, fp, fn, a.positives / a.n, 5007, 9007)
+    q = a.prior if a.prior > 0 else a.positives / a.n
+    inst = synth.make_instance(a.n, a.m, a.deg, a.positives, fp, fn, q, 5007, 9007)
     ctx = mcpd.Context(0)
     t0 = time.perf_counter()
     ref, active, st_ref = _decode(ctx, inst, n_active=a.n_active, coupled=False, scan=mcpd.MCPD_SCAN_SYSTEMATIC,
@@ -98,39 +143,23 @@ def main(argv=None):
                                   horizon=(a.ref_burn + a.ref_sweeps) * a.n_active, slots=a.ref_chains,
                                   seed=a.seed + 1)
     t_ref = time.perf_counter() - t0
-    top = np.argsort(-ref, kind="stable")[:10]
-    horizon = a.horizon_sweeps * a.n_active
-    methods = {
-        "SS": dict(coupled=False, scan=mcpd.MCPD_SCAN_SYSTEMATIC),
-        "RU": dict(coupled=False, scan=mcpd.MCPD_SCAN_UNIFORM),
-        "SW": dict(coupled=False, scan=mcpd.MCPD_SCAN_SCORE),
-        "cRU": dict(coupled=True, scan=mcpd.MCPD_SCAN_UNIFORM),
-        "cSW": dict(coupled=True, scan=mcpd.MCPD_SCAN_SCORE),
-        "cSW-nr": dict(coupled=True, scan=mcpd.MCPD_SCAN_SCORE, horizon=0),
-    }
-    methods = {m: methods[m] for m in a.methods.split(",")}
+    top = top_clones(ref)
+    methods = [m for m in a.methods.split(",")]
     sweeps = [int(v) for v in a.sweeps.split(",")]
     rows = []
     for e in range(a.executions):
         for si, s in enumerate(sweeps):
-            M = s * a.n_active
-            b = round_half_even(0.1 * M)
-            for ci, (name, kw) in enumerate(methods.items()):
-                if kw["coupled"]:
-                    cap = a.cap_sweeps * a.n_active
-                    kw2 = dict(kw, k=b + 1, ell=M, slots=a.slots, tau_audit=cap, lag=a.lag)
-                    if not a.uncapped:
-                        kw2["meeting_cap"] = cap
-                else:
-                    kw2 = dict(kw, burn=b, length=M - b, slots=2 * a.slots)
+            for ci, name in enumerate(methods):
+                kw = METHODS[name]
+                kw2 = cell_params(name, s, a.n_active, a.slots, a.horizon_sweeps, a.cap_sweeps, a.uncapped, a.lag)
                 t1 = time.perf_counter()
-                kw2.setdefault("horizon", horizon)
                 # one seed per (length, method) cell, shifted for each further execution
                 seed = a.seed + 100 * s + si * len(methods) + ci + 1000003 * e
-                est, act, st = _decode(ctx, inst, n_active=a.n_active, seed=seed, **kw2)
+                est, act, st = _decode(ctx, inst, seed=seed, **kw2)
                 assert np.array_equal(act, active)
-                rows.append({"execution": e, "sweeps": s, "method": name, "mae_all": float(np.mean(np.abs(est - ref))),
-                             "mae_top10": float(np.mean(np.abs(est[top] - ref[top]))),
+                mae_all, mae_top = scores(est, ref, top)
+                rows.append({"execution": e, "sweeps": s, "method": name, "mae_all": mae_all,
+                             "mae_top10": mae_top,
                              "site_updates": st["site_updates"], "kernel_ms": st["kernel_ms"],
                              "step_limit_hits": st["step_limit_hits"], "reps_retained": st["reps_retained"],
                              "mean_tau_sweeps": (st["sum_tau"] / max(1, st["reps_retained"]) / a.n_active) if kw["coupled"] else None,
@@ -139,7 +168,8 @@ def main(argv=None):
                              "cap_hits": st["tau_over_audit"] if kw["coupled"] else None,
                              "cap_hit_rate": (st["tau_over_audit"] / max(1, st["reps_started"])) if kw["coupled"] else None,
                              "seconds": time.perf_counter() - t1})
-    out = {"instance": dict(n=a.n, m=a.m, deg=a.deg, positives=a.positives, fn=fn, fp=fp, n_active=a.n_active),
+    out = {"instance": dict(n=a.n, m=a.m, deg=a.deg, positives=a.positives, fn=fn, fp=fp, prior=q,
+                            n_active=a.n_active),
            "reference": dict(burn_sweeps=a.ref_burn, sweeps=a.ref_sweeps, chains=a.ref_chains, seconds=t_ref,
                              site_updates=st_ref["site_updates"], top10=[int(active[i]) for i in top]),
            "slots_coupled": a.slots, "slots_uncoupled": 2 * a.slots, "horizon_sweeps": a.horizon_sweeps,

@@ -338,3 +338,17 @@ def test_lag_sets_the_smallest_replication_cost(L):
     assert mcpd.mcpd_inspect(inst, lag=1, **base)["info"][1] == 400 // 20
     assert mcpd.mcpd_inspect(inst, lag=0, **base)["info"][1] == 400 // 20
     assert mcpd.mcpd_inspect(inst, lag=50, **base)["info"][1] == 400 // 50
+
+
+def test_integer_sum_bounds(L):
+    """The sums' overflow guard: an uncoupled run keeps at most nb replications of G in [0, T] per
+    slot, so the paper's long-run reference (2,000,000 chains, 1000 + 10,000 sweeps of 333 clones)
+    is accepted; a coupled run whose per-slot bound L (2 (B + step limit) + 1) times the slots
+    passes 9e18 is refused."""
+    inst = synth.tiny_config(1)
+    ok = mcpd.mcpd_inspect(inst, coupled=False, scan=mcpd.MCPD_SCAN_SYSTEMATIC, slots=2_000_000,
+                           burn=333_000, length=3_330_000, horizon=3_663_000)
+    assert int(ok["info"][1]) == 1
+    with pytest.raises(mcpd.McpdError) as ei:
+        mcpd.mcpd_inspect(inst, slots=1 << 31, k=0, ell=20000, horizon=1 << 30)
+    assert ei.value.code == mcpd.MCPD_EOVERFLOW

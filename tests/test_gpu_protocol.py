@@ -35,3 +35,36 @@ def test_protocol_small():
             assert r["reps_retained"] == 2048
         elif r["method"] == "cSW":
             assert r["reps_retained"] > 2048
+
+
+@pytest.mark.parametrize("method", ["cSW", "SS", "cRU", "SW", "cSW-nr"])
+def test_protocol_cell_equals_the_oracle(method):
+    """One cell of the comparison (estimator length 1 sweep, the paper's instance shape: 3 pools
+    per clone, q = 2.6 / n, pruned) decoded by the program's own path gives, bit for bit, the
+    estimate vector of the CPU oracle run with the same cell parameters, and so the same scores."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import os
+
+    import oracle
+    import synth
+    from paper_2608_30239_gb300 import build, mcpd, protocol
+    build.build()
+    inst = synth.make_instance(260, 20, 3, 3, 0.10, 0.10, 2.6 / 260, 5007, 9007)
+    kw = protocol.cell_params(method, 1, 90, 512)
+    ctx = mcpd.Context(0)
+    est, active, st = protocol._decode(ctx, inst, seed=77, **kw)
+    ctx.close()
+    scan = {mcpd.MCPD_SCAN_SCORE: oracle.SCAN_SCORE, mcpd.MCPD_SCAN_UNIFORM: oracle.SCAN_UNIFORM,
+            mcpd.MCPD_SCAN_SYSTEMATIC: oracle.SCAN_SYSTEMATIC}[kw["scan"]]
+    if kw["coupled"]:
+        ref = oracle.decode(inst, kw["slots"], kw["k"], kw["ell"], kw["horizon"], seed=77, threads=os.cpu_count(),
+                            n_active=90, scan=scan, meeting_cap=kw.get("meeting_cap", 0))
+    else:
+        ref = oracle.decode(inst, kw["slots"], 0, 0, kw["horizon"], seed=77, threads=os.cpu_count(), n_active=90,
+                            scan=scan, coupled=False, burn=kw["burn"], length=kw["length"])
+    assert np.array_equal(est, ref["est"])
+    other = np.linspace(0.0, 0.5, len(est))
+    top = protocol.top_clones(other)
+    assert protocol.scores(est, other, top) == protocol.scores(ref["est"], other, top)

@@ -44,3 +44,35 @@ def test_protocol_windows_follow_table_s1():
                 assert round_half_even(0.1 * M) == b and M - round_half_even(0.1 * M) == mb, (n_a, s)
                 checked += 1
     assert checked == 15
+
+
+def test_scores_and_top_clones_on_hand_values():
+    """All-clone MAE and top-10 MAE are plain means of absolute errors, over every clone and over the
+    reference's largest marginals (ties to the lower position)."""
+    from paper_2608_30239_gb300.protocol import scores, top_clones
+    ref = np.array([0.0, 0.5, 0.4, 0.5, 0.1])
+    est = np.array([0.1, 0.5, 0.2, 0.3, 0.1])
+    top = top_clones(ref, 3)
+    assert list(top) == [1, 3, 2]
+    mae_all, mae_top = scores(est, ref, top)
+    assert math.isclose(mae_all, (0.1 + 0.0 + 0.2 + 0.2 + 0.0) / 5)
+    assert math.isclose(mae_top, (0.0 + 0.2 + 0.2) / 3)
+
+
+def test_cell_parameters_follow_the_experimental_setup():
+    """At n_a = 333 and s = 5: M = 1665 and b = 166 (Table S1); coupled k = b + 1 = 167, l = M, a
+    20-sweep horizon and meeting cap; uncoupled b = 166, T = M - b = 1499 over twice the slots; the
+    no-refill ablation has a horizon of zero; an uncapped run audits the cap without imposing it."""
+    from paper_2608_30239_gb300 import mcpd
+    from paper_2608_30239_gb300.protocol import cell_params
+    c = cell_params("cSW", 5, 333, 1000)
+    assert (c["k"], c["ell"], c["slots"], c["horizon"], c["meeting_cap"], c["tau_audit"]) == \
+        (167, 1665, 1000, 20 * 333, 20 * 333, 20 * 333)
+    assert c["coupled"] and c["scan"] == mcpd.MCPD_SCAN_SCORE and c["lag"] == 1 and c["n_active"] == 333
+    u = cell_params("SS", 5, 333, 1000)
+    assert (u["burn"], u["length"], u["slots"], u["horizon"]) == (166, 1499, 2000, 20 * 333)
+    assert not u["coupled"] and u["scan"] == mcpd.MCPD_SCAN_SYSTEMATIC
+    assert cell_params("cSW-nr", 1, 333, 1000)["horizon"] == 0
+    assert cell_params("cRU", 1, 333, 1000)["scan"] == mcpd.MCPD_SCAN_UNIFORM
+    assert "meeting_cap" not in cell_params("cSW", 1, 333, 1000, uncapped=True)
+    assert cell_params("SW", 1, 333, 1000)["scan"] == mcpd.MCPD_SCAN_SCORE
