@@ -1,7 +1,11 @@
 """The five-method comparison on a synthetic instance (the protocol of the paper's experiments,
 Section "Experimental Setup", on a generated stand-in for its unpublished instance).
 
-  python -m paper_2608_30239_gb300.protocol [--noise 0.10,0.10] [--sweeps 1,3,5,10,20] [--slots 65536]
+  python -m paper_2608_30239_gb300.protocol [--noise 0.10,0.10] [--sweeps 1,3,5,10,20] [--slots 1000000]
+
+Defaults follow the paper's synthetic instance: 1298 clones x 97 pools, 3 pools per clone, three
+true positives, prior q = 2.6 / n, pruned to 333 clones; 1,000,000 coupled slots, 2,000,000
+uncoupled chains, a 2,000,000-chain reference.
 
 Methods, at an estimator length of s sweeps (M = s n_a single-site updates, b = round(0.1 M)):
   SS   systematic scan, uncoupled: discard b updates, average the next M - b (Algorithm 1);
@@ -113,18 +117,18 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=1298)
     ap.add_argument("--m", type=int, default=97)
-    ap.add_argument("--deg", type=int, default=6)
+    ap.add_argument("--deg", type=int, default=3, help="pools per clone (the paper's synthetic instance: 3)")
     ap.add_argument("--positives", type=int, default=3)
-    ap.add_argument("--prior", type=float, default=0.0,
-                    help="prior q (0: positives / n; the paper's synthetic runs use 2.6 / 1298)")
+    ap.add_argument("--prior", type=float, default=-1.0,
+                    help="prior q (default 2.6 / n, the paper's synthetic runs; 0: positives / n)")
     ap.add_argument("--noise", default="0.10,0.10", help="fn,fp")
     ap.add_argument("--n-active", type=int, default=333)
     ap.add_argument("--sweeps", default="1,3,5,10,20")
     ap.add_argument("--horizon-sweeps", type=int, default=20)
-    ap.add_argument("--slots", type=int, default=65536, help="coupled slots (uncoupled: twice as many)")
+    ap.add_argument("--slots", type=int, default=1000000, help="coupled slots (uncoupled: twice as many)")
     ap.add_argument("--ref-burn", type=int, default=1000, help="reference burn-in, sweeps")
     ap.add_argument("--ref-sweeps", type=int, default=10000, help="reference sampling length, sweeps")
-    ap.add_argument("--ref-chains", type=int, default=65536)
+    ap.add_argument("--ref-chains", type=int, default=2000000)
     ap.add_argument("--seed", type=int, default=20260)
     ap.add_argument("--cap-sweeps", type=int, default=20, help="meeting cap, sweeps")
     ap.add_argument("--uncapped", action="store_true", help="audit the cap without imposing it")
@@ -134,7 +138,7 @@ def main(argv=None):
                     help="independent executions per cell (new seeds), summarised as mean and SE")
     a = ap.parse_args(argv)
     fn, fp = (float(v) for v in a.noise.split(","))
-    q = a.prior if a.prior > 0 else a.positives / a.n
+    q = a.prior if a.prior > 0 else (2.6 / a.n if a.prior < 0 else a.positives / a.n)
     inst = synth.make_instance(a.n, a.m, a.deg, a.positives, fp, fn, q, 5007, 9007)
     ctx = mcpd.Context(0)
     t0 = time.perf_counter()
