@@ -261,6 +261,17 @@ int mcpd_batch_set_shape(mcpd_ctx *ctx, mcpd_batch *batch, int32_t lanes_per_pai
                          int32_t warps_per_block);
 /* Enqueue one decode of every instance; est_dev, se_dev: device arrays [info[0]]. */
 int mcpd_batch_run_async(mcpd_ctx *ctx, mcpd_batch *batch, double *est_dev, double *se_dev);
+/* Extend the last decode of the batch, as mcpd_run_slots_async does for a plan: every instance i
+ * with mask[i] != 0 (all if mask is NULL) runs its next P_i slots, the global slot ids after
+ * those already in its N*_p buckets, and adds their sums; est_dev / se_dev receive every
+ * instance's theta_CT and standard error over all slots in its buckets (an instance not extended
+ * keeps its estimate).  For each instance the result is bit-identical to one decode over that
+ * many slots with the same horizon.  Needs a previous mcpd_batch_run_async or
+ * mcpd_batch_launch_graph (which start every instance again from its first slot).  Slots per
+ * instance stay <= 2^31 and global slot ids < 2^32.  Asynchronous; mcpd_batch_collect reads this
+ * extension's counters and kernel time. */
+int mcpd_batch_extend_async(mcpd_ctx *ctx, mcpd_batch *batch, const int32_t *mask, double *est_dev,
+                            double *se_dev);
 /* Capture one decode (scratch clears, sampling kernel, finalize) into a CUDA graph on the
  * context's stream (which must not be the legacy default stream); replay it with
  * mcpd_batch_launch_graph. */

@@ -473,7 +473,10 @@ struct mcpd_batch {
     int32_t n_inst = 0, lanes = 1;
     bool coupled = true;
     mcpd::InstDesc *d_insts = nullptr;
-    std::vector<mcpd::InstDesc> insts;     // in launch order
+    std::vector<mcpd::InstDesc> insts;     // in launch order, as the device holds them
+    std::vector<mcpd::InstDesc> insts0;    // the descriptors of a decode from the first slot
+    std::vector<long long> total_work0;    // per class, for those
+    bool extended = false;                 // the device descriptors describe an extension
     int32_t *d_clone_inst = nullptr, *d_clone_local = nullptr;
     unsigned long long *d_buckets = nullptr;   // S1 | S2lo | S2hi, each total_bucket_words
     unsigned long long *d_bcount = nullptr;
@@ -565,10 +568,24 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
     return MCPD_OK;
 }
 
-int batch_enqueue(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev, bool always_clear) {
+// Put back the descriptors of a decode from each instance's first slot after an extension.
+int restore_descriptors(mcpd_ctx *ctx, mcpd_batch *b) {
+    if (!b->extended) return MCPD_OK;
+    b->insts = b->insts0;
+    for (size_t c = 0; c < b->cls.size(); ++c) b->cls[c].bp.total_work = b->total_work0[c];
+    CU(cudaMemcpyAsync(b->d_insts, b->insts.data(), sizeof(mcpd::InstDesc) * b->insts.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    b->extended = false;
+    return MCPD_OK;
+}
+
+int batch_enqueue(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev, bool always_clear,
+                  bool accumulate = false) {
     const cudaStream_t s = ctx->stream;
-    CU(cudaMemsetAsync(b->d_buckets, 0, b->total_bucket_words * 3 * 8, s));
-    CU(cudaMemsetAsync(b->d_bcount, 0, b->total_counts * 8, s));
+    if (!accumulate) {
+        CU(cudaMemsetAsync(b->d_buckets, 0, b->total_bucket_words * 3 * 8, s));
+        CU(cudaMemsetAsync(b->d_bcount, 0, b->total_counts * 8, s));
+    }
     CU(cudaMemsetAsync(b->d_counters, 0, b->cls.size() * mcpd::kNumCounters * 8, s));
     CU(cudaMemsetAsync(b->d_error, 0, sizeof(int), s));
     for (BatchClass &c : b->cls) {
@@ -577,6 +594,7 @@ int batch_enqueue(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev,
                                static_cast<size_t>(c.pairs) * mcpd::pair_words(c.bp.max_na, c.bp.max_W) * 8, s));
             CU(cudaMemsetAsync(c.bp.y_state, 0, static_cast<size_t>(c.pairs) * c.bp.max_wpp * 4, s));
         }
+        if (c.bp.total_work == 0) continue;              // an extension with no instance of this class
         if ((c.bp.lanes == 1 ? mcpd::launch_batch(c.bp, c.grid, c.block, c.smem, s)
                              : mcpd::launch_group(c.bp, c.grid, c.block, c.smem, s)) != MCPD_OK)
             return set_err(ctx, MCPD_ECUDA, std::string("batch kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
@@ -751,6 +769,7 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         d.capped = t.capped ? 1 : 0;
         d.lag = static_cast<int32_t>(t.lag);
         d.work_begin = work; work += t.P;
+        d.P_total = t.P;
         d.seed = t.seed; d.instance = t.instance;
         mcpd::BParams &bp = c.bp;
         bp.total_work = work;
@@ -779,6 +798,8 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     }
     CU_OR(cudaMemcpyAsync(d_tables, host.data(), table_bytes, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
     CU_OR(cudaMemcpyAsync(b->d_insts, b->insts.data(), sizeof(mcpd::InstDesc) * n_inst, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
+    b->insts0 = b->insts;
+    for (const BatchClass &c : b->cls) b->total_work0.push_back(c.bp.total_work);
     CU_OR(cudaMemcpyAsync(b->d_clone_inst, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
     CU_OR(cudaMemcpyAsync(b->d_clone_local, cl.data(), cl.size() * 4, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
     if ((rc = batch_shape(ctx, b, 0)) != MCPD_OK) { mcpd_batch_destroy(b); return rc; }
@@ -825,12 +846,51 @@ int mcpd_batch_run_async(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *
     NvtxRange nvtx_range("mcpd.batch_run");
     if (!ctx || !b || !est_dev || !se_dev) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
+    int rc = restore_descriptors(ctx, b);
+    if (rc != MCPD_OK) return rc;
     CU(cudaEventRecord(b->ev0, ctx->stream));
-    const int rc = batch_enqueue(ctx, b, est_dev, se_dev, false);
+    rc = batch_enqueue(ctx, b, est_dev, se_dev, false);
     if (rc != MCPD_OK) return rc;
     CU(cudaEventRecord(b->ev1, ctx->stream));
     b->dirty = true;
     b->ran = true;
+    return MCPD_OK;
+}
+
+int mcpd_batch_extend_async(mcpd_ctx *ctx, mcpd_batch *b, const int32_t *mask, double *est_dev, double *se_dev) {
+    NvtxRange nvtx_range("mcpd.batch_extend");
+    if (!ctx || !b || !est_dev || !se_dev) return MCPD_EINVAL;
+    if (!b->ran) return set_err(ctx, MCPD_EINVAL, "nothing to extend: run the batch first");
+    CU(cudaSetDevice(ctx->device));
+    // Each chosen instance runs its next P_i slots (the next global ids after those in its
+    // buckets); the others run none.  Work items are renumbered per class.
+    size_t pos = 0;
+    for (BatchClass &c : b->cls) {
+        long long work = 0;
+        for (int32_t k = 0; k < c.count; ++k, ++pos) {
+            mcpd::InstDesc &d = b->insts[pos];
+            const mcpd::Tables &t = b->t[b->order[pos]];
+            const bool go = !mask || mask[b->order[pos]] != 0;
+            if (go && (d.P_total + t.P > (int64_t(1) << 31) || t.slot_offset + d.P_total + t.P > (int64_t(1) << 32)))
+                return set_err(ctx, MCPD_EINVAL, "extension beyond 2^31 slots or 32-bit global slot ids");
+            d.work_begin = work;
+            d.P = go ? t.P : 0;
+            if (go) {
+                d.slot_offset = t.slot_offset + d.P_total;
+                d.P_total += t.P;
+                work += t.P;
+            }
+        }
+        c.bp.total_work = work;
+    }
+    b->extended = true;
+    CU(cudaMemcpyAsync(b->d_insts, b->insts.data(), sizeof(mcpd::InstDesc) * b->insts.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    CU(cudaEventRecord(b->ev0, ctx->stream));
+    const int rc = batch_enqueue(ctx, b, est_dev, se_dev, false, true);
+    if (rc != MCPD_OK) return rc;
+    CU(cudaEventRecord(b->ev1, ctx->stream));
+    b->dirty = true;
     return MCPD_OK;
 }
 
@@ -839,6 +899,10 @@ int mcpd_batch_capture_graph(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, doub
     if (!ctx || !b || !est_dev || !se_dev) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
     if (!ctx->stream) return set_err(ctx, MCPD_EINVAL, "graph capture needs a non-default stream");
+    {
+        const int r = restore_descriptors(ctx, b);
+        if (r != MCPD_OK) return r;
+    }
     if (b->graph_exec) { cudaGraphExecDestroy(b->graph_exec); b->graph_exec = nullptr; }
     if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
     CU(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
@@ -856,6 +920,10 @@ int mcpd_batch_launch_graph(mcpd_ctx *ctx, mcpd_batch *b) {
     NvtxRange nvtx_range("mcpd.batch_launch_graph");
     if (!ctx || !b || !b->graph_exec) return MCPD_EINVAL;
     CU(cudaSetDevice(ctx->device));
+    {
+        const int r = restore_descriptors(ctx, b);
+        if (r != MCPD_OK) return r;
+    }
     CU(cudaEventRecord(b->ev0, ctx->stream));
     CU(cudaGraphLaunch(b->graph_exec, ctx->stream));
     CU(cudaEventRecord(b->ev1, ctx->stream));

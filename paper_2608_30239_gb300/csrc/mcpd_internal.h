@@ -175,6 +175,7 @@ struct InstDesc {
     uint32_t dummy_entry, dummy_word;
     long long P, B, k, ell, L, burn, length, unit, step_limit, slot_offset, tau_audit;
     long long work_begin;             // global index of this instance's first slot in the launch
+    long long P_total;                // slots in this instance's buckets (the finalize's P)
     unsigned long long seed;
     uint32_t instance;
     int32_t lag;                      // coupled lag L >= 1

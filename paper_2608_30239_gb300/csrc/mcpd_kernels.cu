@@ -62,7 +62,7 @@ __global__ void finalize_batch_kernel(const InstDesc *insts, const int32_t *clon
     const long long g = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (g >= total) return;
     const InstDesc &d = insts[clone_inst[g]];
-    finalize_one(d.S1, d.S2lo, d.S2hi, d.na, d.nb, d.P, d.L, clone_local[g], &est[g], &se[g]);
+    finalize_one(d.S1, d.S2lo, d.S2hi, d.na, d.nb, d.P_total, d.L, clone_local[g], &est[g], &se[g]);
 }
 
 __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out, long long n) {

@@ -285,5 +285,49 @@ def time_to_se(ctx, inst, target=0.005, sweeps=29.4, seed=7, weights=None, init=
                 met=mse <= target, ranges=len(path), mean_tau=mean_tau_num / max(1, mean_tau_den))
 
 
+def batched_time_to_se(ctx, instances, target=0.005, sweeps=29.4, seed=7, weights=None, init=None,
+                       chunk_slots=131072, max_slots=1 << 26):
+    """Measured time for a batch of instances to bring every instance's largest per-clone SE to
+    `target`, decoded together: one batched decode with `chunk_slots` slots per instance (horizon
+    `sweeps` sweeps of each instance's n), then extensions (mcpd_batch_extend_async) in which
+    every instance not yet at the target runs its next `chunk_slots` slots, until all are there.
+    Each instance's estimate is the same estimator over all its slots.  Returns the summed
+    sampling-kernel time of the decode and its extensions, the wall time from batch creation
+    through the last SE copy, the slots each instance used and its final largest SE."""
+    import torch
+    t0 = time.perf_counter()
+    seg = segments(instances)
+    params = []
+    for i, inst in enumerate(instances):
+        kw = dict(slots=chunk_slots, horizon=int(sweeps * inst.n), seed=seed + i, instance_id=i)
+        if weights is not None:
+            kw.update(scan=mcpd.MCPD_SCAN_CUSTOM, scan_weights=weights[seg[i]:seg[i + 1]])
+        if init is not None:
+            kw.update(init_marginals=init[seg[i]:seg[i + 1]])
+        params.append(kw)
+    b = mcpd.Batch(ctx, instances, params)
+    est = torch.empty(b.total_active, dtype=torch.float64, device=f"cuda:{ctx.device}")
+    se = torch.empty_like(est)
+    off = b.offsets
+    slots = np.full(len(instances), chunk_slots, np.int64)
+    b.run_async(est, se)
+    kernel_ms = b.collect()["kernel_ms"]
+    rounds = 1
+    while True:
+        s = se.cpu().numpy()
+        worst = np.array([s[off[i]:off[i + 1]].max() for i in range(len(instances))])
+        todo = (worst > target).astype(np.int32)
+        if not todo.any() or slots.max() + chunk_slots > max_slots:
+            break
+        b.extend_async(est, se, todo)
+        kernel_ms += b.collect()["kernel_ms"]
+        slots += chunk_slots * todo
+        rounds += 1
+    wall_ms = 1000.0 * (time.perf_counter() - t0)
+    b.close()
+    return dict(kernel_ms=kernel_ms, wall_ms=wall_ms, slots=slots.tolist(), max_se=worst.tolist(),
+                met=bool((worst <= target).all()), launches=rounds)
+
+
 def now() -> float:
     return time.perf_counter()

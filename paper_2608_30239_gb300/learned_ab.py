@@ -16,6 +16,8 @@
 4. With --direct, measure time-to-SE on the bench instance and the first `--direct-held` held-out
    instances: one decode per variant extended slot range by slot range until its largest SE is
    <= 0.005 (learned.time_to_se), reporting the summed kernel time and the wall time.
+5. With --batched N, measure the batched form: the first N held-out instances decoded as one
+   batch, extended until every instance's largest SE is <= 0.005 (learned.batched_time_to_se).
 Prints one JSON line.
 """
 from __future__ import annotations
@@ -45,6 +47,9 @@ def main(argv=None):
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--direct", action="store_true", help="also measure time-to-SE directly")
     ap.add_argument("--direct-held", type=int, default=4, help="held-out instances measured directly")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="also measure the time for this many held-out instances, decoded as one batch, "
+                         "to all reach SE <= 0.005 (learned.batched_time_to_se)")
     a = ap.parse_args(argv)
     ctx = mcpd.Context(0)
     rng = np.random.default_rng(0)
@@ -104,6 +109,18 @@ def main(argv=None):
             for v in arms.values():
                 v["speedup_vs_paper"] = base / v["kernel_ms"]
             out["direct"][label] = arms
+    if a.batched:
+        sub = held[:a.batched]
+        hs = learned.segments(sub)
+        wb, nub = learned.learned_inputs(model, learned.features(ctx, sub), hs, nu_floor=a.nu_floor)
+        arms = {}
+        for name, kw in (("paper_weights_allneg", {}), ("paper_weights_learned_nu", dict(init=nub)),
+                         ("learned_w_learned_nu", dict(weights=wb, init=nub))):
+            arms[name] = learned.batched_time_to_se(ctx, sub, 0.005, 29.4, seed=7, **kw)
+        base = arms["paper_weights_allneg"]["kernel_ms"]
+        for v in arms.values():
+            v["speedup_vs_paper"] = base / v["kernel_ms"]
+        out["batched"] = {"instances": a.batched, "arms": arms}
     print(json.dumps(out), flush=True)
     ctx.close()
     return out

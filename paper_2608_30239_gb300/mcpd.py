@@ -110,6 +110,7 @@ def lib(build_if_missing: bool = False):
             "mcpd_batch_capture_graph": (C.c_int, [P, P, P, P]),
             "mcpd_batch_launch_graph": (C.c_int, [P, P]),
             "mcpd_batch_collect": (C.c_int, [P, P, C.POINTER(mcpd_stats)]),
+            "mcpd_batch_extend_async": (C.c_int, [P, P, P, P, P]),
             "mcpd_batch_fetch": (C.c_int, [P, P, C.c_int32, C.c_int, P, C.c_size_t]),
             "mcpd_batch_autotune": (C.c_int, [P, P, P, P, C.c_int32, C.c_int32, P, P, P, P]),
         }
@@ -408,6 +409,16 @@ class Batch:
         _check_out(est_dev, se_dev, self.total_active, self.ctx.device)
         self.ctx.check(lib().mcpd_batch_run_async(self.ctx.h, self.h, _ptr(est_dev), _ptr(se_dev)),
                        "mcpd_batch_run_async")
+
+    def extend_async(self, est_dev, se_dev, mask=None):
+        """mcpd_batch_extend_async: every instance (or those with mask[i]) runs its next P_i slots
+        into the same buckets; est/se are finalized over all slots so far."""
+        _check_out(est_dev, se_dev, self.total_active, self.ctx.device)
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.int32)
+        if m is not None and len(m) != self.n_inst:
+            raise ValueError("mask needs one entry per instance")
+        self.ctx.check(lib().mcpd_batch_extend_async(self.ctx.h, self.h, _ptr(m), _ptr(est_dev), _ptr(se_dev)),
+                       "mcpd_batch_extend_async")
 
     def capture_graph(self, est_dev, se_dev):
         _check_out(est_dev, se_dev, self.total_active, self.ctx.device)

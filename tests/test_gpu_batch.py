@@ -338,3 +338,43 @@ def test_uniform_degree_batches(ctx, deg, warps):
         a, b = batch.offsets[i], batch.offsets[i + 1]
         assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"]), i
     batch.close()
+
+
+def test_batch_extension_by_slot_ranges(ctx):
+    """mcpd_batch_extend_async: every instance (or the masked ones) runs its next P_i slots into the
+    same buckets; each instance then equals the oracle over all its slots, an instance left out
+    keeps its estimate, and a later run or graph launch starts again from the first slot."""
+    from paper_2608_30239_gb300 import mcpd
+    insts = _uneven(6, seed=9)
+    ps = _params(insts)
+    batch = mcpd.Batch(ctx, insts, ps, classes=2)
+    e0, s0, _ = _run(ctx, batch)
+    import torch
+    est = torch.empty(batch.total_active, dtype=torch.float64, device="cuda:0")
+    se = torch.empty_like(est)
+    mask = np.array([1, 0, 1, 1, 0, 1], np.int32)
+    ranges = np.ones(len(insts), np.int64)
+    with torch.cuda.stream(ctx.torch_stream):
+        for m in (None, mask):
+            batch.extend_async(est, se, m)
+            batch.collect()
+            ranges += 1 if m is None else m
+    got_e, got_s = est.cpu().numpy(), se.cpu().numpy()
+    for i, (inst, kw) in enumerate(zip(insts, ps)):
+        total = kw["slots"] * int(ranges[i])
+        ref = _oracle(inst, dict(kw, slots=total))
+        got = batch.buckets(i)
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(got_e[a:b], ref["est"]) and np.array_equal(got_s[a:b], ref["se"]), i
+    e1, s1, _ = _run(ctx, batch)                     # a plain run starts from the first slot again
+    assert np.array_equal(e1, e0) and np.array_equal(s1, s0)
+    with torch.cuda.stream(ctx.torch_stream):
+        batch.extend_async(est, se)
+        batch.collect()
+        batch.capture_graph(est, se)                  # capture and launch restore the first range
+        batch.launch_graph()
+        batch.collect()
+    assert np.array_equal(est.cpu().numpy(), e0)
+    batch.close()
