@@ -498,3 +498,54 @@ def test_full_size_partition_and_determinism(ctx, full_run):
     again = _gpu_run(ctx, inst, slots=P_FULL, budget_site_updates=BUDGET, seed=20260)
     assert np.array_equal(again["S1"], g["S1"])
     assert np.array_equal(again["est"], g["est"])
+
+
+# -------------------------------------------------------------------------------------------
+# The other workload configurations at their full sizes.
+def test_tiny_workload_against_the_exact_posterior(ctx):
+    """The tiny workload (20 clones x 8 pools, 3 pools per clone, 2 positives, fp .02, fn .05,
+    q .01; 4096 lag-1 pairs with the paper's score weights, each run to meeting, k = 3, l = 20):
+    bit-exact with the oracle, and within sampling error of the exact posterior marginals of the
+    2^20 enumeration (z < 4.5 for every clone)."""
+    from oracle import exact
+    inst = synth.tiny_config(1)
+    P = 4096
+    g = _gpu_run(ctx, inst, slots=P, k=3, ell=20, horizon=0, seed=2026, record_slots=True)
+    o = _oracle_run(inst, P, 3, 20, 0, 2026)
+    _assert_same(g, o)
+    _, p = exact.posterior(inst)
+    z = np.abs(g["est"] - p) / np.where(g["se"] > 0, g["se"], np.inf)
+    assert np.all(z < 4.5), z
+    assert np.all(g["est"][g["se"] == 0] == 0.0)        # a clone never positive in any chain
+
+
+@pytest.mark.parametrize("method", ["coupled-score", "uncoupled-systematic"])
+def test_library_workload_full_size_sampled_slots(ctx, method):
+    """The paper-shaped library workload (1298 x 97, 6 pools per clone, 3 positives, fp .01, fn .05,
+    q = 3/1298) at its full size, 262,144 slots and a budget of 1e10 site updates, in both of its
+    methods: coupled score-weighted pairs (B = 19073 progress units per slot, one-sweep window) and
+    uncoupled systematic scan (B = 38146 draws per slot, b = 130, T = 1168).  Twelve slots spread
+    over the run are recomputed one by one by the oracle (N*_p, retained cost, G vector)."""
+    inst = synth.paper_shaped_config()
+    P, budget = 262144, 1e10
+    stride = P // 11 + 1
+    k, ell = oracle.window_defaults(inst.n, 1)
+    if method == "coupled-score":
+        g = _gpu_run(ctx, inst, slots=P, budget_site_updates=budget, seed=4242, record_slots=True,
+                     trace_stride=stride)
+        B = synth.budget_horizon(budget, P)
+        run = lambda p: oracle.coupled_run(k, ell, B, 4242, slot_offset=p)          # noqa: E731
+        M = oracle.Model(inst)
+    else:
+        b = k - 1
+        g = _gpu_run(ctx, inst, slots=P, budget_site_updates=budget, seed=4243, coupled=False,
+                     scan=2, burn=b, length=ell - b, record_slots=True, trace_stride=stride)
+        B = int(budget // P)
+        run = lambda p: oracle.uncoupled_run(b, ell - b, B, 4243, slot_offset=p)    # noqa: E731
+        M = oracle.Model(inst, scan=oracle.SCAN_SYSTEMATIC)
+    assert g["stats"]["status"] == 0 and int(g["count"].sum()) == P
+    for idx, p in enumerate(range(0, P, stride)):
+        r = M.run_slots(run(p), 0, 1, 1, per_slot=True, slot_G=True)
+        assert g["slot_nstar"][p] == r["slot_nstar"][0], p
+        assert g["slot_S"][p] == r["slot_S"][0], p
+        assert np.array_equal(g["trace_G"][idx], r["slot_G"][0]), p
