@@ -105,7 +105,7 @@ typedef struct mcpd_params {
                                   tau = inf{t >= L : X_t = Y_{t-L}} and
                                   H_r = X_r + sum_{j>=1} (X_{r+jL} - Y_{r+(j-1)L}).  Every
                                   replication costs max(l, tau) >= max(l, L).  At most 2^20      */
-    int64_t trace_steps;       /* > 0 (coupled, trace_stride > 0): also record, for the first
+    int64_t trace_steps;       /* > 0 (trace_stride > 0): also record, for the first
                                   trace_reps replications of every traced slot, the meeting time,
                                   the completion time and, for the first trace_steps draws, the
                                   site and which chains flipped (MCPD_FETCH_TRACE_REC).  Runs that
@@ -197,13 +197,14 @@ int mcpd_collect(mcpd_ctx *ctx, mcpd_plan *plan, mcpd_stats *stats);
 #define MCPD_FETCH_TRACE_G 7   /* int64  [ceil(slots/stride)][n_active] (trace_stride > 0)          */
 #define MCPD_FETCH_TRACE_REC 8 /* int32  [ceil(slots/stride)][trace_reps][4 + trace_steps]
                                   (trace_steps > 0): per replication r of traced slot p: [0] its
-                                  meeting time tau (0: stopped unmet at the meeting cap), [1] its
+                                  meeting time tau (0: stopped unmet at the meeting cap, or an
+                                  uncoupled chain), [1] its
                                   completion time C (or the clock when it was stopped), [2] 1
                                   completed, 2 stopped as doomed (Algorithm 4: it could not finish
                                   within the horizon), 3 step limit, 0 not started; [3] r; then for
                                   draw t < min(C, trace_steps): the site I_t | X flipped << 16 |
                                   Y flipped << 17 (the chain that draw t moves: X_{t+1} and, from
-                                  t = L on, Y_{t+1-L})                                           */
+                                  t = L on, Y_{t+1-L}; an uncoupled run has X only)              */
 size_t mcpd_fetch_bytes(const mcpd_plan *plan, int what);
 int mcpd_fetch(mcpd_ctx *ctx, const mcpd_plan *plan, int what, void *host_dst, size_t bytes);
 

@@ -45,9 +45,9 @@ namespace {
 // for size classes whose pair state leaves room for more than 12 warps.
 // EXT: the meeting cap and lags L > 1 (runs that use neither launch the variant without them, whose
 // hot loop the completion path's code would otherwise perturb).
-// TRACE (single instance, coupled): also record the first replications of every traced slot (meeting
-// time, completion time, and per draw the site and which chains flipped; MCPD_FETCH_TRACE_REC),
-// for the trajectory parity tests.  The production variants compile none of it.
+// TRACE (single instance): also record the first replications of every traced slot (meeting time,
+// completion time, and per draw the site and which chains flipped; MCPD_FETCH_TRACE_REC), for the
+// trajectory parity tests.  The production variants compile none of it.
 template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG, bool WIDE = false, bool EXT = false, bool TRACE = false>
 __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 : 512), 1) pairs_kernel(const KParams p, const BParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -502,7 +502,11 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     // TRACE: the replication's meeting time, its clock at the end and how it ended.
     auto trace_end = [&](int how) {
         if constexpr (TRACE) {
-            if (trec) { trec[0] = static_cast<int32_t>(tau); trec[1] = static_cast<int32_t>(t); trec[2] = how; }
+            if (trec) {
+                trec[0] = COUPLED ? static_cast<int32_t>(tau) : 0;
+                trec[1] = static_cast<int32_t>(t);
+                trec[2] = how;
+            }
         }
     };
     auto complete = [&]() {
@@ -731,7 +735,9 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
             // alike, and before t = L Y stays at Y_0
             if (trec && t < static_cast<uint32_t>(p.trace_steps)) {
                 const uint32_t xf = nX != xI ? 1u : 0u;
-                const uint32_t yf = own ? ((nY != yI && !(EXT && t < v_lag())) ? 1u : 0u) : (xf && t >= v_lag() ? 1u : 0u);
+                const uint32_t yf = !COUPLED ? 0u
+                                    : own ? ((nY != yI && !(EXT && t < v_lag())) ? 1u : 0u)
+                                          : (xf && t >= v_lag() ? 1u : 0u);
                 trec[4 + t] = static_cast<int32_t>(I | (xf << 16) | (yf << 17));
             }
         }

@@ -319,8 +319,8 @@ int build_tables(const mcpd_design *d, const uint8_t *y, const mcpd_params *prm,
     if (prm->trace_steps < 0 || prm->trace_steps > (int64_t(1) << 20) || prm->trace_reps < 0 ||
         prm->trace_reps > 1024)
         return fail(err, "trace_steps must be in [0, 2^20] and trace_reps in [0, 1024]", MCPD_EINVAL);
-    if (prm->trace_steps > 0 && (!t.coupled || t.trace_stride == 0))
-        return fail(err, "trajectory records need a coupled run with trace_stride > 0", MCPD_EINVAL);
+    if (prm->trace_steps > 0 && t.trace_stride == 0)
+        return fail(err, "trajectory records need trace_stride > 0", MCPD_EINVAL);
     t.trace_steps = prm->trace_steps;
     t.trace_reps = prm->trace_steps > 0 ? (prm->trace_reps > 0 ? prm->trace_reps : 8) : 0;
     t.record_slots = prm->record_slots != 0;

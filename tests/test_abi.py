@@ -277,7 +277,6 @@ def test_window_and_horizon_defaults(L, oracle_lib):
     (dict(k=2, ell=20, lag=30, meeting_cap=25), mcpd.MCPD_EINVAL),
     (dict(k=2, ell=20, lag=30, step_limit=29), mcpd.MCPD_EINVAL),
     (dict(trace_steps=16), mcpd.MCPD_EINVAL),                          # no traced slots
-    (dict(trace_steps=16, trace_stride=2, coupled=False), mcpd.MCPD_EINVAL),
     (dict(trace_steps=-1, trace_stride=2), mcpd.MCPD_EINVAL),
     (dict(trace_steps=(1 << 20) + 1, trace_stride=2), mcpd.MCPD_EINVAL),
     (dict(trace_steps=16, trace_stride=2, trace_reps=1025), mcpd.MCPD_EINVAL),

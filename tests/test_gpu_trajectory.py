@@ -90,6 +90,13 @@ CASES = {
     # the largest instances of the batched workload (n = 5000, m = 385, 8 pools per clone)
     "n5000-degree8": (lambda: synth.make_instance(5000, 385, 8, 4, 0.05, 0.15, 4 / 5000, 41, 42),
                       dict(slots=300, k=501, ell=5000, horizon=10000, seed=12), None),
+    # the uncoupled comparators (Algorithms 1 and 2): one chain, sites and flips of X only
+    "uncoupled-systematic": (lambda: synth.make_instance(200, 20, 4, 2, 0.05, 0.1, 2 / 200, 51, 52),
+                             dict(slots=700, coupled=False, scan=2, burn=20, length=180, horizon=700,
+                                  seed=21), None),
+    "uncoupled-score-degree6": (lambda: synth.make_instance(300, 30, 6, 3, 0.10, 0.20, 3 / 300, 71, 72),
+                                dict(slots=700, coupled=False, burn=30, length=270, horizon=900, seed=22),
+                                "random"),
     # a Tapestry-shaped regular design (961 x 93, 3 pools per sample, 31 samples per pool)
     "tapestry-961": (lambda: synth.make_tapestry_like_instance(961, 93, 3, 3, 0.05, 0.10, 3 / 961, 43, 44),
                      dict(slots=800, k=97, ell=961, horizon=2000, seed=13), "random"),
@@ -108,9 +115,14 @@ def test_trajectories_match_the_oracle(ctx, case):
     for key in ("S1", "S2_lo", "S2_hi", "count"):          # recording changes no result
         assert np.array_equal(g[key], plain[key]), key
     assert np.array_equal(g["est"], plain["est"])
-    M = oracle.Model(inst, init_marginals=nu)
-    k, ell, B, seed = kw["k"], kw["ell"], kw["horizon"], kw["seed"]
-    run = oracle.coupled_run(k, ell, B, seed, meeting_cap=kw.get("meeting_cap", 0), lag=kw.get("lag", 1))
+    if kw.get("coupled", True):
+        M = oracle.Model(inst, init_marginals=nu)
+        run = oracle.coupled_run(kw["k"], kw["ell"], kw["horizon"], kw["seed"],
+                                 meeting_cap=kw.get("meeting_cap", 0), lag=kw.get("lag", 1))
+    else:
+        M = oracle.Model(inst, init_marginals=nu,
+                         scan=oracle.SCAN_SYSTEMATIC if kw.get("scan") == 2 else oracle.SCAN_SCORE)
+        run = oracle.uncoupled_run(kw["burn"], kw["length"], kw["horizon"], kw["seed"])
     checked = 0
     for idx, p in enumerate(range(0, kw["slots"], stride)):
         checked += _check_slot(M, run, g["rec"][idx], p, int(g["reps"][p]), kw.get("lag", 1), steps)
