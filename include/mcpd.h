@@ -238,8 +238,10 @@ typedef struct mcpd_batch mcpd_batch;
  * slots (largest horizon) first.  Bits 8-15: size classes, 0 for automatic, else 1..8.  The
  * instances are sorted by pair state (largest first) and cut into classes of about equal work
  * (slots x slot length); each class is its own launch of the sampling kernel, with a launch shape
- * fitted to its largest pair state.  Automatic gives as many classes as the total slots fill
- * whole launches (at most four).  Results do not depend on the order or the classes. */
+ * fitted to its largest pair state, on its own stream forked from the context's stream (the
+ * classes run concurrently; the finalize waits for all).  Automatic gives as many classes as the
+ * total slots fill whole launches (at most four).  Results do not depend on the order or the
+ * classes. */
 int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
                       const uint8_t *const *ys, const mcpd_params *params, int32_t order_mode,
                       mcpd_batch **out);

@@ -477,6 +477,12 @@ struct mcpd_batch {
     std::vector<mcpd::InstDesc> insts0;    // the descriptors of a decode from the first slot
     std::vector<long long> total_work0;    // per class, for those
     bool extended = false;                 // the device descriptors describe an extension
+    // The size classes launch concurrently, each on its own stream forked from the context's
+    // stream and joined back before the finalize: a class's last, partly filled round of pairs
+    // overlaps the next class's launch instead of leaving SMs idle.
+    std::vector<cudaStream_t> cls_streams;
+    std::vector<cudaEvent_t> cls_done;
+    cudaEvent_t fork = nullptr;
     int32_t *d_clone_inst = nullptr, *d_clone_local = nullptr;
     unsigned long long *d_buckets = nullptr;   // S1 | S2lo | S2hi, each total_bucket_words
     unsigned long long *d_bcount = nullptr;
@@ -594,10 +600,19 @@ int batch_enqueue(mcpd_ctx *ctx, mcpd_batch *b, double *est_dev, double *se_dev,
                                static_cast<size_t>(c.pairs) * mcpd::pair_words(c.bp.max_na, c.bp.max_W) * 8, s));
             CU(cudaMemsetAsync(c.bp.y_state, 0, static_cast<size_t>(c.pairs) * c.bp.max_wpp * 4, s));
         }
-        if (c.bp.total_work == 0) continue;              // an extension with no instance of this class
-        if ((c.bp.lanes == 1 ? mcpd::launch_batch(c.bp, c.grid, c.block, c.smem, s)
-                             : mcpd::launch_group(c.bp, c.grid, c.block, c.smem, s)) != MCPD_OK)
-            return set_err(ctx, MCPD_ECUDA, std::string("batch kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
+    }
+    CU(cudaEventRecord(b->fork, s));
+    for (size_t k = 0; k < b->cls.size(); ++k) {
+        const BatchClass &c = b->cls[k];
+        const cudaStream_t cs = b->cls_streams[k];
+        CU(cudaStreamWaitEvent(cs, b->fork, 0));
+        if (c.bp.total_work != 0) {                      // an extension may leave a class without work
+            if ((c.bp.lanes == 1 ? mcpd::launch_batch(c.bp, c.grid, c.block, c.smem, cs)
+                                 : mcpd::launch_group(c.bp, c.grid, c.block, c.smem, cs)) != MCPD_OK)
+                return set_err(ctx, MCPD_ECUDA, std::string("batch kernel launch: ") + cudaGetErrorString(cudaGetLastError()));
+        }
+        CU(cudaEventRecord(b->cls_done[k], cs));
+        CU(cudaStreamWaitEvent(s, b->cls_done[k], 0));
     }
     if (mcpd::launch_finalize_batch(b->d_insts, b->n_inst, b->d_clone_inst, b->d_clone_local,
                                     b->total_active, est_dev, se_dev, s) != MCPD_OK)
@@ -618,6 +633,9 @@ void mcpd_batch_destroy(mcpd_batch *b) {
     for (BatchClass &c : b->cls) free_list(c.scratch);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
+    for (cudaStream_t cs : b->cls_streams) if (cs) cudaStreamDestroy(cs);
+    for (cudaEvent_t e : b->cls_done) if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     delete b;
 }
 
@@ -803,6 +821,13 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     CU_OR(cudaMemcpyAsync(b->d_clone_inst, ci.data(), ci.size() * 4, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
     CU_OR(cudaMemcpyAsync(b->d_clone_local, cl.data(), cl.size() * 4, cudaMemcpyHostToDevice, ctx->stream), mcpd_batch_destroy(b));
     if ((rc = batch_shape(ctx, b, 0)) != MCPD_OK) { mcpd_batch_destroy(b); return rc; }
+    b->cls_streams.assign(b->cls.size(), nullptr);
+    b->cls_done.assign(b->cls.size(), nullptr);
+    for (size_t k = 0; k < b->cls.size(); ++k) {
+        CU_OR(cudaStreamCreateWithFlags(&b->cls_streams[k], cudaStreamNonBlocking), mcpd_batch_destroy(b));
+        CU_OR(cudaEventCreateWithFlags(&b->cls_done[k], cudaEventDisableTiming), mcpd_batch_destroy(b));
+    }
+    CU_OR(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming), mcpd_batch_destroy(b));
     CU_OR(cudaEventCreate(&b->ev0), mcpd_batch_destroy(b));
     CU_OR(cudaEventCreate(&b->ev1), mcpd_batch_destroy(b));
     CU_OR(cudaStreamSynchronize(ctx->stream), mcpd_batch_destroy(b));
