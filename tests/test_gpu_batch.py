@@ -378,3 +378,43 @@ def test_batch_extension_by_slot_ranges(ctx):
         batch.collect()
     assert np.array_equal(est.cpu().numpy(), e0)
     batch.close()
+
+
+def test_batched_workload_full_size(ctx):
+    """The batched workload at its full size, as the bench decodes it: 512 uneven instances (n in
+    [200, 5000], k in 4..8, rates and positives per instance), 2048 slots each with a 10-sweep
+    horizon and the paper's 20-sweep meeting cap, automatic size classes running concurrently, in
+    a captured graph.  The four smallest instances equal the oracle alone bit for bit (buckets and
+    doubles); every instance's estimates are finite, in the valid range of an unbiased estimator's
+    mean of bounded corrections, and every slot is counted once."""
+    import torch
+    from paper_2608_30239_gb300 import mcpd
+    insts = synth.batched_configs(512, seed=11)
+    ps = [dict(slots=2048, horizon=10 * inst.n, seed=5000 + i, instance_id=i, meeting_cap=20 * inst.n)
+          for i, inst in enumerate(insts)]
+    batch = mcpd.Batch(ctx, insts, ps, order_mode=1)
+    assert batch.classes == 4
+    est = torch.empty(batch.total_active, dtype=torch.float64, device="cuda:0")
+    se = torch.empty_like(est)
+    with torch.cuda.stream(ctx.torch_stream):
+        batch.capture_graph(est, se)
+        batch.launch_graph()
+        st = batch.collect()
+    e, s = est.cpu().numpy(), se.cpu().numpy()
+    assert st["status"] == 0 and np.all(np.isfinite(e)) and np.all(s >= 0)
+    for i in range(len(insts)):
+        assert int(batch.buckets(i)["count"].sum()) == 2048
+    for i in np.argsort([inst.n for inst in insts], kind="stable")[:4]:
+        inst, kw = insts[i], ps[i]
+        k, ell = oracle.window_defaults(inst.n, 1)
+        M = oracle.Model(inst)
+        run = oracle.coupled_run(k, ell, kw["horizon"], kw["seed"], instance=kw["instance_id"],
+                                 meeting_cap=kw["meeting_cap"])
+        ref = M.run_slots(run, 0, kw["slots"], THREADS)
+        ref["est"], ref["se"] = M.finalize(ref, kw["slots"], ell - k + 1)
+        got = batch.buckets(int(i))
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(e[a:b], ref["est"]) and np.array_equal(s[a:b], ref["se"]), i
+    batch.close()
