@@ -243,6 +243,40 @@ def batched_leg(ctx, device, count=512, budget_slots=1024, budget_sweeps=20, see
     return out
 
 
+def library_leg(ctx, device, slots=262144, budget=1e10, seed=4242, steps=3):
+    """The paper-shaped library workload (1298 x 97, 6 pools per clone, 3 positives, fp .01,
+    fn .05, q = 3/1298) at its size: 262,144 slots and a budget of 1e10 single-site updates, decoded
+    by the two methods it compares: coupled score-weighted pairs (Algorithms 3-4, B = 19073
+    progress units per slot, one-sweep window) and uncoupled systematic scan (Algorithms 1-2, the
+    same budget: B = 38146 draws per slot, b = 130, T = 1168).  Reports each one's site-updates/s
+    (best of `steps` decodes), its largest per-clone SE, and the SE each would reach in one second
+    of the sampling kernel (SE scales as P^-1/2)."""
+    import torch
+
+    import synth
+    from paper_2608_30239_gb300 import mcpd
+    inst = synth.paper_shaped_config()
+    out = {"workload": "1298x97 k=6 fp=.01 fn=.05, 262144 slots, budget 1e10 site-updates; the library's "
+                       "default one-sweep windows (coupled k = 131, l = 1298; uncoupled b = 130, T = 1168)"}
+    for name, kw in (("coupled_score_weighted", dict(scan=mcpd.MCPD_SCAN_SCORE)),
+                     ("uncoupled_systematic", dict(coupled=False, scan=mcpd.MCPD_SCAN_SYSTEMATIC))):
+        plan = mcpd.Plan(ctx, inst, slots=slots, budget_site_updates=budget, seed=seed, **kw)
+        est = torch.empty(plan.n_active, dtype=torch.float64, device=f"cuda:{device}")
+        se = torch.empty_like(est)
+        ms, st = [], None
+        for _ in range(steps):
+            plan.run_async(est, se)
+            st = plan.collect()
+            ms.append(st["kernel_ms"])
+        best = min(ms)
+        mse = float(se.max().item())
+        out[name] = {"kernel_ms": best, "site_updates_per_s": st["site_updates"] / (best / 1000.0),
+                     "max_se": mse, "max_se_at_1s_of_kernel": mse * (best / 1000.0) ** 0.5,
+                     "replications": st["reps_retained"], "horizon": int(plan.horizon)}
+        plan.close()
+    return out
+
+
 def learned_leg(ctx, device, train=4096, held=2):
     """Time to a largest per-clone SE of 0.005 on the bench instance (1298 x 97, high noise, a
     29.4-sweep horizon per slot, B = 38146), measured for every arm: one fixed-budget decode per arm
@@ -366,6 +400,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 512-instance batch leg")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned time-to-SE leg")
+    ap.add_argument("--no-library", action="store_true", help="skip the library-shaped two-method leg")
     ap.add_argument("--slots", type=int, default=SLOTS,
                     help="slots per GPU; the budget scales with it so the horizon B stays 38146 "
                          "(smaller cases are for profiling captures)")
@@ -489,6 +524,8 @@ def main():
                                         10000)
     if rank == 0 and not args.no_learned:
         line["time_to_se"] = auxiliary_leg(learned_leg, ctx, device)
+    if rank == 0 and not args.no_library:
+        line["library_config"] = auxiliary_leg(library_leg, ctx, device)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = auxiliary_leg(cpu_oracle_sample, args.cpu_seconds)
     if rank == 0:
