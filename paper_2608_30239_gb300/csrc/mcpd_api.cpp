@@ -138,7 +138,7 @@ int mcpd_plan_create(mcpd_ctx *ctx, const mcpd_design *design, const uint8_t *y,
     const size_t tables = mcpd::kernel_table_bytes(t);
     mcpd::PairsShape shape;
     rc = mcpd::pairs_shape(t.coupled, t.scan, t.udeg, false, tables, t.wpp, ctx->smem_optin, t.P,
-                           ctx->sm_count, 0, t.capped || t.lag > 1, &shape);
+                           ctx->sm_count, 0, t.capped || t.lag > 1, !t.Tnu.empty(), &shape);
     if (rc != MCPD_OK) {
         delete pl;
         return set_err(ctx, rc, rc == MCPD_ETOO_LARGE ? "instance too large for the one-thread-per-pair layout"
@@ -527,12 +527,12 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
         if (lanes == 1) {
             mcpd::PairsShape shape;
             int rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, c.bp.udeg, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
-                                       ctx->sm_count, 0, c.bp.ext != 0, &shape);
+                                       ctx->sm_count, 0, c.bp.ext != 0, true, &shape);
             if (rc == MCPD_ETOO_LARGE) return set_err(ctx, rc, "largest instance does not fit one warp of pair state");
             if (rc != MCPD_OK) return set_err(ctx, rc, "cudaFuncSetAttribute / occupancy");
             if (warps > 0 && warps < shape.warps) {
                 rc = mcpd::pairs_shape(c.bp.coupled, c.bp.scan, c.bp.udeg, true, 0, c.bp.max_wpp, ctx->smem_optin, 0,
-                                       ctx->sm_count, warps, c.bp.ext != 0, &shape);
+                                       ctx->sm_count, warps, c.bp.ext != 0, true, &shape);
                 if (rc != MCPD_OK) return set_err(ctx, rc, "launch shape");
             }
             w = shape.warps;
@@ -792,6 +792,7 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         mcpd::BParams &bp = c.bp;
         bp.total_work = work;
         if (t.capped || t.lag > 1) bp.ext = 1;
+        if (!t.Tnu.empty()) bp.any_init = 1;
         // the class's uniform degree: the first instance's, kept while every instance shares it
         if (d.work_begin == 0) bp.udeg = t.udeg;
         else if (bp.udeg != t.udeg) bp.udeg = 0;

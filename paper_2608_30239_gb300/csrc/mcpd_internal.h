@@ -196,6 +196,7 @@ struct BParams {
     int32_t wide;                     // launch the 20-warp variant of the batch kernel
     int32_t ext;                      // some instance has a meeting cap or a lag > 1
     int32_t udeg;                     // every instance of the class has this uniform degree (0: mixed)
+    int32_t any_init;                 // some instance of the class has a random start
 };
 
 // Launch shape of the one-thread-per-pair kernel (mcpd_kernels.cu).
@@ -210,9 +211,10 @@ int pairs_y_regions(int coupled, int warps);
 size_t pairs_smem_bytes(size_t tables, int wpp, int warps, int y_regions);
 // tables: bytes staged at the start of shared memory (0 for batches); wpp: words per column;
 // P: slots of a single instance (0 = do not shape by rounds); warps: requested warps (0 = auto);
-// ext: the run launches the kernel variant with meeting caps and lags > 1.
+// ext: the run launches the kernel variant with meeting caps and lags > 1; rnd: a single
+// instance with random starts (batches ignore it).
 int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int wpp, size_t smem_optin,
-                long long P, int sm_count, int warps, bool ext, PairsShape *out);
+                long long P, int sm_count, int warps, bool ext, bool rnd, PairsShape *out);
 
 // The batched sampling-kernel variants (mcpd_batch.cu): the kernel for a class, and the
 // compile-time degree a class of uniform degree udeg runs with (0: the generic build).
@@ -226,7 +228,8 @@ int launch_group(const BParams &bp, int grid, int block, size_t smem, void *stre
 int set_group_smem(int lanes, size_t bytes);
 int group_max_threads(int lanes);
 int group_occupancy(int lanes, int block, size_t smem, int *blocks_per_sm);
-int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide = false, bool ext = false);
+int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide = false, bool ext = false,
+                      bool rnd = true);
 int launch_finalize_batch(const InstDesc *insts, int n_inst, const int32_t *clone_inst,
                           const int32_t *clone_local, long long total_clones, double *est,
                           double *se, void *stream);

@@ -75,8 +75,19 @@ __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, uin
 
 using PairsFn = PairsKernelFn;
 
-PairsFn pick(int coupled, int scan, bool batch, int udeg = 0, bool wide = false, bool ext = false) {
+PairsFn pick(int coupled, int scan, bool batch, int udeg = 0, bool wide = false, bool ext = false, bool rnd = true) {
     if (batch) return pick_batch(coupled, scan, batch_kernel_degree(coupled, ext, udeg), wide, ext);
+    if (coupled && !ext && !rnd) {   // the default all-negative start: no random-start check in the loop
+        switch (udeg) {
+            case 3: return pairs_kernel<true, false, false, 3, false, false, false, false>;
+            case 4: return pairs_kernel<true, false, false, 4, false, false, false, false>;
+            case 5: return pairs_kernel<true, false, false, 5, false, false, false, false>;
+            case 6: return pairs_kernel<true, false, false, 6, false, false, false, false>;
+            case 7: return pairs_kernel<true, false, false, 7, false, false, false, false>;
+            case 8: return pairs_kernel<true, false, false, 8, false, false, false, false>;
+            default: return pairs_kernel<true, false, false, 0, false, false, false, false>;
+        }
+    }
     if (coupled && ext) {
         switch (udeg) {
             case 3: return pairs_kernel<true, false, false, 3, false, true>;
@@ -126,10 +137,11 @@ int set_smem(size_t bytes, bool batch) {
                 if (batch && ud != batch_kernel_degree(c, 0, ud)) continue;
                 for (int wide = 0; wide <= (batch ? 1 : 0); ++wide)
                     for (int ext = 0; ext <= c; ++ext)
-                        if (cudaFuncSetAttribute(pick(c, sc, batch, ud, wide != 0, ext != 0),
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 static_cast<int>(bytes)) != cudaSuccess)
-                            return MCPD_ECUDA;
+                        for (int rnd = 0; rnd <= 1; ++rnd)
+                            if (cudaFuncSetAttribute(pick(c, sc, batch, ud, wide != 0, ext != 0, rnd != 0),
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     static_cast<int>(bytes)) != cudaSuccess)
+                                return MCPD_ECUDA;
             }
         }
     return batch ? MCPD_OK : set_trace_smem(bytes);
@@ -149,7 +161,8 @@ int launch_pairs(const KParams &kp, int grid, int block, size_t smem, void *stre
     if (kp.trace_rec) return launch_pairs_trace(kp, grid, block, smem, stream);
     const BParams none{};
     const bool ext = kp.capped != 0 || kp.lag > 1;
-    pick(kp.coupled, kp.scan, false, kp.udeg, false, ext)<<<grid, block, smem, static_cast<cudaStream_t>(stream)>>>(kp, none);
+    pick(kp.coupled, kp.scan, false, kp.udeg, false, ext, kp.Tnu != nullptr)<<<grid, block, smem,
+                                                                           static_cast<cudaStream_t>(stream)>>>(kp, none);
     return cudaGetLastError() == cudaSuccess ? MCPD_OK : MCPD_ECUDA;
 }
 
@@ -193,13 +206,13 @@ size_t pairs_smem_bytes(size_t tables, int wpp, int warps, int y_regions) {
 }
 
 int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int wpp, size_t smem_optin,
-                long long P, int sm_count, int warps, bool ext, PairsShape *out) {
+                long long P, int sm_count, int warps, bool ext, bool rnd, PairsShape *out) {
     // Batches: the wide variant when the pair state leaves room for more warps than the narrow one
     // is compiled for.  The thread cap and the occupancy query use the variant the run launches
-    // (ext: the one with meeting caps and lags > 1).
+    // (ext: the one with meeting caps and lags > 1; rnd: the one that draws random starts).
     ext = ext && coupled;
     bool wide = batch;
-    int cap = pairs_max_threads(coupled, scan, udeg, batch, wide, ext) / 32;
+    int cap = pairs_max_threads(coupled, scan, udeg, batch, wide, ext, rnd) / 32;
     auto bytes = [&](int w) { return pairs_smem_bytes(tables, wpp, w, pairs_y_regions(coupled, w)); };
     auto most = [&](size_t budget) {
         int best = 0;
@@ -208,7 +221,7 @@ int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int 
     };
     auto resident = [&](int w, int *per_sm) {
         *per_sm = 1;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pick(coupled, scan, batch, udeg, wide, ext),
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pick(coupled, scan, batch, udeg, wide, ext, rnd),
                                                              w * 32, bytes(w)) == cudaSuccess;
     };
     int w1 = most(smem_optin);
@@ -253,9 +266,10 @@ int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int 
     return MCPD_OK;
 }
 
-int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide, bool ext) {
+int pairs_max_threads(int coupled, int scan, int udeg, bool batch, bool wide, bool ext, bool rnd) {
     cudaFuncAttributes a{};
-    if (cudaFuncGetAttributes(&a, pick(coupled, scan, batch, udeg, wide, ext && coupled)) != cudaSuccess) return 512;
+    if (cudaFuncGetAttributes(&a, pick(coupled, scan, batch, udeg, wide, ext && coupled, rnd)) != cudaSuccess)
+        return 512;
     return a.maxThreadsPerBlock;
 }
 

@@ -113,7 +113,7 @@ extern "C" int mcpd_decode_noalloc(mcpd_ctx *ctx, const mcpd_design *design, con
     const size_t tables = kernel_table_bytes(t);
     PairsShape shape;
     const int src = pairs_shape(t.coupled, t.scan, t.udeg, false, tables, t.wpp, ctx->smem_optin, t.P,
-                                ctx->sm_count, 0, t.capped || t.lag > 1, &shape);
+                                ctx->sm_count, 0, t.capped || t.lag > 1, !t.Tnu.empty(), &shape);
     if (src == MCPD_ETOO_LARGE) return fail(ctx, src, "instance too large for the one-thread-per-pair layout");
     if (src != MCPD_OK) return fail(ctx, MCPD_ECUDA, "launch shape (cudaFuncSetAttribute / occupancy)");
     // scratch block (sums, statistics, touched sets) and Y column

@@ -48,7 +48,10 @@ namespace {
 // TRACE (single instance): also record the first replications of every traced slot (meeting time,
 // completion time, and per draw the site and which chains flipped; MCPD_FETCH_TRACE_REC), for the
 // trajectory parity tests.  The production variants compile none of it.
-template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG, bool WIDE = false, bool EXT = false, bool TRACE = false>
+// RND = false: the instance has no random start (Z_0 = 0), so the warp never draws one; the
+// runs with a random start launch RND = true (the default), whose loop checks for pending starts.
+template <bool COUPLED, bool SYSTEMATIC, bool BATCH, int DEG, bool WIDE = false, bool EXT = false, bool TRACE = false,
+          bool RND = true>
 __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 : 512), 1) pairs_kernel(const KParams p, const BParams bp) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -140,11 +143,8 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     MCPD_FIELD(v_work_begin, __ldg(&desc()->work_begin), 0ll);
     MCPD_FIELD(v_dwi, __ldg(&desc()->dummy_word_index), p.dummy_word_index);
     MCPD_FIELD(v_dw, __ldg(&desc()->dummy_word), p.dummy_word);
-    MCPD_FIELD(v_n_init, __ldg(&desc()->n_init_pairs), p.n_init_pairs);
     MCPD_FIELD(v_Tnu, reinterpret_cast<const unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->Tnu))),
                reinterpret_cast<const unsigned long long *>(p.Tnu));
-    MCPD_FIELD(v_init_pairs, reinterpret_cast<const uint32_t *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->init_pairs))),
-               p.init_pairs);
     MCPD_FIELD(v_S1, reinterpret_cast<unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->S1))), p.S1);
     MCPD_FIELD(v_S2lo, reinterpret_cast<unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->S2lo))), p.S2lo);
     MCPD_FIELD(v_S2hi, reinterpret_cast<unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->S2hi))), p.S2hi);
@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     auto wstep = [&](uint32_t u) -> uint32_t { return u < ws0 ? 0u : min(u - ws0 + 1u, wcap); };
 
     bool alive = true;
+    bool init_pending = false;        // a random start waits for the warp's draw (coop_init)
     uint32_t slot_local = 0, slot_g = 0, r = 0, t = 0, S = 0, N = 0, tau = 0, D = 0;
     uint32_t abort_t = 0xFFFFFFFFu, t_end = 0, stop_unmet = 0, sysI = 0, reps_in_slot = 0;
     uint32_t rep_words = 0, slot_words = 0;   // groups of 2^gshift bit words touched
@@ -323,28 +324,10 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
                 trec[3] = static_cast<int32_t>(r);
             }
         }
-        const unsigned long long *Tnu = v_Tnu();
-        if (Tnu) {   // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0 (clones with nu_i = 0 stay 0)
-            const uint32_t *init_pairs = v_init_pairs();
-            const int n_init_pairs = v_n_init();
-            for (int e = 0; e < n_init_pairs; ++e) {
-                const int a = static_cast<int>(init_pairs[e]);
-                const uint4 b = philox10(make_uint4(static_cast<uint32_t>(a) >> 1, r, slot_g,
-                                                    instance | (1u << 24)), k0, k1);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = a + h;
-                    if (c >= na) break;
-                    const unsigned long long u = h ? ((static_cast<unsigned long long>(b.z) << 32) | b.w)
-                                                   : ((static_cast<unsigned long long>(b.x) << 32) | b.y);
-                    if (u < Tnu[c]) {
-                        const uint32_t q = c >> 5;
-                        st[q * 32] |= 1u << (c & 31);
-                        bump_counts(c, 1u, cbase);
-                        rep_words |= 1u << (q >> gshift);
-                    }
-                }
-            }
+        // Z_0 ~ prod Bernoulli(nu_i); X_0 = Y_0 = Z_0 (clones with nu_i = 0 stay 0): drawn by the
+        // whole warp before this lane's next step (coop_init at the top of the loop)
+        if constexpr (RND) {
+            if (v_Tnu()) init_pending = true;
         }
     };
 
@@ -757,6 +740,96 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         if constexpr (BATCH) return philox10(make_uint4(c0, r, slot_g, instance), k0, k1);
         else return philox10_rk(make_uint4(c0, r, slot_g, instance), p.rk);
     };
+    // Random start Z_0 ~ prod Bernoulli(nu_i): the initial state of lane src's new replication
+    // (batched: of src's instance), drawn by every lane of `act`.  Lane e of the group takes the clone pairs e,
+    // e + |act|, ... of the clones with nu_i > 0 (one Philox block each, tag 1, counter
+    // (a / 2, r, slot, instance)), and sets the bits and pool counts it draws in src's column with
+    // shared-memory atomics (a count word holds four pools of one column, and a count never passes
+    // 255, so adding 1 << 8 b touches only its own byte).  The same draws and the same state as one
+    // lane drawing them all, in about 1/|act| of the time, and not divergent.
+    auto coop_init = [&](int src, unsigned act) {
+        if constexpr (BATCH) {
+            // src's instance: its tables, seed and layout
+            const int c_s = __shfl_sync(act, cur, src);
+            const uint32_t r_s = __shfl_sync(act, r, src), slot_s = __shfl_sync(act, slot_g, src);
+            const InstDesc &d = bp.insts[c_s];
+            const uint32_t *ip = d.init_pairs;
+            const unsigned long long *tnu = reinterpret_cast<const unsigned long long *>(d.Tnu);
+            const int n_ip = d.n_init_pairs, na_s = d.na, deg_s = d.deg;
+            const uint32_t dummy_s = d.dummy_entry, inst_s = d.instance, W_s = static_cast<uint32_t>(d.W);
+            const uint32_t k0_s = static_cast<uint32_t>(d.seed), k1_s = static_cast<uint32_t>(d.seed >> 32);
+            const uint4 *rows_s = reinterpret_cast<const uint4 *>(MASKT ? d.rows_mask : d.rows);
+            uint32_t gsh = 0;
+            while (((W_s + (1u << gsh) - 1) >> gsh) > 32) ++gsh;
+            uint32_t *const st_s = regions + warp * region_words + src;
+            unsigned char *const cb_s = reinterpret_cast<unsigned char *>(st_s);
+            const int nthr = __popc(act), rank = __popc(act & ((1u << lane) - 1u));
+            uint32_t groups = 0;
+            for (int e = rank; e < n_ip; e += nthr) {
+                const int a = static_cast<int>(ip[e]);
+                const uint4 b = philox10(make_uint4(static_cast<uint32_t>(a) >> 1, r_s, slot_s, inst_s | (1u << 24)),
+                                         k0_s, k1_s);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = a + h;
+                    if (c >= na_s) break;
+                    const unsigned long long u = h ? ((static_cast<unsigned long long>(b.z) << 32) | b.w)
+                                                   : ((static_cast<unsigned long long>(b.x) << 32) | b.y);
+                    if (u < tnu[c]) {
+                        const uint32_t q = c >> 5;
+                        atomicOr(&st_s[q * 32], 1u << (c & 31));
+                        uint32_t ent[8];
+                        entries(__ldg(rows_s + c), ent);
+#pragma unroll
+                        for (int l = 0; l < kRow; ++l) {
+                            if (!(l < NE && (DEG > 0 || (l < deg_s && ent[l] != dummy_s)))) continue;
+                            const uint32_t off = MASKT ? ent[l] : (ent[l] & 0x7FFFu);
+                            atomicAdd(reinterpret_cast<uint32_t *>(cb_s + (off & ~3u)), 1u << (8u * (off & 3u)));
+                        }
+                        groups |= 1u << (q >> gsh);
+                    }
+                }
+            }
+            groups = __reduce_or_sync(act, groups);
+            if (lane == src) rep_words |= groups;
+            __syncwarp(act);
+        } else {
+            const uint32_t r_s = __shfl_sync(act, r, src), slot_s = __shfl_sync(act, slot_g, src);
+            uint32_t *const st_s = regions + warp * region_words + src;
+            unsigned char *const cb_s = reinterpret_cast<unsigned char *>(st_s);
+            const int nthr = __popc(act), rank = __popc(act & ((1u << lane) - 1u));
+            uint32_t groups = 0;
+            for (int e = rank; e < p.n_init_pairs; e += nthr) {
+                const int a = static_cast<int>(p.init_pairs[e]);
+                const uint4 b = philox10_rk(make_uint4(static_cast<uint32_t>(a) >> 1, r_s, slot_s,
+                                                       instance | (1u << 24)), p.rk);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = a + h;
+                    if (c >= na) break;
+                    const unsigned long long u = h ? ((static_cast<unsigned long long>(b.z) << 32) | b.w)
+                                                   : ((static_cast<unsigned long long>(b.x) << 32) | b.y);
+                    if (u < p.Tnu[c]) {
+                        const uint32_t q = c >> 5;
+                        atomicOr(&st_s[q * 32], 1u << (c & 31));
+                        uint32_t ent[8];
+                        entries(rowAt(c), ent);
+#pragma unroll
+                        for (int l = 0; l < kRow; ++l) {
+                            if (!real(l, ent)) continue;
+                            const uint32_t off = MASKT ? ent[l] : (ent[l] & 0x7FFFu);
+                            atomicAdd(reinterpret_cast<uint32_t *>(cb_s + (off & ~3u)), 1u << (8u * (off & 3u)));
+                        }
+                        groups |= 1u << (q >> gshift);
+                    }
+                }
+            }
+            groups = __reduce_or_sync(act, groups);
+            if (lane == src) rep_words |= groups;
+            __syncwarp(act);
+        }
+    };
+
     start_slot();
     uint4 blk = draw(t >> 1);
     auto first_site = [&]() {               // the first step of a block
@@ -764,6 +837,18 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     };
     first_site();
     while (alive) {
+        if constexpr (RND) {
+            if (BATCH ? bp.any_init != 0 : p.Tnu != nullptr) {   // random starts of lanes that began a replication
+                const unsigned act = __activemask();
+                unsigned pend = __ballot_sync(act, init_pending);
+                while (pend) {
+                    const int src = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    coop_init(src, act);
+                }
+                init_pending = false;
+            }
+        }
         // words (0,1) at even t and (2,3) at odd t; the next block is computed ahead (its first
         // site word is the second step's prefetch) and discarded if the replication ends
         uint4 nxt;

@@ -3,7 +3,7 @@
 #include "mcpd.h"
 #include "mcpd_internal.h"
 namespace mcpd {
-int pairs_shape(int, int, int, bool, size_t, int, size_t, long long, int, int, bool, PairsShape *) { return MCPD_ECUDA; }
+int pairs_shape(int, int, int, bool, size_t, int, size_t, long long, int, int, bool, bool, PairsShape *) { return MCPD_ECUDA; }
 int pairs_y_regions(int, int) { return 0; }
 size_t pairs_smem_bytes(size_t, int, int, int) { return 0; }
 int batch_kernel_degree(int, int, int) { return 0; }
