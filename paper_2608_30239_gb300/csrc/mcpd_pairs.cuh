@@ -835,16 +835,24 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     auto first_site = [&]() {               // the first step of a block
         if (!SYSTEMATIC) { I_cur = site_of(blk.x); row_cur = rowAt(I_cur); }
     };
-    first_site();
+    // A batched thread that found no slot has loaded no instance (its table pointers are null):
+    // only threads with a slot draw their first site.
+    if (alive) first_site();
+    // Random starts: the lanes still in the loop (every lane of the warp runs the kernel to its
+    // end, so the first ballot names all 32).  The warp meets at the bottom of each iteration, so
+    // that a lane whose replication began in a divergent branch has its start drawn by all of
+    // them, not only by the lanes that reached the top of the loop with it.
+    const bool rnd_run = RND && (BATCH ? bp.any_init != 0 : p.Tnu != nullptr);
+    unsigned live = 0;
+    if (rnd_run) live = __ballot_sync(0xFFFFFFFFu, alive);
     while (alive) {
         if constexpr (RND) {
-            if (BATCH ? bp.any_init != 0 : p.Tnu != nullptr) {   // random starts of lanes that began a replication
-                const unsigned act = __activemask();
-                unsigned pend = __ballot_sync(act, init_pending);
+            if (rnd_run) {   // random starts of lanes that began a replication
+                unsigned pend = __ballot_sync(live, init_pending);
                 while (pend) {
                     const int src = __ffs(pend) - 1;
                     pend &= pend - 1;
-                    coop_init(src, act);
+                    coop_init(src, live);
                 }
                 init_pending = false;
             }
@@ -880,6 +888,9 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
             first_site();
         } else {
             blk = nxt;
+        }
+        if constexpr (RND) {
+            if (rnd_run) live = __ballot_sync(live, alive);
         }
     }
 
