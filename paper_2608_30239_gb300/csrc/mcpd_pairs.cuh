@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     MCPD_FIELD(v_work_begin, __ldg(&desc()->work_begin), 0ll);
     MCPD_FIELD(v_dwi, __ldg(&desc()->dummy_word_index), p.dummy_word_index);
     MCPD_FIELD(v_dw, __ldg(&desc()->dummy_word), p.dummy_word);
+    MCPD_FIELD(v_wpp, static_cast<uint32_t>(__ldg(&desc()->wpp)), static_cast<uint32_t>(p.wpp));
     MCPD_FIELD(v_Tnu, reinterpret_cast<const unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->Tnu))),
                reinterpret_cast<const unsigned long long *>(p.Tnu));
     MCPD_FIELD(v_S1, reinterpret_cast<unsigned long long *>(__ldg(reinterpret_cast<const unsigned long long *>(&desc()->S1))), p.S1);
@@ -235,18 +236,6 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     uint32_t rep_words = 0, slot_words = 0;   // groups of 2^gshift bit words touched
     int32_t *trec = nullptr;                   // TRACE: the record of the current replication
 
-    // Add delta (mod 256) to the counts of every pool of clone c in the column at `base`.
-    auto bump_counts = [&](uint32_t c, uint32_t delta, unsigned char *base) {
-        const uint4 row = rowAt(c);
-        uint32_t ent[8];
-        entries(row, ent);
-#pragma unroll
-        for (int l = 0; l < kRow; ++l) {
-            if (!real(l, ent)) continue;
-            unsigned char *cnt = base + (ent[l] & 0x7FFFu);
-            *cnt = static_cast<unsigned char>(*cnt + delta);
-        }
-    };
     // A pair that stops being met takes a free Y column (column `lane` of a Y region first,
     // then any free one; bounded tries), else its global column.
     auto acquire_y = [&]() {
@@ -265,43 +254,43 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         ycol = yslot >= 0 ? yreg + (yslot >> 5) * region_words + (yslot & 31) : yglob();
         if (DEG == 0) ycol[v_dwi() * 32] = v_dw();
     };
-    // Empty the Y column in use (every Y bit lies in a group marked in rep_words) and return it.
+    // Empty the Y column in use and return it: its bit words (every Y bit lies in a group marked in
+    // rep_words) and all its count words (the padding pool's word among them) to zero.  Zeroing
+    // the count words costs one store each, where taking each set bit's pools back down costs a
+    // row load and deg count updates per bit (a random start leaves many bits set).
     auto release_y = [&]() {
-        unsigned char *yb = reinterpret_cast<unsigned char *>(ycol);
         uint32_t groups = rep_words;
         while (groups) {
             const int g = __ffs(groups) - 1;
             groups &= groups - 1;
             const uint32_t q0 = static_cast<uint32_t>(g) << gshift, q1 = min(W, q0 + (1u << gshift));
-            for (uint32_t q = q0; q < q1; ++q) {
-                uint32_t yw = ycol[q * 32];
-                if (!yw) continue;
-                ycol[q * 32] = 0u;
-                while (yw) { const int b = __ffs(yw) - 1; yw &= yw - 1; bump_counts(q * 32 + b, 0xFFu, yb); }
-            }
+            for (uint32_t q = q0; q < q1; ++q) ycol[q * 32] = 0u;
         }
-        if (DEG == 0) ycol[v_dwi() * 32] = 0u;
+        for (uint32_t w = W, e = v_wpp(); w < e; ++w) ycol[w * 32] = 0u;
         __threadfence_block();
         if (yslot >= 0) atomicOr(&ymask[yslot >> 5], 1u << (yslot & 31));
         yslot = -1;
         ycol = nullptr;
     };
-    // A pre-lag update flipped site I of X_t = X_0 and the start was random: Y_0 = X_0 (X_{t+1}
-    // with bit I restored) goes to the Y column.
-    auto copy_y0 = [&](uint32_t qI, uint32_t bitI) {
-        unsigned char *yb = reinterpret_cast<unsigned char *>(ycol);
+    // A pre-lag update flipped site I of X_t = X_0 and the start was random: Y_0 = X_0 goes to the
+    // (empty) Y column: X_{t+1}'s bit words with bit I restored, X_{t+1}'s count words, and the
+    // counts of I's pools as they were before the flip (cx, loaded this step).
+    auto copy_y0 = [&](uint32_t qI, uint32_t bitI, const uint32_t *ent, const uint32_t *cx) {
         uint32_t groups = rep_words;
         while (groups) {
             const int g = __ffs(groups) - 1;
             groups &= groups - 1;
             const uint32_t q0 = static_cast<uint32_t>(g) << gshift, q1 = min(W, q0 + (1u << gshift));
             for (uint32_t q = q0; q < q1; ++q) {
-                uint32_t yw = st[q * 32] ^ (q == qI ? bitI : 0u);
-                if (!yw) continue;
-                ycol[q * 32] = yw;
-                while (yw) { const int b = __ffs(yw) - 1; yw &= yw - 1; bump_counts(q * 32 + b, 1u, yb); }
+                const uint32_t yw = st[q * 32] ^ (q == qI ? bitI : 0u);
+                if (yw) ycol[q * 32] = yw;
             }
         }
+        for (uint32_t w = W, e = v_wpp(); w < e; ++w) ycol[w * 32] = st[w * 32];
+        unsigned char *yb = reinterpret_cast<unsigned char *>(ycol);
+#pragma unroll
+        for (int l = 0; l < kRow; ++l)
+            if (real(l, ent)) yb[ent[l] & 0x7FFFu] = static_cast<unsigned char>(cx[l]);
     };
 
     // A batched pair keeps the pre-lag updates of its replications (sum of L) in the high half of
@@ -392,18 +381,15 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
                         red_add(sacc(q * 32 + b), wX);
                     }
                 }
-                uint32_t xm = xw;                 // X's counts back to zero
-                while (xm) {
-                    const int b = __ffs(xm) - 1;
-                    xm &= xm - 1;
-                    bump_counts(q * 32 + b, 0xFFu, cbase);
-                }
                 const uint32_t touched = tw | (move && wX != 0 ? xw : 0u);
                 if (tw) trep()[q] = 0u;
                 if (xw) st[q * 32] = 0u;
                 if (touched) { red_or(&tslot()[q], touched); slot_words |= 1u << g; }
             }
         }
+        // X's counts back to zero (one store per count word), the padding pool's count kept
+        for (uint32_t w = W, e = v_wpp(); w < e; ++w) st[w * 32] = 0u;
+        st[v_dwi() * 32] = v_dw();
         rep_words = 0;
     };
 
@@ -574,7 +560,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
             D = 1; tau = 0; t_end = stop_unmet;
             if (!EXT || ycol == nullptr) {      // first move: Y_0 = X_t to the Y column
                 acquire_y();
-                if (v_Tnu()) copy_y0(q, bit);
+                if (v_Tnu()) copy_y0(q, bit, ent, cx);
             }
         }
     };
