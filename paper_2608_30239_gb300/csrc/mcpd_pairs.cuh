@@ -231,6 +231,9 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
 
     bool alive = true;
     bool init_pending = false;        // a random start waits for the warp's draw (coop_init)
+    bool fin_pending = false;         // a completed replication's state waits for the warp (coop_finish)
+    uint32_t fin_words = 0;           // its groups of bit words (rep_words at completion)
+    long long fin_wX = 0;             // its closing weight w(C)
     uint32_t slot_local = 0, slot_g = 0, r = 0, t = 0, S = 0, N = 0, tau = 0, D = 0;
     uint32_t abort_t = 0xFFFFFFFFu, t_end = 0, stop_unmet = 0, sysI = 0, reps_in_slot = 0;
     uint32_t rep_words = 0, slot_words = 0;   // groups of 2^gshift bit words touched
@@ -353,9 +356,18 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     // replication only zeroes its own (stores) and adds its closing terms; the replication's sums
     // are read back only when it is discarded (doomed or at the step limit), to take its events
     // out of the slot's sums.
-    auto finish_rep = [&](bool move, uint32_t C) {
+    // defer (a completed replication whose slot goes on): the Y column is returned here and the
+    // rest is left to the whole warp at the top of the loop (coop_finish).
+    auto finish_rep = [&](bool move, uint32_t C, bool defer) {
         const long long wX = move ? static_cast<long long>(wstep(C)) : 0;
         if (COUPLED && (EXT ? ycol != nullptr : D != 0)) release_y();
+        if (defer) {
+            fin_pending = true;
+            fin_words = rep_words;
+            fin_wX = wX;
+            rep_words = 0;
+            return;
+        }
         uint32_t groups = rep_words;
         while (groups) {
             const int g = __ffs(groups) - 1;
@@ -490,13 +502,15 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
             const long long audit = v_tau_audit();
             over = (audit > 0 && (tau > audit || tau == 0u)) ? (1ll << 32) : 0ll;
         }
-        finish_rep(true, C);
-        S += C;
+        const uint32_t B = v_B();
+        const uint32_t S_next = S + C;
+        const bool goes_on = S_next < B && B - S_next >= v_unit();
+        finish_rep(true, C, goes_on);     // a slot's last replication ends before its flush (end_slot)
+        S = S_next;
         N += 1;
         red_add(reinterpret_cast<long long *>(&pst()[kPsRetained]), 1 + over);
-        const uint32_t B = v_B();
         if (S > B) red_add(reinterpret_cast<long long *>(&pst()[kPsZero]), 1);   // only a slot's first replication ends beyond B
-        if (S < B && B - S >= v_unit()) { ++r; start_rep(); }
+        if (goes_on) { ++r; start_rep(); }
         else end_slot(true);
     };
 
@@ -504,7 +518,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         trace_end(2);
         red_add(reinterpret_cast<long long *>(&pst()[kPsProgress]), t);
         red_add(reinterpret_cast<long long *>(&pst()[kPsAborted]), 1);
-        finish_rep(false, 0);
+        finish_rep(false, 0, false);
         end_slot(true);
     };
 
@@ -513,7 +527,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         red_add(reinterpret_cast<long long *>(&pst()[kPsProgress]), t);
         red_add(reinterpret_cast<long long *>(&pst()[kPsLimit]), 1);
         atomicExch(BATCH ? bp.error : p.error, 1);
-        finish_rep(false, 0);
+        finish_rep(false, 0, false);
         end_slot(false);
     };
 
@@ -816,6 +830,74 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         }
     };
 
+    // The end of lane src's completed replication (deferred by finish_rep), by every lane of act:
+    // the lane of rank e in act takes the words e, e + |act|, ... of src's column that lie in
+    // src's fin_words groups.
+    // Each reads its word of the replication's touched bits (independent loads across the lanes,
+    // where one lane alone would wait on a chain of dependent loads), zeroes the replication sums
+    // of those clones, adds the closing term w(C) of every site set in X_C to the slot's sums,
+    // marks the slot's touched bits, and clears the word in the touched set and in X_C; the lanes
+    // also zero X_C's count words (the padding pool's word back to its value).  The same state and
+    // the same sums as src doing it alone, once every lane's writes are fenced.
+    const long long pw = pair_words(stride_na, stride_W);
+    auto coop_finish = [&](int src, unsigned act) {
+        const uint32_t words_s = __shfl_sync(act, fin_words, src);
+        const long long wX_s = __shfl_sync(act, fin_wX, src);
+        uint32_t W_s, gsh_s, wpp_s, dwi_s, dw_s;
+        if constexpr (BATCH) {
+            const InstDesc &d = bp.insts[__shfl_sync(act, cur, src)];
+            W_s = static_cast<uint32_t>(__ldg(&d.W));
+            wpp_s = static_cast<uint32_t>(__ldg(&d.wpp));
+            dwi_s = static_cast<uint32_t>(__ldg(&d.dummy_word_index));
+            dw_s = __ldg(&d.dummy_word);
+            gsh_s = __shfl_sync(act, gshift, src);
+        } else {
+            W_s = W; gsh_s = gshift;
+            wpp_s = static_cast<uint32_t>(p.wpp);
+            dwi_s = static_cast<uint32_t>(p.dummy_word_index);
+            dw_s = p.dummy_word;
+        }
+        long long *const pb_s = pb + static_cast<long long>(src - lane) * pw;
+        uint32_t *const trep_s = reinterpret_cast<uint32_t *>(pb_s + 2 * stride_na + kPairStats);
+        uint32_t *const tslot_s = trep_s + stride_W;
+        uint32_t *const st_s = regions + warp * region_words + src;
+        const uint32_t nthr = static_cast<uint32_t>(__popc(act));
+        const uint32_t rank = static_cast<uint32_t>(__popc(act & ((1u << lane) - 1u)));
+        uint32_t grp = 0;
+        for (uint32_t q = rank; q < W_s; q += nthr) {
+            const uint32_t g = q >> gsh_s;
+            if (!((words_s >> g) & 1u)) continue;
+            const uint32_t xw = st_s[q * 32];
+            const uint32_t tw = __ldcg(&trep_s[q]);
+            uint32_t tm = tw;
+            while (tm) {
+                const int b = __ffs(tm) - 1;
+                tm &= tm - 1;
+                pb_s[2 * static_cast<size_t>(q * 32 + b)] = 0;            // replication sum
+            }
+            if (wX_s != 0) {
+                uint32_t om = xw;
+                while (om) {
+                    const int b = __ffs(om) - 1;
+                    om &= om - 1;
+                    red_add(pb_s + 2 * static_cast<size_t>(q * 32 + b) + 1, wX_s);   // slot sum
+                }
+            }
+            const uint32_t touched = tw | (wX_s != 0 ? xw : 0u);
+            if (tw) trep_s[q] = 0u;
+            if (xw) st_s[q * 32] = 0u;
+            if (touched) { red_or(&tslot_s[q], touched); grp |= 1u << g; }
+        }
+        for (uint32_t w = W_s + rank; w < wpp_s; w += nthr) st_s[w * 32] = w == dwi_s ? dw_s : 0u;
+        grp = __reduce_or_sync(act, grp);
+        if (lane == src) slot_words |= grp;
+        // src's next replication reduces into the sums and touched words these lanes just stored
+        // to, and its slot's flush reads the slot sums they reduced into: every lane's global
+        // writes are performed (GPU scope) before the warp goes on.
+        __threadfence();
+        __syncwarp(act);
+    };
+
     start_slot();
     uint4 blk = draw(t >> 1);
     auto first_site = [&]() {               // the first step of a block
@@ -824,14 +906,29 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
     // A batched thread that found no slot has loaded no instance (its table pointers are null):
     // only threads with a slot draw their first site.
     if (alive) first_site();
-    // Random starts: the lanes still in the loop (every lane of the warp runs the kernel to its
-    // end, so the first ballot names all 32).  The warp meets at the bottom of each iteration, so
-    // that a lane whose replication began in a divergent branch has its start drawn by all of
-    // them, not only by the lanes that reached the top of the loop with it.
+    // The lanes still in the loop (every lane of the warp runs the kernel to its end, so the first
+    // ballot names all 32).  The warp meets at the bottom of each iteration, so that the end of a
+    // replication, or a random start, that a lane reached in a divergent branch is worked by all
+    // of them at the top of the next, not only by the lanes that reached it with that lane.
     const bool rnd_run = RND && (BATCH ? bp.any_init != 0 : p.Tnu != nullptr);
-    unsigned live = 0;
-    if (rnd_run) live = __ballot_sync(0xFFFFFFFFu, alive);
+    unsigned live = __ballot_sync(0xFFFFFFFFu, alive);
     while (alive) {
+        {
+            unsigned pend = __ballot_sync(live, fin_pending);
+            if (pend) {
+                // An ending lane's last flip events (reductions into its touched words and sums,
+                // some issued this iteration) are performed before the other lanes read or store
+                // to those words.
+                if (fin_pending) __threadfence();
+                __syncwarp(live);
+                while (pend) {
+                    const int src = __ffs(pend) - 1;
+                    pend &= pend - 1;
+                    coop_finish(src, live);
+                }
+                fin_pending = false;
+            }
+        }
         if constexpr (RND) {
             if (rnd_run) {   // random starts of lanes that began a replication
                 unsigned pend = __ballot_sync(live, init_pending);
@@ -875,9 +972,7 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         } else {
             blk = nxt;
         }
-        if constexpr (RND) {
-            if (rnd_run) live = __ballot_sync(live, alive);
-        }
+        live = __ballot_sync(live, alive);
     }
 
     // Split the packed records.  Started: count (low half) and, batched, the pre-lag updates (high
