@@ -35,9 +35,9 @@ BUDGET = 4e10
 SEED = 20260
 # DRAM bytes (read + written) per coupled draw of the sampling kernel on this workload, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the 87,552-slot case of this
-# configuration (3.294e9 draws, 2.208 + 3.234 GB), scaled to a launch by its draws.  Taken for the
+# configuration (3.294e9 draws, 2.200 + 3.262 GB), scaled to a launch by its draws.  Taken for the
 # current kernel revision; it is the accumulator events and flushes, not a per-step stream.
-DRAM_BYTES_PER_DRAW = 1.6521
+DRAM_BYTES_PER_DRAW = 1.6582
 
 
 def workload_config(extra=None):
