@@ -322,6 +322,32 @@ def test_degenerate_inputs(ctx, case):
         assert g["est"].shape == (1,)
 
 
+@pytest.mark.parametrize("variant", ["plain", "random_start", "cap_lag_random_start"])
+@pytest.mark.parametrize("P", [1, 2, 5, 33, 97])
+def test_few_live_lanes_per_warp(ctx, variant, P):
+    """Far fewer slots than the launch has threads, so most warps hold one or a few lanes with
+    work, and lanes leave while others go on. The ends of replications and the random starts
+    that the live lanes of a warp share (split by rank among them) must still cover every word
+    of the ending lane's column. Refill on a 300-clone design (10 bit words per column), plain,
+    from a random start, and from a random start with lag 3 and a meeting cap; bit-exact
+    against the oracle, per slot and in every slot's G record."""
+    inst = synth.make_instance(300, 24, 5, 3, 0.05, 0.15, 3 / 300, 501, 502)
+    k, ell, B, seed = 31, 300, 1200, 4242
+    kw, okw = {}, {}
+    if variant != "plain":
+        nu = np.random.default_rng(12).random(inst.n) * 0.2
+        kw["init_marginals"] = nu
+        okw["init"] = nu
+    if variant == "cap_lag_random_start":
+        kw.update(meeting_cap=2 * ell, lag=3)
+        okw.update(meeting_cap=2 * ell, lag=3)
+    g = _gpu_run(ctx, inst, slots=P, k=k, ell=ell, horizon=B, seed=seed, record_slots=True,
+                 trace_stride=1, **kw)
+    o = _oracle_run(inst, P, k, ell, B, seed, slot_G=True, **okw)
+    _assert_same(g, o)
+    assert np.array_equal(g["trace_G"], o["slot_G"])
+
+
 def test_near_maximum_pair_state(ctx):
     """6560 clones x 200 pools, 4 pools per clone: a chain's column is 256 words, the most that
     15-bit count offsets address, and the staged tables (161 KB) with one warp region and one Y
