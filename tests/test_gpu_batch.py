@@ -278,6 +278,38 @@ def test_batch_mixed_degree_instances(ctx, lanes):
     batch.close()
 
 
+@pytest.mark.parametrize("classes", [1, 2])
+def test_batch_few_slots_per_instance(ctx, classes):
+    """One to three slots per instance, so that a warp's few live lanes hold slots of different
+    instances (2 to 16 bit words per column, mixed degrees) and leave while others go on: the work
+    the live lanes share at a replication's start and end reads the ending lane's own instance.
+    Refill with a horizon of three windows, a random start on two instances; every instance
+    equals the oracle."""
+    from paper_2608_30239_gb300 import mcpd
+    insts = _uneven(5, seed=31) + [synth.make_mixed_instance(40 + 150 * i, 9 + 3 * i, 2, 7, 3, 0.08, 0.18,
+                                                             3 / (40 + 150 * i), 820 + i, 830 + i)
+                                   for i in range(3)]
+    ps = []
+    for i, inst in enumerate(insts):
+        k, ell = oracle.window_defaults(inst.n, 1)
+        ps.append(dict(slots=1 + i % 3, k=k, ell=ell, horizon=3 * ell + 7 * i, seed=901 + i, instance_id=i))
+    ps[1] = dict(ps[1], init_marginals=np.random.default_rng(31).random(insts[1].n) * 0.3)
+    ps[6] = dict(ps[6], init_marginals=np.random.default_rng(32).random(insts[6].n) * 0.3)
+    batch = mcpd.Batch(ctx, insts, ps, classes=classes)
+    est, se, st = _run(ctx, batch)
+    for i, (inst, kw) in enumerate(zip(insts, ps)):
+        M = oracle.Model(inst, init_marginals=kw.get("init_marginals"))
+        run = oracle.coupled_run(kw["k"], kw["ell"], kw["horizon"], kw["seed"], instance=kw["instance_id"])
+        ref = M.run_slots(run, 0, kw["slots"], THREADS)
+        ref["est"], ref["se"] = M.finalize(ref, kw["slots"], kw["ell"] - kw["k"] + 1)
+        got = batch.buckets(i)
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (classes, i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"], equal_nan=True)
+    batch.close()
+
+
 def test_batch_systematic_uncoupled(ctx):
     """Uncoupled systematic-scan chains (Algorithm 1) in a batch of uneven instances, two classes."""
     from paper_2608_30239_gb300 import mcpd
