@@ -239,20 +239,24 @@ typedef struct mcpd_batch mcpd_batch;
  * instances are sorted by pair state (largest first) and cut into classes of about equal work
  * (slots x slot length); each class is its own launch of the sampling kernel, with a launch shape
  * fitted to its largest pair state, on its own stream forked from the context's stream (the
- * classes run concurrently; the finalize waits for all).  Automatic gives as many classes as the
- * total slots fill whole launches (at most four).  Results do not depend on the order or the
- * classes. */
+ * classes run concurrently; the finalize waits for all).  A fixed number cuts all instances
+ * together.  Automatic takes as many classes as the total slots fill whole launches (at most
+ * four) and, in a coupled batch, first groups the instances whose clones all sit in the same
+ * number of pools (3 to 8) by that number, the others together, and cuts each group by size
+ * into that many classes (at most one per instance), so that every class of a degree launches the
+ * build compiled for it.  Results do not depend on the order or the classes. */
 int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
                       const uint8_t *const *ys, const mcpd_params *params, int32_t order_mode,
                       mcpd_batch **out);
 void mcpd_batch_destroy(mcpd_batch *batch);
 /* info[0] total retained clones, [1] instances, [2] total slots, [3] largest n_active,
  * [4] warps per block, [5] blocks and [7] shared-memory bytes per block of the first class (the
- * largest pair state), [6] resident pairs of the widest class, [8] lanes per pair, [9] size
+ * largest pair state of its degree group), [6] resident pairs of the widest class, [8] lanes
+ * per pair, [9] size
  * classes, [10] largest warps per block over the classes, [11] classes that launch the kernel
  * variant with meeting caps and lags > 1, [12] classes that launch a build with a compile-time
- * degree and mask-indexed thresholds (coupled classes, without caps or lags, whose instances all
- * sit in exactly 3 or exactly 6 pools per clone). */
+ * degree (coupled classes whose instances all sit in the same number of pools per clone, 3 to 8;
+ * thresholds indexed by the mask of deciding pools up to 6). */
 int mcpd_batch_info(const mcpd_batch *batch, int64_t info[16]);
 /* offsets: [n_inst + 1] host array receiving each instance's first output index. */
 int mcpd_batch_offsets(const mcpd_batch *batch, int64_t *offsets);

@@ -35,7 +35,8 @@ def _cuda_home() -> str:
 
 def sources():
     return [os.path.join(SRC, f) for f in ("mcpd_tables.cpp", "mcpd_api.cpp", "mcpd_kernels.cu",
-                                           "mcpd_trace.cu", "mcpd_batch.cu", "mcpd_noalloc.cu", "mcpd_mlp.cu", "mcpd_group.cu",
+                                           "mcpd_trace.cu", "mcpd_batch.cu", "mcpd_batch_deg.cu", "mcpd_batch_ext.cu",
+                                           "mcpd_noalloc.cu", "mcpd_mlp.cu", "mcpd_group.cu",
                                            "mcpd_internal.h", "mcpd_device.cuh", "mcpd_pairs.cuh")] + \
         [os.path.join(INCLUDE, "mcpd.h")]
 
@@ -55,7 +56,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     nvcc = os.path.join(cuda, "bin", "nvcc")
     inc = ["-I" + INCLUDE, "-I" + SRC, "-I" + os.path.join(cuda, "include")]
     objs = {name: os.path.join(BUILD, name + ".o")
-            for name in ("tables", "api", "kernels", "trace", "batch", "noalloc", "mlp", "group")}
+            for name in ("tables", "api", "kernels", "trace", "batch", "batch_deg", "batch_ext", "noalloc", "mlp",
+                         "group")}
     cxx = ["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-fno-fast-math", "-Wall"]
     jobs = [
         cxx + inc + ["-c", os.path.join(SRC, "mcpd_tables.cpp"), "-o", objs["tables"]],
@@ -67,6 +69,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         + inc + ["-c", os.path.join(SRC, "mcpd_trace.cu"), "-o", objs["trace"]],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
         + inc + ["-c", os.path.join(SRC, "mcpd_batch.cu"), "-o", objs["batch"]],
+        [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
+        + inc + ["-c", os.path.join(SRC, "mcpd_batch_deg.cu"), "-o", objs["batch_deg"]],
+        [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
+        + inc + ["-c", os.path.join(SRC, "mcpd_batch_ext.cu"), "-o", objs["batch_ext"]],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off"]
         + inc + ["-c", os.path.join(SRC, "mcpd_noalloc.cu"), "-o", objs["noalloc"]],
         [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
@@ -86,7 +92,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         sys.stdout.write("".join(logs))
     tmp = LIB + f".tmp{os.getpid()}"
     link = [nvcc, ARCH, "-shared", "-o", tmp, objs["tables"], objs["api"], objs["kernels"], objs["trace"],
-            objs["batch"], objs["noalloc"], objs["mlp"], objs["group"], "-cudart", "static"]
+            objs["batch"], objs["batch_deg"], objs["batch_ext"], objs["noalloc"], objs["mlp"], objs["group"],
+            "-cudart", "static"]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
     return LIB

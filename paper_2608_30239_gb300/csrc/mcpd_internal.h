@@ -220,6 +220,8 @@ int pairs_shape(int coupled, int scan, int udeg, bool batch, size_t tables, int 
 // compile-time degree a class of uniform degree udeg runs with (0: the generic build).
 using PairsKernelFn = void (*)(const KParams, const BParams);
 PairsKernelFn pick_batch(int coupled, int scan, int udeg, bool wide, bool ext);
+PairsKernelFn pick_batch_degree(int udeg, bool wide);       // coupled, degrees 4, 5, 7, 8 (mcpd_batch_deg.cu)
+PairsKernelFn pick_batch_ext_degree(int udeg, bool wide);   // coupled, cap / lag, degrees 3..8 (mcpd_batch_ext.cu)
 int batch_kernel_degree(int coupled, int ext, int udeg);
 
 // Launchers (mcpd_kernels.cu).

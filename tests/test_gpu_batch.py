@@ -331,13 +331,14 @@ def test_batch_systematic_uncoupled(ctx):
     batch.close()
 
 
-@pytest.mark.parametrize("deg", [3, 6])
+@pytest.mark.parametrize("capped", [False, True])
+@pytest.mark.parametrize("deg", [3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("warps", [0, 12, 20])
-def test_uniform_degree_batches(ctx, deg, warps):
+def test_uniform_degree_batches(ctx, deg, warps, capped):
     """Coupled batches whose instances all sit in `deg` pools per clone launch the build with that
-    compile-time degree and mask-indexed thresholds (info[12]); every instance, of its own size,
-    rates, window, random start or scan weights, equals the oracle alone, in the 12-warp build and
-    the 20-warp one."""
+    compile-time degree (mask-indexed thresholds up to degree 6; info[12]), and with meeting caps
+    the capped build of that degree; every instance, of its own size, rates, window, random start
+    or scan weights, equals the oracle alone, in the 12-warp build and the 20-warp one."""
     from paper_2608_30239_gb300 import mcpd
     insts, ps = [], []
     rng = np.random.default_rng(deg)
@@ -347,6 +348,8 @@ def test_uniform_degree_batches(ctx, deg, warps):
                                    (1 + i % 3) / n, 60 + i, 70 + i)
         k, ell = oracle.window_defaults(n, 1)
         kw = dict(slots=400 + 61 * i, k=k, ell=ell, horizon=3 * ell + 7 * i, seed=90 + i, instance_id=i)
+        if capped and i != 2:
+            kw["meeting_cap"] = ell + 5 * i
         if i == 1:
             kw["init_marginals"] = rng.uniform(0.0, 0.2, n)
         if i == 3:
@@ -361,7 +364,8 @@ def test_uniform_degree_batches(ctx, deg, warps):
     for i, (inst, kw) in enumerate(zip(insts, ps)):
         M = oracle.Model(inst, scan=kw.get("scan", oracle.SCAN_SCORE), custom_w=kw.get("scan_weights"),
                          init_marginals=kw.get("init_marginals"))
-        run = oracle.coupled_run(kw["k"], kw["ell"], kw["horizon"], kw["seed"], instance=kw["instance_id"])
+        run = oracle.coupled_run(kw["k"], kw["ell"], kw["horizon"], kw["seed"], instance=kw["instance_id"],
+                                 meeting_cap=kw.get("meeting_cap", 0))
         ref = M.run_slots(run, 0, kw["slots"], THREADS)
         ref["est"], ref["se"] = M.finalize(ref, kw["slots"], kw["ell"] - kw["k"] + 1)
         got = batch.buckets(i)
@@ -369,6 +373,31 @@ def test_uniform_degree_batches(ctx, deg, warps):
             assert np.array_equal(got[key], ref[key]), (i, key)
         a, b = batch.offsets[i], batch.offsets[i + 1]
         assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"]), i
+    batch.close()
+
+
+def test_automatic_classes_follow_uniform_degree(ctx):
+    """With the number of classes left to the library, coupled instances of one uniform degree
+    get classes of their own (each launching the build of its degree, info[12]); mixed-degree
+    instances stay in the generic build. Every instance equals the oracle."""
+    from paper_2608_30239_gb300 import mcpd
+    insts = [synth.make_instance(150 + 90 * i, 14 + i, d, 2, 0.05, 0.12, 2 / (150 + 90 * i), 970 + i, 980 + i)
+             for i, d in enumerate([4, 7, 4, 5, 7, 4])]
+    insts.append(synth.make_mixed_instance(260, 21, 2, 7, 3, 0.08, 0.18, 3 / 260, 990, 991))
+    ps = _params(insts)
+    for i in (0, 4):
+        ps[i] = dict(ps[i], meeting_cap=ps[i]["ell"] + 11)
+    batch = mcpd.Batch(ctx, insts, ps)
+    # degree groups 4, 5, 7 and the mixed instance: at least one class each, three with a degree build
+    assert batch.classes >= 4 and int(batch.info[12]) >= 3
+    est, se, st = _run(ctx, batch)
+    for i, (inst, kw) in enumerate(zip(insts, ps)):
+        ref = _oracle(inst, kw)
+        got = batch.buckets(i)
+        for key in ("S1", "S2_lo", "S2_hi", "count"):
+            assert np.array_equal(got[key], ref[key]), (i, key)
+        a, b = batch.offsets[i], batch.offsets[i + 1]
+        assert np.array_equal(est[a:b], ref["est"]) and np.array_equal(se[a:b], ref["se"])
     batch.close()
 
 
@@ -415,8 +444,8 @@ def test_batch_extension_by_slot_ranges(ctx):
 def test_batched_workload_full_size(ctx):
     """The batched workload at its full size, as the bench decodes it: 512 uneven instances (n in
     [200, 5000], k in 4..8, rates and positives per instance), 2048 slots each with a 10-sweep
-    horizon and the paper's 20-sweep meeting cap, automatic size classes running concurrently, in
-    a captured graph.  The four smallest instances equal the oracle alone bit for bit (buckets and
+    horizon and the paper's 20-sweep meeting cap, automatic classes (by degree, then size) running
+    concurrently, in a captured graph.  The four smallest instances equal the oracle alone bit for bit (buckets and
     doubles); every instance's estimates are finite, in the valid range of an unbiased estimator's
     mean of bounded corrections, and every slot is counted once."""
     import torch
@@ -425,7 +454,9 @@ def test_batched_workload_full_size(ctx):
     ps = [dict(slots=2048, horizon=10 * inst.n, seed=5000 + i, instance_id=i, meeting_cap=20 * inst.n)
           for i, inst in enumerate(insts)]
     batch = mcpd.Batch(ctx, insts, ps, order_mode=1)
-    assert batch.classes == 4
+    # every instance sits in the same number of pools per clone: every class launches the build
+    # of its degree
+    assert batch.classes >= 4 and int(batch.info[12]) == batch.classes
     est = torch.empty(batch.total_active, dtype=torch.float64, device="cuda:0")
     se = torch.empty_like(est)
     with torch.cuda.stream(ctx.torch_stream):
