@@ -179,8 +179,8 @@ def batched_leg(ctx, device, count=512, budget_slots=1024, budget_sweeps=20, see
     same budget in its own sweeps: `budget_slots` x `budget_sweeps` x n progress units, split into
     P slots of horizon budget_slots x budget_sweeps / P sweeps, with P (slots per instance) chosen by
     the autotuner among `slot_candidates` together with the launch shape (lanes per pair, warps per
-    block; cached per GPU and shape).  One persistent launch per size class (automatic classes),
-    captured in one CUDA graph.  As in the paper's runs, pairs have a meeting cap of `cap_sweeps`
+    block; cached per GPU and shape).  One persistent launch per class (automatic classes: by
+    degree, then by size, each on the build compiled for its degree), captured in one CUDA graph.  As in the paper's runs, pairs have a meeting cap of `cap_sweeps`
     sweeps (a pair unmet there is kept with its correction cut at the cap, and counted).  With
     `uncapped_limit_sweeps` the same batch is also decoded uncapped (the unbiased estimator), with a
     safety step limit of that many sweeps; its step-limit hits are reported (0 means the result is

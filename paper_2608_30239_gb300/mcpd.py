@@ -361,11 +361,12 @@ class Plan:
 
 class Batch:
     """mcpd_batch: many instances (each with its own parameters) decoded in one persistent launch
-    per size class.
+    per class.
 
     `instances` is a list of synth-like instances; `params` a list of keyword dicts (one per
     instance) or one dict for all.  `order_mode` 0 (input order) or 1 (longest slots first);
-    `classes` 0 (automatic) or 1..8 size classes.  Outputs of run()/fetch are concatenated in
+    `classes` 0 (automatic: coupled instances grouped by uniform degree, then cut by size) or 1..8
+    size classes.  Outputs of run()/fetch are concatenated in
     input order; `offsets[i]:offsets[i+1]` belong to instance i."""
 
     def __init__(self, ctx: Context, instances, params, order_mode=0, classes=0):
