@@ -522,7 +522,8 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
     if (lanes != 1 && lanes != 8 && lanes != 16 && lanes != 32)
         return set_err(ctx, MCPD_EINVAL, "lanes per pair must be 1, 8, 16 or 32");
     if (lanes > 1 && !b->coupled) return set_err(ctx, MCPD_EINVAL, "lane groups run coupled batches only");
-    for (BatchClass &c : b->cls) {
+    for (size_t ci = 0; ci < b->cls.size(); ++ci) {
+        BatchClass &c = b->cls[ci];
         int per_sm = 1, w = 0;
         if (lanes == 1) {
             mcpd::PairsShape shape;
@@ -555,7 +556,14 @@ int batch_shape(mcpd_ctx *ctx, mcpd_batch *b, int warps, int lanes = 1) {
         c.warps = w;
         c.block = w * 32;
         c.bp.lanes = lanes;
-        c.grid = ctx->sm_count * per_sm;
+        // A class with fewer slots than one full launch holds pairs for launches only the blocks
+        // its slots fill: a block keeps its shared memory until its last warp ends, so blocks
+        // whose warps find no slot would hold SMs that the concurrently running classes need.
+        const long long class_slots = ci < b->total_work0.size() ? b->total_work0[ci] : c.bp.total_work;
+        const long long pairs_per_block = std::max(1, c.block / lanes);
+        c.grid = static_cast<int>(std::max<long long>(
+            1, std::min<long long>(static_cast<long long>(ctx->sm_count) * per_sm,
+                                   (class_slots + pairs_per_block - 1) / pairs_per_block)));
         c.pairs = static_cast<long long>(c.grid) * c.block / lanes;
         if (c.pairs > c.scratch_pairs) {
             free_list(c.scratch);
