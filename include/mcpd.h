@@ -249,6 +249,13 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
                       const uint8_t *const *ys, const mcpd_params *params, int32_t order_mode,
                       mcpd_batch **out);
 void mcpd_batch_destroy(mcpd_batch *batch);
+/* The classes mcpd_batch_create would form, computed on the host (no device, no context):
+ * class_of[n_inst] (caller-owned) receives each instance's class, numbered 0, 1, ... in launch
+ * order, and *n_classes their number, for a GPU with sm_count multiprocessors (the automatic
+ * class count depends on it).  The same validation of the inputs as mcpd_batch_create. */
+int mcpd_batch_classes(int32_t n_inst, const mcpd_design *designs, const uint8_t *const *ys,
+                       const mcpd_params *params, int32_t order_mode, int32_t sm_count,
+                       int32_t *class_of, int32_t *n_classes);
 /* info[0] total retained clones, [1] instances, [2] total slots, [3] largest n_active,
  * [4] warps per block, [5] blocks and [7] shared-memory bytes per block of the first class (the
  * largest pair state of its degree group), [6] resident pairs of the widest class, [8] lanes

@@ -87,6 +87,76 @@ int dev_alloc(mcpd_ctx *ctx, mcpd_plan *pl, T **ptr, size_t count) {
 
 }  // namespace
 
+// The classes of a batch (mcpd_batch_create, mcpd_batch_classes): each instance's class in
+// cls_of, classes numbered 0, 1, ... in launch order; returns their number.
+static int assign_classes(const std::vector<mcpd::Tables> &t, int want_classes, int sm_count,
+                          std::vector<int32_t> *cls_out) {
+    const int32_t n_inst = static_cast<int32_t>(t.size());
+    // Size classes: instances by pair state (words per column), largest first, cut into classes
+    // of about equal work (slots x slot length), as many as whole rounds of a full launch allow
+    // (at most four) unless the caller fixed the number.  With the number left to the library,
+    // coupled instances of one uniform degree (3 to 8) are grouped by that degree first, so that
+    // each class launches the build compiled for its degree, and every group is cut by size into
+    // that many classes (at most one per instance).  Measured on 512 uneven instances with
+    // degrees 4 to 8: four size classes per degree group beat one and two.
+    auto work_of = [&](int32_t i) { return static_cast<double>(t[i].P) * static_cast<double>(std::max(t[i].B, t[i].unit)); };
+    int64_t total_slots = 0;
+    double total_work = 0.0;
+    for (int32_t i = 0; i < n_inst; ++i) { total_slots += t[i].P; total_work += work_of(i); }
+    int n_cls = want_classes;
+    if (n_cls == 0) {
+        const int64_t round = static_cast<int64_t>(sm_count) * 32 * 20;
+        n_cls = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(4, total_slots / std::max<int64_t>(1, round))));
+    }
+    n_cls = std::min(n_cls, n_inst);
+    std::vector<int32_t> key(n_inst, 0);       // degree group (0: any degree, the generic build)
+    if (want_classes == 0)
+        for (int32_t i = 0; i < n_inst; ++i) key[i] = mcpd::batch_kernel_degree(t[0].coupled ? 1 : 0, 0, t[i].udeg);
+    // instances by group, then largest pair state first
+    std::vector<int32_t> by_size(n_inst);
+    for (int32_t i = 0; i < n_inst; ++i) by_size[i] = i;
+    std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t c) {
+        if (key[a] != key[c]) return key[a] < key[c];
+        return t[a].wpp > t[c].wpp;
+    });
+    std::vector<int32_t> cls_of(n_inst, 0);
+    {
+        int base = 0;
+        for (int32_t g0 = 0; g0 < n_inst;) {
+            int32_t g1 = g0;
+            double gwork = 0.0;
+            while (g1 < n_inst && key[by_size[g1]] == key[by_size[g0]]) gwork += work_of(by_size[g1++]);
+            const int32_t gn = g1 - g0;
+            const int ng = std::max(1, std::min(n_cls, gn));
+            double acc = 0.0;
+            for (int32_t pos = g0; pos < g1; ++pos) {
+                const int32_t i = by_size[pos];
+                const int32_t k = pos - g0;
+                int c = static_cast<int>(gwork > 0 ? acc / gwork * ng : 0.0);
+                c = std::min(c, ng - 1);
+                // every class keeps at least one instance
+                c = std::max(c, ng - (gn - k));
+                c = std::min(c, k);
+                cls_of[i] = base + c;
+                acc += work_of(i);
+            }
+            base += ng;
+            g0 = g1;
+        }
+        // number the classes that received instances 0, 1, ... (a heavy instance may skip one)
+        int next = 0, last = -1;
+        for (int32_t pos = 0; pos < n_inst; ++pos) {
+            const int32_t i = by_size[pos];
+            if (cls_of[i] != last) { last = cls_of[i]; ++next; }
+            cls_of[i] = next - 1;
+        }
+    }
+    *cls_out = cls_of;
+    int n_cls_out = 0;
+    for (int32_t i = 0; i < n_inst; ++i) n_cls_out = std::max(n_cls_out, cls_of[i] + 1);
+    return n_cls_out;
+}
+
 extern "C" {
 
 int mcpd_ctx_create(int device, void *cuda_stream, mcpd_ctx **out) {
@@ -436,6 +506,26 @@ int mcpd_inspect(const mcpd_design *design, const uint8_t *y, const mcpd_params 
     return MCPD_OK;
 }
 
+int mcpd_batch_classes(int32_t n_inst, const mcpd_design *designs, const uint8_t *const *ys,
+                       const mcpd_params *params, int32_t order_mode, int32_t sm_count,
+                       int32_t *class_of, int32_t *n_classes) {
+    if (n_inst < 1 || !designs || !ys || !params || !class_of || !n_classes || sm_count < 1) return MCPD_EINVAL;
+    const int32_t want_classes = (order_mode >> 8) & 0xFF;
+    if ((order_mode & 0xFF) > 1 || want_classes > 8 || (order_mode >> 16) != 0) return MCPD_EINVAL;
+    std::vector<mcpd::Tables> t(n_inst);
+    for (int32_t i = 0; i < n_inst; ++i) {
+        std::string err;
+        const int rc = mcpd::build_tables(&designs[i], ys[i], &params[i], &t[i], &err);
+        if (rc != MCPD_OK) return rc;
+        if (t[i].coupled != t[0].coupled || (t[i].scan == MCPD_SCAN_SYSTEMATIC) != (t[0].scan == MCPD_SCAN_SYSTEMATIC))
+            return MCPD_EINVAL;
+    }
+    std::vector<int32_t> cls;
+    *n_classes = assign_classes(t, want_classes, sm_count, &cls);
+    std::memcpy(class_of, cls.data(), static_cast<size_t>(n_inst) * sizeof(int32_t));
+    return MCPD_OK;
+}
+
 int mcpd_philox_device(mcpd_ctx *ctx, const uint32_t *ctr_dev, uint32_t key0, uint32_t key1,
                        uint32_t *out_dev, int64_t n) {
     if (!ctx || (n > 0 && (!ctr_dev || !out_dev)) || n < 0) return MCPD_EINVAL;
@@ -676,65 +766,10 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
     b->coupled = b->t[0].coupled;
     if (cudaSetDevice(ctx->device) != cudaSuccess) { mcpd_batch_destroy(b); return set_err(ctx, MCPD_ECUDA, "cudaSetDevice"); }
 
-    // Size classes: instances by pair state (words per column), largest first, cut into classes
-    // of about equal work (slots x slot length), as many as whole rounds of a full launch allow
-    // (at most four) unless the caller fixed the number.  With the number left to the library,
-    // coupled instances of one uniform degree (3 to 8) are grouped by that degree first, so that
-    // each class launches the build compiled for its degree, and every group is cut by size into
-    // that many classes (at most one per instance).  Measured on 512 uneven instances with
-    // degrees 4 to 8: four size classes per degree group beat one and two.
-    auto work_of = [&](int32_t i) { return static_cast<double>(b->t[i].P) * static_cast<double>(std::max(b->t[i].B, b->t[i].unit)); };
+    std::vector<int32_t> cls_of;
+    int n_cls = assign_classes(b->t, want_classes, ctx->sm_count, &cls_of);
     int64_t total_slots = 0;
-    double total_work = 0.0;
-    for (int32_t i = 0; i < n_inst; ++i) { total_slots += b->t[i].P; total_work += work_of(i); }
-    int n_cls = want_classes;
-    if (n_cls == 0) {
-        const int64_t round = static_cast<int64_t>(ctx->sm_count) * 32 * 20;
-        n_cls = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(4, total_slots / std::max<int64_t>(1, round))));
-    }
-    n_cls = std::min(n_cls, n_inst);
-    std::vector<int32_t> key(n_inst, 0);       // degree group (0: any degree, the generic build)
-    if (want_classes == 0)
-        for (int32_t i = 0; i < n_inst; ++i) key[i] = mcpd::batch_kernel_degree(b->t[0].coupled ? 1 : 0, 0, b->t[i].udeg);
-    // instances by group, then largest pair state first
-    std::vector<int32_t> by_size(n_inst);
-    for (int32_t i = 0; i < n_inst; ++i) by_size[i] = i;
-    std::stable_sort(by_size.begin(), by_size.end(), [&](int32_t a, int32_t c) {
-        if (key[a] != key[c]) return key[a] < key[c];
-        return b->t[a].wpp > b->t[c].wpp;
-    });
-    std::vector<int32_t> cls_of(n_inst, 0);
-    {
-        int base = 0;
-        for (int32_t g0 = 0; g0 < n_inst;) {
-            int32_t g1 = g0;
-            double gwork = 0.0;
-            while (g1 < n_inst && key[by_size[g1]] == key[by_size[g0]]) gwork += work_of(by_size[g1++]);
-            const int32_t gn = g1 - g0;
-            const int ng = std::max(1, std::min(n_cls, gn));
-            double acc = 0.0;
-            for (int32_t pos = g0; pos < g1; ++pos) {
-                const int32_t i = by_size[pos];
-                const int32_t k = pos - g0;
-                int c = static_cast<int>(gwork > 0 ? acc / gwork * ng : 0.0);
-                c = std::min(c, ng - 1);
-                // every class keeps at least one instance
-                c = std::max(c, ng - (gn - k));
-                c = std::min(c, k);
-                cls_of[i] = base + c;
-                acc += work_of(i);
-            }
-            base += ng;
-            g0 = g1;
-        }
-        // number the classes that received instances 0, 1, ... (a heavy instance may skip one)
-        int next = 0, last = -1;
-        for (int32_t pos = 0; pos < n_inst; ++pos) {
-            const int32_t i = by_size[pos];
-            if (cls_of[i] != last) { last = cls_of[i]; ++next; }
-            cls_of[i] = next - 1;
-        }
-    }
+    for (int32_t i = 0; i < n_inst; ++i) total_slots += b->t[i].P;
     // Launch order: class by class; within a class, 0 = input order, 1 = longest slots first.
     b->order.resize(n_inst);
     for (int32_t i = 0; i < n_inst; ++i) b->order[i] = i;
@@ -743,7 +778,6 @@ int mcpd_batch_create(mcpd_ctx *ctx, int32_t n_inst, const mcpd_design *designs,
         if (mode == 1) return std::max(b->t[a].B, b->t[a].unit) > std::max(b->t[c].B, b->t[c].unit);
         return false;
     });
-    n_cls = cls_of[b->order[n_inst - 1]] + 1;
 
     // Sizes.
     size_t table_bytes = 0;

@@ -103,6 +103,7 @@ def lib(build_if_missing: bool = False):
                                               P, P, C.POINTER(mcpd_stats)]),
             "mcpd_batch_create": (C.c_int, [P, C.c_int32, P, P, P, C.c_int32, C.POINTER(P)]),
             "mcpd_batch_destroy": (None, [P]),
+            "mcpd_batch_classes": (C.c_int, [C.c_int32, P, P, P, C.c_int32, C.c_int32, P, P]),
             "mcpd_batch_info": (C.c_int, [P, P]),
             "mcpd_batch_offsets": (C.c_int, [P, P]),
             "mcpd_batch_set_shape": (C.c_int, [P, P, C.c_int32, C.c_int32]),
@@ -357,6 +358,31 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def batch_classes(instances, params, order_mode=0, classes=0, sm_count=152):
+    """mcpd_batch_classes: the classes a Batch of these instances would form on a GPU with
+    `sm_count` multiprocessors, computed on the host.  Returns (class of each instance, number of
+    classes)."""
+    n = len(instances)
+    if isinstance(params, dict):
+        params = [params] * n
+    keep = _Keep()
+    designs = (mcpd_design * n)()
+    ys = (C.c_void_p * n)()
+    prms = (mcpd_params * n)()
+    for i, (inst, kw) in enumerate(zip(instances, params)):
+        d, y = make_design(inst, keep)
+        designs[i] = d
+        ys[i] = _ptr(y).value
+        prms[i] = make_params(inst, keep, **kw)
+    cls = np.zeros(n, np.int32)
+    nc = C.c_int32(0)
+    rc = lib().mcpd_batch_classes(n, designs, ys, prms, int(order_mode) | (int(classes) << 8), int(sm_count),
+                                  _ptr(cls), C.byref(nc))
+    if rc != MCPD_OK:
+        raise McpdError(rc, "mcpd_batch_classes")
+    return cls, int(nc.value)
 
 
 class Batch:
