@@ -609,7 +609,7 @@ def test_uncoupled_path_follows_algorithms_1_and_2(oracle_lib, scan, burn, lengt
     the path, the site I_t = t mod n_a (systematic) or the alias draw of the step word (score,
     uniform), X_{t+1} differs from X_t at most at I_t, and its new bit is 1{U_t / 2^64 < p} with
     p = sigmoid(log pi(x^{I<-1}) - log pi(x^{I<-0})) from the unnormalised posterior (draws within
-    1e-9 of p are not judged).  A chain that averages X_{b+1}..X_{b+T}, charges b + T draws or
+    1e-9 of p are not checked).  A chain that averages X_{b+1}..X_{b+T}, charges b + T draws or
     visits I_t = (t + 1) mod n_a fails here."""
     inst = _noisy()
     sc = {"systematic": oracle_lib.SCAN_SYSTEMATIC, "score": oracle_lib.SCAN_SCORE,
@@ -621,7 +621,7 @@ def test_uncoupled_path_follows_algorithms_1_and_2(oracle_lib, scan, burn, lengt
     active = np.arange(inst.n)
     run = oracle_lib.uncoupled_run(burn, length, 0, seed=seed)
     C = burn + length - 1
-    judged = 0
+    checked = 0
     for slot in range(40):
         rr = M.replication(run, slot, 0, traj_cap=C + 1)
         assert rr["status"] == 0 and rr["C"] == C and rr["draws"] == C
@@ -640,8 +640,8 @@ def test_uncoupled_path_follows_algorithms_1_and_2(oracle_lib, scan, burn, lengt
             u = U / 2.0 ** 64
             if abs(u - p) > 1e-9:
                 assert X[t + 1][I] == (1 if u < p else 0), (slot, t)
-                judged += 1
-    assert judged >= 40 * C * 0.99
+                checked += 1
+    assert checked >= 40 * C * 0.99
 
 
 def test_uncoupled_long_chain_agrees_with_enumeration(oracle_lib):
