@@ -505,7 +505,9 @@ __global__ void __launch_bounds__(BATCH ? (WIDE ? 640 : 384) : (DEG >= 6 ? 640 :
         const uint32_t B = v_B();
         const uint32_t S_next = S + C;
         const bool goes_on = S_next < B && B - S_next >= v_unit();
-        finish_rep(true, C, goes_on);     // a slot's last replication ends before its flush (end_slot)
+        // a slot's last replication ends before its flush (end_slot); the 12-warp batch build
+        // (up to 168 registers) keeps the one-lane end, measured faster there
+        finish_rep(true, C, goes_on && !(BATCH && !WIDE));
         S = S_next;
         N += 1;
         red_add(reinterpret_cast<long long *>(&pst()[kPsRetained]), 1 + over);
